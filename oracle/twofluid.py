@@ -24,7 +24,9 @@ binary fluid mixture", arXiv 2511.00445):
 Readings where the paper is silent or ambiguous (each is listed in the design doc):
 lattice units (dt = dx = 1, tau given directly); A_ch multiplies the double
 well and kappa = eps^2; the LdG coefficients A_Q, B_Q, C_Q are parameters (B_Q
-drops out in 2D); forces enter each lattice-Boltzmann fluid per unit volume
+drops out in 2D) and default to a bulk order S = sqrt(-A_Q/C_Q) = 1/2, the
+value at which the co-rotation term puts the tumbling-to-aligning transition
+at |lambda| = 1 as Sec. II states; forces enter each lattice-Boltzmann fluid per unit volume
 (the phi factors on the left of Eq. 4-5 are not divided out); the elastic force
 is the divergence of the elastic stress on its second index, applied to fluid 1;
 the Guo half-force velocity shift includes the implicit drag, which turns the
@@ -70,7 +72,7 @@ class Params:
     Gamma_Q: float = 0.2     # rotational diffusion Gamma in Eq. (11)
     A_Q: float = -0.1        # Landau-de Gennes A, Eq. (8)
     B_Q: float = 0.0         # Landau-de Gennes B (drops out in 2D)
-    C_Q: float = 0.1         # Landau-de Gennes C
+    C_Q: float = 0.4         # Landau-de Gennes C (bulk order sqrt(-A_Q/C_Q) = 1/2)
     M: float = 0.2           # Cahn-Hilliard mobility, Eq. (1)
     A_ch: float = 0.05       # prefactor of the double well f(phi)
     kappa: float = 0.1       # eps^2 in mu = A_ch f'(phi) - eps^2 lap(phi), Eq. (2)

@@ -1,0 +1,285 @@
+"""Thin ctypes binding of libtwofluid (include/twofluid.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies the device workspace and the stream.  If the
+library is missing the import of the binding raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields, replace
+from typing import Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtwofluid.so")
+
+TF_OK = 0
+TF_ERR_ARG = -1
+TF_ERR_CUDA = -2
+TF_ERR_NONFINITE = -3
+TF_ERR_TIMEOUT = -4
+TF_ERR_IO = -5
+TF_ERR_WORKSPACE = -6
+
+FIELD_PHI, FIELD_QXX, FIELD_QXY = 0, 1, 2
+FIELD_U1X, FIELD_U1Y, FIELD_U2X, FIELD_U2Y = 3, 4, 5, 6
+FIELD_RHO1, FIELD_RHO2, FIELD_MU = 7, 8, 9
+FIELD_F1, FIELD_F2 = 16, 32
+STORE_F32 = 0
+NCONS = 8
+
+# Every symbol include/twofluid.h declares, in declaration order.
+EXPORTS = [
+    "tf_workspace_bytes", "tf_create", "tf_destroy", "tf_last_error", "tf_init_fields",
+    "tf_write_field", "tf_set_equilibrium", "tf_read_field", "tf_step", "tf_sync",
+    "tf_step_count", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
+    "tf_length_scale", "tf_energy_spectrum", "tf_phase_difference", "tf_phi_stats",
+    "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load",
+]
+
+
+class TFParams(ctypes.Structure):
+    """Mirror of struct tf_params."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("n_sub", ctypes.c_int),
+                ("storage", ctypes.c_int),
+                ("tau1", ctypes.c_double), ("tau2", ctypes.c_double),
+                ("rho1", ctypes.c_double), ("rho2", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("K", ctypes.c_double),
+                ("Gamma_Q", ctypes.c_double), ("A_Q", ctypes.c_double), ("C_Q", ctypes.c_double),
+                ("M", ctypes.c_double), ("A_ch", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("phi_ref", ctypes.c_double)]
+
+
+@dataclass(frozen=True)
+class SolverParams:
+    """Per-instance parameters (lattice units); defaults are the 64x64
+    correctness configuration (zeta 0.005, lambda 0.7, K 0.04, drag 0.01,
+    tau 1) with the Sec. III constants M 0.2, A 0.05, kappa 0.1, Gamma_Q 0.2, and
+    Landau-de Gennes A_Q -0.1, C_Q 0.4 (bulk order 1/2)."""
+    nx: int = 64
+    ny: int = 64
+    n_sub: int = 5
+    storage: int = STORE_F32
+    tau1: float = 1.0
+    tau2: float = 1.0
+    rho1: float = 1.0
+    rho2: float = 1.0
+    gamma: float = 0.01
+    zeta: float = 0.005
+    lam: float = 0.7
+    K: float = 0.04
+    Gamma_Q: float = 0.2
+    A_Q: float = -0.1
+    C_Q: float = 0.4
+    M: float = 0.2
+    A_ch: float = 0.05
+    kappa: float = 0.1
+    phi_ref: float = 0.5
+
+    def with_(self, **kw) -> "SolverParams":
+        return replace(self, **kw)
+
+    def to_c(self) -> TFParams:
+        kw = {f.name: getattr(self, f.name) for f in fields(self)}
+        kw["lambda_"] = kw.pop("lam")
+        return TFParams(**kw)
+
+
+class TwoFluidError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libtwofluid error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library() -> ctypes.CDLL:
+    """Load libtwofluid.so (built by paper_2511_00445_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2511_00445_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, i64, d, dp, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                             ctypes.POINTER(ctypes.c_double), ctypes.c_size_t)
+    P = ctypes.POINTER(TFParams)
+    sig = {
+        "tf_workspace_bytes": (sz, [P, i]),
+        "tf_create": (i, [P, i, vp, sz, vp, ctypes.POINTER(vp)]),
+        "tf_destroy": (i, [vp]),
+        "tf_last_error": (ctypes.c_char_p, [vp]),
+        "tf_init_fields": (i, [vp, i, ctypes.c_uint64, d, d, d]),
+        "tf_write_field": (i, [vp, i, i, dp]),
+        "tf_set_equilibrium": (i, [vp, i, dp, dp]),
+        "tf_read_field": (i, [vp, i, i, dp]),
+        "tf_step": (i, [vp, i64]),
+        "tf_sync": (i, [vp]),
+        "tf_step_count": (i64, [vp]),
+        "tf_conserved": (i, [vp, i, dp]),
+        "tf_n_shell": (i, [vp]),
+        "tf_shell_counts": (i, [vp, dp, i]),
+        "tf_structure_factor": (i, [vp, i, dp, i]),
+        "tf_length_scale": (i, [vp, i, dp]),
+        "tf_energy_spectrum": (i, [vp, i, dp, i, dp]),
+        "tf_phase_difference": (i, [vp, i, dp]),
+        "tf_phi_stats": (i, [vp, i, dp, dp]),
+        "tf_state_bytes": (sz, [vp]),
+        "tf_advance_host": (i, [vp, vp, i64, vp]),
+        "tf_save": (i, [vp, ctypes.c_char_p]),
+        "tf_load": (i, [vp, ctypes.c_char_p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class TwoFluid:
+    """A batch of same-size instances on one GPU, behind the C ABI.
+
+    Method names follow the C entry points without their ``tf_`` prefix.
+    """
+
+    def __init__(self, params: SolverParams | Sequence[SolverParams], device="cuda", stream=None):
+        import torch
+        self.lib = load_library()
+        plist = [params] if isinstance(params, SolverParams) else list(params)
+        self.params = plist
+        self.batch = len(plist)
+        self.nx, self.ny = plist[0].nx, plist[0].ny
+        arr = (TFParams * self.batch)(*[p.to_c() for p in plist])
+        self._carr = arr
+        nbytes = self.lib.tf_workspace_bytes(arr, self.batch)
+        if nbytes == 0:
+            raise TwoFluidError(TF_ERR_ARG, "invalid parameters")
+        self.device = torch.device(device)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ctx = ctypes.c_void_p()
+        rc = self.lib.tf_create(arr, self.batch, ctypes.c_void_p(aligned), nbytes,
+                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+        if rc != TF_OK:
+            raise TwoFluidError(rc, "tf_create failed")
+        self.ctx = ctx
+        self.workspace_bytes = nbytes
+
+    # -- helpers
+    def _check(self, rc: int):
+        if rc != TF_OK:
+            raise TwoFluidError(rc, self.lib.tf_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.tf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state
+    def init_fields(self, seed: int, phi0: float = 0.5, dphi: float = 0.01, S0: float = 0.01,
+                    inst: int = -1):
+        self._check(self.lib.tf_init_fields(self.ctx, inst, seed, phi0, dphi, S0))
+
+    def write_field(self, inst: int, field: int, values: np.ndarray):
+        a = np.ascontiguousarray(values, dtype=np.float64).reshape(self.ny, self.nx)
+        self._check(self.lib.tf_write_field(self.ctx, inst, field, _dptr(a)))
+
+    def set_equilibrium(self, inst: int, u1: np.ndarray | None = None, u2: np.ndarray | None = None):
+        def conv(u):
+            if u is None:
+                return None, None
+            a = np.ascontiguousarray(u, dtype=np.float64).reshape(2, self.ny, self.nx)
+            return a, _dptr(a)
+        a1, p1 = conv(u1)
+        a2, p2 = conv(u2)
+        self._check(self.lib.tf_set_equilibrium(self.ctx, inst, p1, p2))
+        del a1, a2
+
+    def read_field(self, inst: int, field: int) -> np.ndarray:
+        out = np.empty((self.ny, self.nx), dtype=np.float64)
+        self._check(self.lib.tf_read_field(self.ctx, inst, field, _dptr(out)))
+        return out
+
+    def step(self, n: int = 1):
+        self._check(self.lib.tf_step(self.ctx, n))
+
+    def sync(self):
+        self._check(self.lib.tf_sync(self.ctx))
+
+    def step_count(self) -> int:
+        return int(self.lib.tf_step_count(self.ctx))
+
+    # -- observables
+    def conserved(self, inst: int, check: bool = True) -> np.ndarray:
+        out = np.empty(NCONS)
+        rc = self.lib.tf_conserved(self.ctx, inst, _dptr(out))
+        if check or rc != TF_ERR_NONFINITE:
+            self._check(rc)
+        return out
+
+    def n_shell(self) -> int:
+        return int(self.lib.tf_n_shell(self.ctx))
+
+    def shell_counts(self) -> np.ndarray:
+        out = np.empty(self.n_shell())
+        self._check(self.lib.tf_shell_counts(self.ctx, _dptr(out), out.size))
+        return out
+
+    def structure_factor(self, inst: int) -> np.ndarray:
+        out = np.empty(self.n_shell())
+        self._check(self.lib.tf_structure_factor(self.ctx, inst, _dptr(out), out.size))
+        return out
+
+    def length_scale(self, inst: int) -> float:
+        out = ctypes.c_double()
+        self._check(self.lib.tf_length_scale(self.ctx, inst, ctypes.byref(out)))
+        return out.value
+
+    def energy_spectrum(self, inst: int):
+        out = np.empty(self.n_shell())
+        tot = ctypes.c_double()
+        self._check(self.lib.tf_energy_spectrum(self.ctx, inst, _dptr(out), out.size,
+                                                ctypes.byref(tot)))
+        return out, tot.value
+
+    def phase_difference(self, inst: int) -> np.ndarray:
+        out = np.empty(6)
+        self._check(self.lib.tf_phase_difference(self.ctx, inst, _dptr(out)))
+        return out
+
+    def phi_stats(self, inst: int):
+        m, s = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.tf_phi_stats(self.ctx, inst, ctypes.byref(m), ctypes.byref(s)))
+        return m.value, s.value
+
+    # -- raw state, end-to-end, checkpoints
+    def state_bytes(self) -> int:
+        return int(self.lib.tf_state_bytes(self.ctx))
+
+    def advance_host(self, h_in_ptr: int | None, n: int, h_out_ptr: int | None):
+        self._check(self.lib.tf_advance_host(self.ctx, h_in_ptr, n, h_out_ptr))
+
+    def save(self, path: str):
+        self._check(self.lib.tf_save(self.ctx, path.encode()))
+
+    def load(self, path: str):
+        self._check(self.lib.tf_load(self.ctx, path.encode()))

@@ -400,6 +400,26 @@ def test_director_rotation_in_shear(lam, S0, th):
     del a, b
 
 
+def test_tumbling_threshold_at_unit_lambda():
+    """Sec. II: |lambda| < 1 tumbles, |lambda| > 1 flow-aligns.  At the bulk
+    order S0 = sqrt(-A_Q/C_Q) of the default parameters the director rate of
+    Eq. (12) under shear has a steady (aligned) angle iff lambda >= 1."""
+    S0 = math.sqrt(-P0.A_Q / P0.C_Q)
+    r = 0.1
+    Wg = np.zeros((2, 2, 1))
+    Wg[0, 1] = r
+    th = np.linspace(0, np.pi, 721)
+    for lam, aligns in ((0.9, False), (0.99, False), (1.01, True), (1.1, True), (2.0, True)):
+        rates = []
+        for t_ in th:
+            Q = O.q_tensor(np.array([S0 * np.cos(2 * t_)]), np.array([S0 * np.sin(2 * t_)]))
+            dxx, dxy = O.traceless_symmetric(O.corotation(Wg, Q, P0.with_(lam=lam)))
+            rates.append(float((-np.sin(2 * t_) * dxx + np.cos(2 * t_) * dxy)[0]))
+        rates = np.array(rates)
+        has_zero = bool(np.any(rates >= 0) and np.any(rates < 0))
+        assert has_zero == aligns
+
+
 def test_corotation_rigid_rotation():
     """lam = 0, rigid rotation u = w (-y, x): Q rotates counter-clockwise at
     angular rate w, i.e. dQxx/dt = -2 w Qxy, dQxy/dt = 2 w Qxx."""
