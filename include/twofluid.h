@@ -1,0 +1,196 @@
+/*
+ * twofluid.h -- C ABI of the GB300 two-fluid active-nematic / passive-fluid
+ * lattice solver (Ahmed, Lin & Qu, "Phase separation dynamics and active
+ * turbulence in a binary fluid mixture", arXiv 2511.00445).
+ *
+ * One coupled lattice time step (Sec. II model, Sec. III scheme):
+ *   - forces from phi^n, Q^n: chemical potential mu = A_ch f'(phi) - kappa
+ *     lap(phi) (Eq. 2), molecular field H (Eq. 7-8), elastic stress (Sec. II
+ *     display after Eq. 6), active force div(zeta phi Q), capillary force
+ *     mu grad(phi) - grad(phi mu) (Eq. 10);
+ *   - two D2Q9 BGK lattice-Boltzmann fluids with Guo forcing, coupled by the
+ *     drag gamma phi (1-phi)(u2 - u1) (Eq. 4-5), taken implicitly inside the
+ *     Guo half-force velocity (a 2x2 solve per site);
+ *   - n_sub forward-Euler finite-difference sub-steps (Sec. III: five per
+ *     lattice step) of Cahn-Hilliard (Eq. 1/3) and Beris-Edwards (Eq. 11-12)
+ *     with the step's velocities frozen;
+ *   - periodic boundaries in x and y for every field.
+ *
+ * Conventions for every entry point:
+ *   - Lattice units: dx = dt_LBM = 1, c_s^2 = 1/3, dt_fd = 1/n_sub.
+ *   - A context holds `batch` independent instances (e.g. a parameter sweep)
+ *     that share nx, ny and n_sub; each instance has its own tf_params.
+ *   - Host arrays are row-major (y, x): element (x, y) at index y*nx + x, in
+ *     double precision, nx*ny entries, caller-owned.
+ *   - Device memory: the caller allocates ONE device workspace of at least
+ *     tf_workspace_bytes() bytes (256-byte aligned) and keeps it alive until
+ *     tf_destroy().  The library never allocates or frees device memory.
+ *   - `stream` is a cudaStream_t passed as void*; all device work of a
+ *     context is ordered on it.  tf_step() is asynchronous; entry points that
+ *     fill host arrays synchronise the stream before returning.
+ *   - Every function returns TF_OK (0) or a negative TF_ERR_* code; the
+ *     message of the last failure is available from tf_last_error().  No
+ *     C++ exception crosses this boundary and no kernel traps.
+ */
+#ifndef TWOFLUID_H
+#define TWOFLUID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define TF_OK             0
+#define TF_ERR_ARG       (-1)  /* invalid argument (sizes, ids, null pointers)   */
+#define TF_ERR_CUDA      (-2)  /* a CUDA runtime call or kernel launch failed    */
+#define TF_ERR_NONFINITE (-3)  /* NaN or Inf found in the state                  */
+#define TF_ERR_TIMEOUT   (-4)  /* a bounded device wait ran out                  */
+#define TF_ERR_IO        (-5)  /* checkpoint file could not be read or written   */
+#define TF_ERR_WORKSPACE (-6)  /* workspace missing, too small or misaligned     */
+
+/* ---- field ids for tf_read_field / tf_write_field -------------------- */
+#define TF_FIELD_PHI   0   /* concentration phi of the active fluid (r/w)        */
+#define TF_FIELD_QXX   1   /* Q_xx (Q is traceless symmetric, Q_yy = -Q_xx) (r/w) */
+#define TF_FIELD_QXY   2   /* Q_xy (r/w)                                         */
+#define TF_FIELD_U1X   3   /* Guo velocity of fluid 1 (read only, derived)      */
+#define TF_FIELD_U1Y   4
+#define TF_FIELD_U2X   5   /* Guo velocity of fluid 2 (read only, derived)      */
+#define TF_FIELD_U2Y   6
+#define TF_FIELD_RHO1  7   /* density of fluid 1 (read only, derived)            */
+#define TF_FIELD_RHO2  8   /* density of fluid 2 (read only, derived)            */
+#define TF_FIELD_MU    9   /* chemical potential mu (read only, derived)         */
+#define TF_FIELD_F1   16   /* + i (i = 0..8): pre-collision population f_i of fluid 1 (r/w) */
+#define TF_FIELD_F2   32   /* + i (i = 0..8): pre-collision population f_i of fluid 2 (r/w) */
+/* D2Q9 direction order: c0 = (0,0); c1..c4 = (1,0), (0,1), (-1,0), (0,-1);
+ * c5..c8 = (1,1), (-1,1), (-1,-1), (1,-1). */
+
+/* ---- storage precision of the populations ---------------------------- */
+#define TF_STORE_F32   0   /* FP32 deviations f_i - w_i                       */
+
+/* Per-instance parameters (Sec. III parameter list; lattice units). */
+typedef struct tf_params {
+    int    nx, ny;      /* grid size, >= 1 each; identical for all instances    */
+    int    n_sub;       /* FD sub-steps per lattice step (Sec. III: 5), 1..64   */
+    int    storage;     /* TF_STORE_*                                           */
+    double tau1, tau2;  /* BGK relaxation times (> 1/2); nu_k = (tau_k - 1/2)/3 */
+    double rho1, rho2;  /* rest densities of the initial equilibrium           */
+    double gamma;       /* drag coefficient (Eq. 4-5)                          */
+    double zeta;        /* activity (F_active = div(zeta phi Q))               */
+    double lambda;      /* tumbling parameter (Eq. 12, elastic stress)         */
+    double K;           /* Frank elastic constant (Eq. 8)                      */
+    double Gamma_Q;     /* rotational diffusion Gamma (Eq. 11)                 */
+    double A_Q, C_Q;    /* Landau-de Gennes coefficients (Eq. 8; B drops in 2D)*/
+    double M;           /* Cahn-Hilliard mobility (Eq. 1)                      */
+    double A_ch;        /* double-well prefactor: f -> A_ch phi^2 (1-phi)^2    */
+    double kappa;       /* eps^2 of Eq. (2)                                    */
+    double phi_ref;     /* reference value phi is stored relative to (use the
+                           mean concentration, e.g. 0.5)                        */
+} tf_params;
+
+typedef struct tf_ctx tf_ctx;   /* opaque, library-owned host object */
+
+/* Bytes of device workspace needed for `batch` instances described by
+ * params[0..batch-1].  Returns 0 when the parameters are invalid. */
+size_t tf_workspace_bytes(const tf_params* params, int batch);
+
+/* Create a context over caller-owned device memory.  `params` holds `batch`
+ * entries (copied).  `d_workspace` must be 256-byte aligned and at least
+ * tf_workspace_bytes(params, batch) bytes.  The state starts zeroed (all
+ * populations at the rest equilibrium w_i, phi = phi_ref, Q = 0). */
+int tf_create(const tf_params* params, int batch, void* d_workspace,
+              size_t workspace_bytes, void* stream, tf_ctx** out);
+int tf_destroy(tf_ctx* ctx);
+const char* tf_last_error(const tf_ctx* ctx);
+
+/* Initial condition of Sec. III with the director form of Eq. (9):
+ * phi = phi0 + dphi (2U - 1), theta = pi U', Q_xx = S0 cos 2theta,
+ * Q_xy = S0 sin 2theta, populations at the rest equilibrium (u = 0) with
+ * densities rho1, rho2.  U, U' are SplitMix64 counter draws keyed by
+ * (seed, field id 0 / 1, site index y*nx + x).  inst = -1: all instances,
+ * each with the same seed.  Asynchronous. */
+int tf_init_fields(tf_ctx* ctx, int inst, uint64_t seed, double phi0,
+                   double dphi, double S0);
+
+/* Overwrite a stored field of one instance from a host array (synchronous).
+ * Writable: TF_FIELD_PHI, QXX, QXY and the 18 populations. */
+int tf_write_field(tf_ctx* ctx, int inst, int field, const double* host);
+
+/* Set both fluids' populations to the equilibrium with rest densities
+ * rho1, rho2 and the given velocities (host arrays of 2*nx*ny doubles laid
+ * out as [component x/y][y][x]; NULL means zero).  Synchronous. */
+int tf_set_equilibrium(tf_ctx* ctx, int inst, const double* u1, const double* u2);
+
+/* Read one field of one instance into a host array of nx*ny doubles.
+ * Derived fields (velocities, densities, mu) are evaluated on the current
+ * state exactly as the next step would evaluate them.  Synchronous. */
+int tf_read_field(tf_ctx* ctx, int inst, int field, double* host);
+
+/* Advance every instance by n >= 0 coupled lattice steps.  Asynchronous on
+ * the context stream; launch errors are returned, execution errors are
+ * reported by the next synchronising call. */
+int tf_step(tf_ctx* ctx, int64_t n);
+
+/* Wait for the context stream; returns TF_ERR_CUDA on an execution error. */
+int tf_sync(tf_ctx* ctx);
+
+/* Number of lattice steps taken since the last init / load. */
+int64_t tf_step_count(const tf_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched so far (all entry points). */
+int64_t tf_kernel_launches(const tf_ctx* ctx);
+
+/* FP64 global sums of one instance (8 doubles, synchronous):
+ *   [0] sum phi, [1] sum rho1, [2] sum rho2,
+ *   [3] sum (m1 + m2)_x, [4] sum (m1 + m2)_y   (bare momenta sum_i c_i f_i),
+ *   [5] sum (G1 + G2)_x, [6] sum (G1 + G2)_y   (non-drag forces of this state),
+ *   [7] number of non-finite stored values.
+ * Guo forcing gives sum m(n+1) - sum m(n) = sum G(n) exactly.
+ * Returns TF_ERR_NONFINITE (after filling out) when [7] > 0. */
+#define TF_NCONS 8
+int tf_conserved(tf_ctx* ctx, int inst, double out[TF_NCONS]);
+
+/* Spectral observables of one instance (Sec. IV).  Transforms are
+ * g_hat(k) = (1/(nx ny)) sum_x g(x) exp(-i k.x), k = 2 pi (n_x/nx, n_y/ny);
+ * shell m collects modes with |k|/k0 in [m - 1/2, m + 1/2), k0 = 2 pi /
+ * min(nx, ny), m = 0 .. tf_n_shell()-1 (corner modes beyond are dropped).
+ * All arithmetic in FP64.  Synchronous. */
+int tf_n_shell(const tf_ctx* ctx);
+/* out[m] = number of modes in shell m. */
+int tf_shell_counts(tf_ctx* ctx, double* out, int n_shell);
+/* S[m] = shell sum of |phi_hat|^2 of phi - <phi> (Eq. 24; Phi(k) of Eq. 27 is S/2). */
+int tf_structure_factor(tf_ctx* ctx, int inst, double* S, int n_shell);
+/* L = sum_{m>=1} Phi_m / sum_{m>=1} k_m Phi_m, k_m = m k0 (Eq. 27). */
+int tf_length_scale(tf_ctx* ctx, int inst, double* L);
+/* E[m] = 1/2 shell sum of |u_c_hat|^2 (Eq. 22), u_c = phi u1 + (1-phi) u2;
+ * *E_total = 1/2 sum over all modes = <|u_c|^2>/2 (Eq. 29). */
+int tf_energy_spectrum(tf_ctx* ctx, int inst, double* E, int n_shell, double* E_total);
+
+/* Inter-phase differences and RMS values (Sec. IV, Fig. 8), 6 doubles:
+ * [0] rms|u1 - u2|, [1] rms(w1 - w2), [2] rms|u1|, [3] rms|u_c|,
+ * [4] rms w1, [5] rms w_c; w = d_x u_y - d_y u_x (central differences). */
+int tf_phase_difference(tf_ctx* ctx, int inst, double out[6]);
+
+/* Standard deviation Delta of phi (Sec. IV, Fig. 3) and its mean. */
+int tf_phi_stats(tf_ctx* ctx, int inst, double* mean, double* stddev);
+
+/* Raw state (populations, phi, Q of every instance) as one byte blob in
+ * the device storage layout.  tf_state_bytes() gives its size. */
+size_t tf_state_bytes(const tf_ctx* ctx);
+
+/* End-to-end entry point with HOST buffers: copy the raw state from
+ * `h_in` (ideally pinned; NULL keeps the device state), advance n steps,
+ * copy the raw state to `h_out` (NULL skips), and synchronise. */
+int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out);
+
+/* Checkpoint / resume of the whole context (header + raw state), bitwise. */
+int tf_save(tf_ctx* ctx, const char* path);
+int tf_load(tf_ctx* ctx, const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TWOFLUID_H */

@@ -445,19 +445,26 @@ def conserved(state: State, p: Params):
 # Observables (Sec. IV).
 # --------------------------------------------------------------------------
 def shell_geometry(nx: int, ny: int):
-    """Wavevector magnitude and shell index of every FFT mode.
+    """Shell index of every FFT mode (Sec. IV, Eq. 27 shells k - 1/2 <= k' < k + 1/2).
 
-    k = 2 pi (n_x/nx, n_y/ny) with signed mode numbers; shells have width
-    k0 = 2 pi / min(nx, ny) and shell m holds |k|/k0 in [m - 1/2, m + 1/2).
-    Shells m = 0 .. min(nx, ny)/2 are kept; corner modes beyond are dropped.
+    Mode (n_x, n_y) (signed integers, numpy fftfreq order) has wavevector
+    k = 2 pi (n_x/nx, n_y/ny).  Shells have width k0 = 2 pi / m, m = min(nx, ny):
+    with r = |k|/k0 = sqrt((n_x m/nx)^2 + (n_y m/ny)^2) the mode lies in shell
+    floor(r + 1/2).  r is formed from the integer mode numbers with separately
+    rounded operations so that modes exactly on a shell boundary are assigned
+    reproducibly.  Shells 0 .. m/2 are kept; corner modes beyond are dropped.
+    Returns (r, shell, n_shell, k0).
     """
-    kx = 2.0 * np.pi * np.fft.fftfreq(nx)
-    ky = 2.0 * np.pi * np.fft.fftfreq(ny)
-    kk = np.sqrt(kx[None, :] ** 2 + ky[:, None] ** 2)
-    k0 = 2.0 * np.pi / min(nx, ny)
-    shell = np.floor(kk / k0 + 0.5).astype(np.int64)
-    n_shell = min(nx, ny) // 2 + 1
-    return kk, shell, n_shell, k0
+    m = min(nx, ny)
+    sx = np.rint(np.fft.fftfreq(nx) * nx)
+    sy = np.rint(np.fft.fftfreq(ny) * ny)
+    tx = sx * m / nx
+    ty = sy * m / ny
+    r = np.sqrt(tx[None, :] * tx[None, :] + ty[:, None] * ty[:, None])
+    shell = np.floor(r + 0.5).astype(np.int64)
+    n_shell = m // 2 + 1
+    k0 = 2.0 * np.pi / m
+    return r, shell, n_shell, k0
 
 
 def fourier(g):

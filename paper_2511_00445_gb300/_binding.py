@@ -35,7 +35,7 @@ NCONS = 8
 EXPORTS = [
     "tf_workspace_bytes", "tf_create", "tf_destroy", "tf_last_error", "tf_init_fields",
     "tf_write_field", "tf_set_equilibrium", "tf_read_field", "tf_step", "tf_sync",
-    "tf_step_count", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
+    "tf_step_count", "tf_kernel_launches", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
     "tf_length_scale", "tf_energy_spectrum", "tf_phase_difference", "tf_phi_stats",
     "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load",
 ]
@@ -122,6 +122,7 @@ def load_library() -> ctypes.CDLL:
         "tf_step": (i, [vp, i64]),
         "tf_sync": (i, [vp]),
         "tf_step_count": (i64, [vp]),
+        "tf_kernel_launches": (i64, [vp]),
         "tf_conserved": (i, [vp, i, dp]),
         "tf_n_shell": (i, [vp]),
         "tf_shell_counts": (i, [vp, dp, i]),
@@ -227,6 +228,9 @@ class TwoFluid:
 
     def step_count(self) -> int:
         return int(self.lib.tf_step_count(self.ctx))
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.tf_kernel_launches(self.ctx))
 
     # -- observables
     def conserved(self, inst: int, check: bool = True) -> np.ndarray:

@@ -1,0 +1,458 @@
+// C ABI of libtwofluid (declared in include/twofluid.h): argument checks,
+// workspace carving, host <-> device staging and checkpoint I/O.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tf_internal.h"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxDim = 32768;
+constexpr int kMaxFFT = 8192;
+constexpr uint64_t kMagic = 0x31444C4655464F57ull;  // checkpoint tag
+constexpr int kVersion = 1;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+int fail(tf_ctx* ctx, int code, const char* msg) {
+    if (ctx) ctx->last_error = msg;
+    return code;
+}
+
+int fail_cuda(tf_ctx* ctx, const char* where, cudaError_t e) {
+    if (ctx) {
+        ctx->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return TF_ERR_CUDA;
+}
+
+#define TF_CK(ctx, call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, #call, e_); \
+    } while (0)
+
+const char* check_params(const tf_params& p) {
+    if (p.nx < 1 || p.ny < 1 || p.nx > kMaxDim || p.ny > kMaxDim) return "nx, ny must be in [1, 32768]";
+    if (p.n_sub < 1 || p.n_sub > 64) return "n_sub must be in [1, 64]";
+    if (p.storage != TF_STORE_F32) return "unsupported storage mode";
+    if (!(p.tau1 > 0.5) || !(p.tau2 > 0.5)) return "tau1, tau2 must exceed 1/2";
+    if (!(p.rho1 > 0) || !(p.rho2 > 0)) return "rho1, rho2 must be positive";
+    const double v[] = {p.gamma, p.zeta, p.lambda, p.K, p.Gamma_Q, p.A_Q,
+                        p.C_Q,   p.M,    p.A_ch,   p.kappa, p.phi_ref};
+    for (double x : v)
+        if (!std::isfinite(x)) return "parameters must be finite";
+    return nullptr;
+}
+
+bool valid_inst(const tf_ctx* ctx, int inst) { return inst >= 0 && inst < ctx->batch; }
+
+bool is_pop_field(int field) {
+    return (field >= TF_FIELD_F1 && field < TF_FIELD_F1 + 9) ||
+           (field >= TF_FIELD_F2 && field < TF_FIELD_F2 + 9);
+}
+
+int red_blocks_for(long long N) {
+    long long b = (N + 2047) / 2048;
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+int shell_blocks_for(long long N) {
+    long long b = (N + 4095) / 4096;
+    if (b < 1) b = 1;
+    if (b > 296) b = 296;
+    return (int)b;
+}
+
+}  // namespace
+
+DevParams tf_make_devparams(const tf_params& p) {
+    DevParams d{};
+    d.omega1 = (float)(1.0 / p.tau1);
+    d.omega2 = (float)(1.0 / p.tau2);
+    d.guo1 = (float)(1.0 - 0.5 / p.tau1);
+    d.guo2 = (float)(1.0 - 0.5 / p.tau2);
+    d.gamma = (float)p.gamma;
+    d.zeta = (float)p.zeta;
+    d.lam = (float)p.lambda;
+    d.K = (float)p.K;
+    d.GammaQ = (float)p.Gamma_Q;
+    d.A_Q = (float)p.A_Q;
+    d.C_Q = (float)p.C_Q;
+    d.M = (float)p.M;
+    d.kappa = (float)p.kappa;
+    d.dt_fd = (float)(1.0 / p.n_sub);
+    d.phi_ref = (float)p.phi_ref;
+    d.rho1 = (float)p.rho1;
+    d.rho2 = (float)p.rho2;
+    // A_ch f'(c + d) with f'(x) = 2x - 6x^2 + 4x^3, Taylor-expanded about c
+    // (exact: f' is a cubic).
+    const double c = (double)d.phi_ref;
+    d.mu0 = (float)(p.A_ch * (2 * c - 6 * c * c + 4 * c * c * c));
+    d.mu1 = (float)(p.A_ch * (2 - 12 * c + 12 * c * c));
+    d.mu2 = (float)(p.A_ch * (-6 + 12 * c));
+    d.mu3 = (float)(p.A_ch * 4);
+    return d;
+}
+
+size_t tf_layout(const tf_params& p0, int batch, DevBuffers* d, char* base) {
+    const size_t N = (size_t)p0.nx * (size_t)p0.ny, B = (size_t)batch;
+    const int n_shell = (p0.nx < p0.ny ? p0.nx : p0.ny) / 2 + 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off = align_up(off + bytes);
+        return p;
+    };
+    DevBuffers t{};
+    for (int k = 0; k < 2; ++k) t.f[k] = (float*)take(18 * B * N * sizeof(float));
+    for (int k = 0; k < 2; ++k) t.phi[k] = (float*)take(B * N * sizeof(float));
+    for (int k = 0; k < 2; ++k) t.Q[k] = (float*)take(2 * B * N * sizeof(float));
+    for (int k = 0; k < 2; ++k) t.u[k] = (float*)take(4 * B * N * sizeof(float));
+    t.mu = (float*)take(B * N * sizeof(float));
+    t.tau = (float*)take(4 * B * N * sizeof(float));
+    t.macro = (float*)take(8 * B * N * sizeof(float));
+    t.prm = (DevParams*)take(B * sizeof(DevParams));
+    t.red_part = (double*)take((size_t)red_blocks_for((long long)N) * 8 * sizeof(double));
+    t.red_out = (double*)take(16 * sizeof(double));
+    for (int k = 0; k < 2; ++k) t.cbuf[k] = (double2*)take(N * sizeof(double2));
+    t.shell_part =
+        (double*)take((size_t)shell_blocks_for((long long)N) * (n_shell + 1) * sizeof(double));
+    t.shell_out = (double*)take((size_t)(n_shell + 1) * sizeof(double));
+    t.stage = (double*)take(N * sizeof(double));
+    t.flags = (int*)take(64 * sizeof(int));
+    if (d) *d = t;
+    return off;
+}
+
+extern "C" {
+
+size_t tf_workspace_bytes(const tf_params* params, int batch) {
+    if (!params || batch < 1) return 0;
+    for (int b = 0; b < batch; ++b) {
+        if (check_params(params[b])) return 0;
+        if (params[b].nx != params[0].nx || params[b].ny != params[0].ny ||
+            params[b].n_sub != params[0].n_sub || params[b].storage != params[0].storage)
+            return 0;
+    }
+    return tf_layout(params[0], batch, nullptr, nullptr);
+}
+
+int tf_create(const tf_params* params, int batch, void* d_workspace, size_t workspace_bytes,
+              void* stream, tf_ctx** out) {
+    if (!out) return TF_ERR_ARG;
+    *out = nullptr;
+    if (!params || batch < 1) return TF_ERR_ARG;
+    for (int b = 0; b < batch; ++b)
+        if (check_params(params[b])) return TF_ERR_ARG;
+    const size_t need = tf_workspace_bytes(params, batch);
+    if (need == 0) return TF_ERR_ARG;
+    if (!d_workspace || ((uintptr_t)d_workspace % kAlign) != 0 || workspace_bytes < need)
+        return TF_ERR_WORKSPACE;
+    tf_ctx* ctx = new (std::nothrow) tf_ctx();
+    if (!ctx) return TF_ERR_ARG;
+    ctx->nx = params[0].nx;
+    ctx->ny = params[0].ny;
+    ctx->batch = batch;
+    ctx->n_sub = params[0].n_sub;
+    ctx->storage = params[0].storage;
+    ctx->N = (long long)ctx->nx * ctx->ny;
+    ctx->params.assign(params, params + batch);
+    for (int b = 0; b < batch; ++b) ctx->dparams.push_back(tf_make_devparams(params[b]));
+    ctx->stream = (cudaStream_t)stream;
+    ctx->ws = (char*)d_workspace;
+    ctx->ws_bytes = workspace_bytes;
+    tf_layout(params[0], batch, &ctx->d, ctx->ws);
+    ctx->n_shell = (ctx->nx < ctx->ny ? ctx->nx : ctx->ny) / 2 + 1;
+    ctx->red_blocks = red_blocks_for(ctx->N);
+    ctx->shell_blocks = shell_blocks_for(ctx->N);
+    cudaError_t e = tf_configure_observe_kernels();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->d.prm, ctx->dparams.data(), batch * sizeof(DevParams),
+                            cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = tf_launch_zero_state(ctx);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return TF_ERR_CUDA;
+    }
+    *out = ctx;
+    return TF_OK;
+}
+
+int tf_destroy(tf_ctx* ctx) {
+    if (!ctx) return TF_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return e == cudaSuccess ? TF_OK : TF_ERR_CUDA;
+}
+
+const char* tf_last_error(const tf_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->last_error.c_str();
+}
+
+int tf_init_fields(tf_ctx* ctx, int inst, uint64_t seed, double phi0, double dphi, double S0) {
+    if (!ctx) return TF_ERR_ARG;
+    if (inst != -1 && !valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
+    if (!std::isfinite(phi0) || !std::isfinite(dphi) || !std::isfinite(S0))
+        return fail(ctx, TF_ERR_ARG, "non-finite initial-condition parameter");
+    TF_CK(ctx, tf_launch_init(ctx, inst, seed, phi0, dphi, S0));
+    ctx->steps = 0;
+    return TF_OK;
+}
+
+int tf_write_field(tf_ctx* ctx, int inst, int field, const double* host) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || !host) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    if (!(field == TF_FIELD_PHI || field == TF_FIELD_QXX || field == TF_FIELD_QXY ||
+          is_pop_field(field)))
+        return fail(ctx, TF_ERR_ARG, "field is not writable");
+    TF_CK(ctx, cudaMemcpyAsync(ctx->d.stage, host, ctx->N * sizeof(double),
+                               cudaMemcpyHostToDevice, ctx->stream));
+    TF_CK(ctx, tf_launch_write_field(ctx, inst, field, ctx->d.stage));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
+int tf_set_equilibrium(tf_ctx* ctx, int inst, const double* u1, const double* u2) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
+    double* d1 = nullptr;
+    double* d2 = nullptr;
+    if (u1) {
+        d1 = (double*)ctx->d.cbuf[0];
+        TF_CK(ctx, cudaMemcpyAsync(d1, u1, 2 * ctx->N * sizeof(double), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    }
+    if (u2) {
+        d2 = (double*)ctx->d.cbuf[1];
+        TF_CK(ctx, cudaMemcpyAsync(d2, u2, 2 * ctx->N * sizeof(double), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    }
+    TF_CK(ctx, tf_launch_set_equilibrium(ctx, inst, d1, d2));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
+int tf_read_field(tf_ctx* ctx, int inst, int field, double* host) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || !host) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    if (!((field >= TF_FIELD_PHI && field <= TF_FIELD_MU) || is_pop_field(field)))
+        return fail(ctx, TF_ERR_ARG, "unknown field id");
+    TF_CK(ctx, tf_launch_read_field(ctx, inst, field, ctx->d.stage));
+    TF_CK(ctx, cudaMemcpyAsync(host, ctx->d.stage, ctx->N * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
+int tf_step(tf_ctx* ctx, int64_t n) {
+    if (!ctx) return TF_ERR_ARG;
+    if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
+    if (n == 0) return TF_OK;
+    TF_CK(ctx, tf_launch_steps(ctx, n));
+    return TF_OK;
+}
+
+int tf_sync(tf_ctx* ctx) {
+    if (!ctx) return TF_ERR_ARG;
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    TF_CK(ctx, cudaGetLastError());
+    return TF_OK;
+}
+
+int64_t tf_step_count(const tf_ctx* ctx) { return ctx ? ctx->steps : -1; }
+
+int64_t tf_kernel_launches(const tf_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int tf_conserved(tf_ctx* ctx, int inst, double out[TF_NCONS]) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    TF_CK(ctx, tf_launch_conserved(ctx, inst, ctx->d.red_out));
+    TF_CK(ctx, cudaMemcpyAsync(out, ctx->d.red_out, TF_NCONS * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const tf_params& p = ctx->params[inst];
+    out[0] += (double)(float)p.phi_ref * (double)ctx->N;   // stored deviations -> phi
+    out[1] += (double)ctx->N;                                // deviations -> rho
+    out[2] += (double)ctx->N;
+    if (out[7] > 0) return fail(ctx, TF_ERR_NONFINITE, "non-finite values in the state");
+    return TF_OK;
+}
+
+int tf_n_shell(const tf_ctx* ctx) { return ctx ? ctx->n_shell : 0; }
+
+static int spectrum_common(tf_ctx* ctx, int inst, int which, double* out, int n_shell,
+                           double* total) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
+    if (out && n_shell != ctx->n_shell) return fail(ctx, TF_ERR_ARG, "n_shell mismatch");
+    if (ctx->nx > kMaxFFT || ctx->ny > kMaxFFT)
+        return fail(ctx, TF_ERR_ARG, "spectra support nx, ny <= 8192");
+    TF_CK(ctx, tf_launch_spectrum(ctx, inst, which));
+    std::vector<double> buf(ctx->n_shell + 1);
+    TF_CK(ctx, cudaMemcpyAsync(buf.data(), ctx->d.shell_out, buf.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (out) std::memcpy(out, buf.data(), ctx->n_shell * sizeof(double));
+    if (total) *total = buf[ctx->n_shell];
+    return TF_OK;
+}
+
+int tf_shell_counts(tf_ctx* ctx, double* out, int n_shell) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!out || n_shell != ctx->n_shell) return fail(ctx, TF_ERR_ARG, "n_shell mismatch");
+    TF_CK(ctx, tf_launch_shell_counts(ctx));
+    TF_CK(ctx, cudaMemcpyAsync(out, ctx->d.shell_out, n_shell * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
+int tf_structure_factor(tf_ctx* ctx, int inst, double* S, int n_shell) {
+    if (!S) return ctx ? fail(ctx, TF_ERR_ARG, "null array") : TF_ERR_ARG;
+    return spectrum_common(ctx, inst, 0, S, n_shell, nullptr);
+}
+
+int tf_length_scale(tf_ctx* ctx, int inst, double* L) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!L) return fail(ctx, TF_ERR_ARG, "null pointer");
+    std::vector<double> S(ctx->n_shell);
+    int rc = spectrum_common(ctx, inst, 0, S.data(), ctx->n_shell, nullptr);
+    if (rc != TF_OK) return rc;
+    const double k0 = 2.0 * M_PI / (double)(ctx->nx < ctx->ny ? ctx->nx : ctx->ny);
+    double num = 0.0, den = 0.0;
+    for (int m = 1; m < ctx->n_shell; ++m) {
+        num += 0.5 * S[m];
+        den += (double)m * k0 * 0.5 * S[m];
+    }
+    *L = den > 0.0 ? num / den : 0.0;
+    return TF_OK;
+}
+
+int tf_energy_spectrum(tf_ctx* ctx, int inst, double* E, int n_shell, double* E_total) {
+    if (!E && !E_total) return ctx ? fail(ctx, TF_ERR_ARG, "null arrays") : TF_ERR_ARG;
+    return spectrum_common(ctx, inst, 1, E, n_shell, E_total);
+}
+
+int tf_phase_difference(tf_ctx* ctx, int inst, double out[6]) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    TF_CK(ctx, tf_launch_phase_difference(ctx, inst, ctx->d.red_out));
+    double s[6];
+    TF_CK(ctx, cudaMemcpyAsync(s, ctx->d.red_out, 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 6; ++k) out[k] = std::sqrt(s[k] / (double)ctx->N);
+    return TF_OK;
+}
+
+int tf_phi_stats(tf_ctx* ctx, int inst, double* mean, double* stddev) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
+    TF_CK(ctx, tf_launch_phi_stats(ctx, inst, ctx->d.red_out));
+    double s[2];
+    TF_CK(ctx, cudaMemcpyAsync(s, ctx->d.red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const double md = s[0] / (double)ctx->N;   // mean of the stored deviation
+    const double var = s[1] / (double)ctx->N - md * md;
+    if (mean) *mean = (double)(float)ctx->params[inst].phi_ref + md;
+    if (stddev) *stddev = std::sqrt(var > 0 ? var : 0.0);
+    return TF_OK;
+}
+
+size_t tf_state_bytes(const tf_ctx* ctx) {
+    if (!ctx) return 0;
+    const size_t N = (size_t)ctx->N, B = (size_t)ctx->batch;
+    return (18 + 1 + 2) * B * N * sizeof(float);
+}
+
+// Raw state blob: populations [B][18][N], phi [B][N], Q [B][2][N] (FP32).
+static int copy_state(tf_ctx* ctx, void* host, bool to_host) {
+    const size_t N = (size_t)ctx->N, B = (size_t)ctx->batch;
+    char* h = (char*)host;
+    const size_t sf = 18 * B * N * sizeof(float), sp = B * N * sizeof(float),
+                 sq = 2 * B * N * sizeof(float);
+    void* dev[3] = {ctx->d.f[ctx->fcur], ctx->d.phi[ctx->pcur], ctx->d.Q[ctx->pcur]};
+    const size_t sz[3] = {sf, sp, sq};
+    size_t off = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (to_host) {
+            TF_CK(ctx, cudaMemcpyAsync(h + off, dev[k], sz[k], cudaMemcpyDeviceToHost, ctx->stream));
+        } else {
+            TF_CK(ctx, cudaMemcpyAsync(dev[k], h + off, sz[k], cudaMemcpyHostToDevice, ctx->stream));
+        }
+        off += sz[k];
+    }
+    return TF_OK;
+}
+
+int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
+    if (!ctx) return TF_ERR_ARG;
+    if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
+    int rc;
+    if (h_in && (rc = copy_state(ctx, const_cast<void*>(h_in), false)) != TF_OK) return rc;
+    if (n > 0) TF_CK(ctx, tf_launch_steps(ctx, n));
+    if (h_out && (rc = copy_state(ctx, h_out, true)) != TF_OK) return rc;
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
+struct CkptHeader {
+    uint64_t magic;
+    int32_t version, nx, ny, batch, n_sub, storage;
+    int64_t steps;
+    uint64_t state_bytes;
+};
+
+int tf_save(tf_ctx* ctx, const char* path) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!path) return fail(ctx, TF_ERR_ARG, "null path");
+    std::vector<char> buf(tf_state_bytes(ctx));
+    int rc = copy_state(ctx, buf.data(), true);
+    if (rc != TF_OK) return rc;
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    CkptHeader h{kMagic, kVersion, ctx->nx, ctx->ny, ctx->batch, ctx->n_sub, ctx->storage,
+                 ctx->steps, (uint64_t)buf.size()};
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(ctx, TF_ERR_IO, "cannot open checkpoint for writing");
+    bool ok = std::fwrite(&h, sizeof h, 1, fp) == 1 &&
+              std::fwrite(ctx->params.data(), sizeof(tf_params), ctx->batch, fp) ==
+                  (size_t)ctx->batch &&
+              std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? TF_OK : fail(ctx, TF_ERR_IO, "short write to checkpoint");
+}
+
+int tf_load(tf_ctx* ctx, const char* path) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!path) return fail(ctx, TF_ERR_ARG, "null path");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(ctx, TF_ERR_IO, "cannot open checkpoint for reading");
+    CkptHeader h{};
+    std::vector<tf_params> prm(ctx->batch);
+    std::vector<char> buf(tf_state_bytes(ctx));
+    bool ok = std::fread(&h, sizeof h, 1, fp) == 1;
+    ok = ok && h.magic == kMagic && h.version == kVersion && h.nx == ctx->nx && h.ny == ctx->ny &&
+         h.batch == ctx->batch && h.n_sub == ctx->n_sub && h.storage == ctx->storage &&
+         h.state_bytes == buf.size();
+    ok = ok && std::fread(prm.data(), sizeof(tf_params), ctx->batch, fp) == (size_t)ctx->batch;
+    ok = ok && std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    std::fclose(fp);
+    if (!ok) return fail(ctx, TF_ERR_IO, "checkpoint header or size does not match this context");
+    int rc = copy_state(ctx, buf.data(), false);
+    if (rc != TF_OK) return rc;
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->steps = h.steps;
+    return TF_OK;
+}
+
+}  // extern "C"

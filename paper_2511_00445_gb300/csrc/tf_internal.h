@@ -1,0 +1,113 @@
+// Internal declarations shared by the CUDA translation units of libtwofluid.
+// Not part of the public ABI (see include/twofluid.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "twofluid.h"
+
+// ---------------------------------------------------------------------------
+// D2Q9 velocity set (Sec. III): rest, axes counter-clockwise from +x, then
+// diagonals counter-clockwise from (+1, +1).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int d2q9_cx(int i) {
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int d2q9_cy(int i) {
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr float d2q9_w(int i) {
+    return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// Exact weights in double: the stored FP32 deviations are f_i - w_i with these.
+__host__ __device__ constexpr double d2q9_wd(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// Per-instance parameters in the form the kernels use (FP32, precomputed).
+// mu(phi_ref + d) = A_ch f'(phi_ref + d) - kappa lap(d) with the cubic
+// A_ch f'(c + d) = mu0 + mu1 d + mu2 d^2 + mu3 d^3 expanded about c.
+struct DevParams {
+    float omega1, omega2;   // 1 / tau_k
+    float guo1, guo2;       // 1 - 1 / (2 tau_k)
+    float gamma, zeta, lam, K;
+    float GammaQ, A_Q, C_Q, M;
+    float kappa, dt_fd, phi_ref, rho1;
+    float mu0, mu1, mu2, mu3;
+    float rho2, pad0, pad1, pad2;
+};
+
+// Device buffers carved out of the caller's workspace.
+struct DevBuffers {
+    float* f[2];       // populations [B][18][N] (pull layout: post-collision of the previous step)
+    float* phi[2];     // phi - phi_ref  [B][N]
+    float* Q[2];       // Q_xx, Q_xy     [B][2][N]
+    float* u[2];       // u1x, u1y, u2x, u2y [B][4][N]
+    float* mu;         // scratch: chemical potential [B][N]
+    float* tau;        // scratch: fluid-1 stress (elastic + active) xx, xy, yx, yy [B][4][N]
+    float* macro;      // scratch: u1x u1y u2x u2y rho1 rho2 (G1+G2)x (G1+G2)y [B][8][N]
+    DevParams* prm;    // [B]
+    double* red_part;  // reduction partials [B][red_blocks][8]
+    double* red_out;   // reduction results [B][8]
+    double2* cbuf[2];  // complex FFT buffers, N each
+    double* shell_part;// shell histogram partials [shell_blocks][n_shell]
+    double* shell_out; // [n_shell]
+    double* stage;     // FP64 staging plane [N] (and small results)
+    int* flags;        // device status words
+};
+
+struct tf_ctx {
+    int nx = 0, ny = 0, batch = 0, n_sub = 5, storage = TF_STORE_F32;
+    long long N = 0;                 // nx * ny
+    std::vector<tf_params> params;
+    std::vector<DevParams> dparams;
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    DevBuffers d{};
+    int fcur = 0;                    // population buffer holding the current state
+    int pcur = 0;                    // phi/Q buffer holding the current state
+    int64_t steps = 0;
+    int64_t launches = 0;            // kernels launched by this context
+    int n_shell = 0;
+    int red_blocks = 0;
+    int shell_blocks = 0;
+    std::string last_error;
+};
+
+// Workspace carving (tf_api.cu).
+size_t tf_layout(const tf_params& p0, int batch, DevBuffers* d, char* base);
+
+// Precompute the kernel parameter block of one instance.
+DevParams tf_make_devparams(const tf_params& p);
+
+// ---- step kernels (tf_step.cu) -------------------------------------------
+// Advance the whole batch by n steps on ctx->stream.
+cudaError_t tf_launch_steps(tf_ctx* ctx, int64_t n);
+// Evaluate mu, the fluid-1 stress, the Guo velocities, densities and the
+// non-drag force sum of the current state into d.mu, d.tau and macro_out
+// ([B][8][N]: u1x u1y u2x u2y rho1 rho2 (G1+G2)x (G1+G2)y).
+cudaError_t tf_launch_macro(tf_ctx* ctx, float* macro_out);
+
+// ---- field / observable kernels (tf_observe.cu) ---------------------------
+cudaError_t tf_launch_init(tf_ctx* ctx, int inst, uint64_t seed, double phi0,
+                           double dphi, double S0);
+cudaError_t tf_launch_zero_state(tf_ctx* ctx);
+cudaError_t tf_launch_write_field(tf_ctx* ctx, int inst, int field, const double* dsrc);
+cudaError_t tf_launch_set_equilibrium(tf_ctx* ctx, int inst, const double* du1,
+                                      const double* du2);
+cudaError_t tf_launch_read_field(tf_ctx* ctx, int inst, int field, double* ddst);
+cudaError_t tf_launch_conserved(tf_ctx* ctx, int inst, double* dout8);
+cudaError_t tf_launch_phase_difference(tf_ctx* ctx, int inst, double* dout6);
+cudaError_t tf_launch_phi_stats(tf_ctx* ctx, int inst, double* dout2);
+// which: 0 = structure factor of phi - <phi>, 1 = kinetic-energy spectrum of u_c.
+// Writes n_shell shell sums to d.shell_out[0..n_shell-1] and the all-mode
+// total to d.shell_out[n_shell].
+cudaError_t tf_launch_spectrum(tf_ctx* ctx, int inst, int which);
+cudaError_t tf_launch_shell_counts(tf_ctx* ctx);
+// One-time kernel attributes (large dynamic shared memory).
+cudaError_t tf_configure_observe_kernels();

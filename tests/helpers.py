@@ -1,0 +1,50 @@
+"""Shared test helpers: GPU <-> oracle state transfer and the parity metric."""
+import numpy as np
+
+from oracle import twofluid as O
+from paper_2511_00445_gb300 import _binding as B
+
+# Parity bar after 200 steps in FP32: max |X_gpu - X_oracle| normalised by the
+# oracle field's own spread max |X - <X>| (pointwise relative error of fields
+# that sit near a constant, phi ~ 1/2, u ~ 0, is ill-posed).
+TOL_200 = 1e-5
+
+
+def oracle_params(sp: B.SolverParams) -> O.Params:
+    return O.Params(nx=sp.nx, ny=sp.ny, tau1=sp.tau1, tau2=sp.tau2, rho1=sp.rho1, rho2=sp.rho2,
+                    gamma=sp.gamma, zeta=sp.zeta, lam=sp.lam, K=sp.K, Gamma_Q=sp.Gamma_Q,
+                    A_Q=sp.A_Q, C_Q=sp.C_Q, M=sp.M, A_ch=sp.A_ch, kappa=sp.kappa, n_sub=sp.n_sub)
+
+
+def read_state(tf: B.TwoFluid, inst: int) -> O.State:
+    """The GPU's current state as an oracle State (exact FP32 values in FP64)."""
+    f1 = np.stack([tf.read_field(inst, B.FIELD_F1 + i) for i in range(9)])
+    f2 = np.stack([tf.read_field(inst, B.FIELD_F2 + i) for i in range(9)])
+    return O.State(f1, f2, tf.read_field(inst, B.FIELD_PHI), tf.read_field(inst, B.FIELD_QXX),
+                   tf.read_field(inst, B.FIELD_QXY))
+
+
+def read_velocities(tf: B.TwoFluid, inst: int):
+    u1 = np.stack([tf.read_field(inst, B.FIELD_U1X), tf.read_field(inst, B.FIELD_U1Y)])
+    u2 = np.stack([tf.read_field(inst, B.FIELD_U2X), tf.read_field(inst, B.FIELD_U2Y)])
+    return u1, u2
+
+
+def rel_err(got: np.ndarray, want: np.ndarray) -> float:
+    spread = np.abs(want - want.mean()).max()
+    diff = np.abs(got - want).max()
+    if spread == 0.0:
+        return 0.0 if diff == 0.0 else float("inf")
+    return float(diff / spread)
+
+
+def field_errors(tf: B.TwoFluid, inst: int, ref: O.State, p: O.Params) -> dict:
+    mc = O.macro(ref, p)
+    u1, u2 = read_velocities(tf, inst)
+    return {
+        "phi": rel_err(tf.read_field(inst, B.FIELD_PHI), ref.phi),
+        "Qxx": rel_err(tf.read_field(inst, B.FIELD_QXX), ref.Qxx),
+        "Qxy": rel_err(tf.read_field(inst, B.FIELD_QXY), ref.Qxy),
+        "u1": max(rel_err(u1[0], mc["u1"][0]), rel_err(u1[1], mc["u1"][1])),
+        "u2": max(rel_err(u2[0], mc["u2"][0]), rel_err(u2[1], mc["u2"][1])),
+    }
