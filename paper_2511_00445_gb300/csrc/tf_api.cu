@@ -173,6 +173,7 @@ int tf_create(const tf_params* params, int batch, void* d_workspace, size_t work
     ctx->red_blocks = red_blocks_for(ctx->N);
     ctx->shell_blocks = shell_blocks_for(ctx->N);
     cudaError_t e = tf_configure_observe_kernels();
+    if (e == cudaSuccess) e = tf_configure_fused_kernels();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->d.prm, ctx->dparams.data(), batch * sizeof(DevParams),
                             cudaMemcpyHostToDevice, ctx->stream);
@@ -203,6 +204,8 @@ int tf_init_fields(tf_ctx* ctx, int inst, uint64_t seed, double phi0, double dph
     if (inst != -1 && !valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
     if (!std::isfinite(phi0) || !std::isfinite(dphi) || !std::isfinite(S0))
         return fail(ctx, TF_ERR_ARG, "non-finite initial-condition parameter");
+    if (inst != -1) TF_CK(ctx, tf_launch_flush(ctx));  // other instances keep their state
+    ctx->fd_pending = false;
     TF_CK(ctx, tf_launch_init(ctx, inst, seed, phi0, dphi, S0));
     ctx->steps = 0;
     return TF_OK;
@@ -214,6 +217,7 @@ int tf_write_field(tf_ctx* ctx, int inst, int field, const double* host) {
     if (!(field == TF_FIELD_PHI || field == TF_FIELD_QXX || field == TF_FIELD_QXY ||
           is_pop_field(field)))
         return fail(ctx, TF_ERR_ARG, "field is not writable");
+    TF_CK(ctx, tf_launch_flush(ctx));
     TF_CK(ctx, cudaMemcpyAsync(ctx->d.stage, host, ctx->N * sizeof(double),
                                cudaMemcpyHostToDevice, ctx->stream));
     TF_CK(ctx, tf_launch_write_field(ctx, inst, field, ctx->d.stage));
@@ -224,6 +228,7 @@ int tf_write_field(tf_ctx* ctx, int inst, int field, const double* host) {
 int tf_set_equilibrium(tf_ctx* ctx, int inst, const double* u1, const double* u2) {
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
+    TF_CK(ctx, tf_launch_flush(ctx));
     double* d1 = nullptr;
     double* d2 = nullptr;
     if (u1) {
@@ -246,6 +251,7 @@ int tf_read_field(tf_ctx* ctx, int inst, int field, double* host) {
     if (!valid_inst(ctx, inst) || !host) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
     if (!((field >= TF_FIELD_PHI && field <= TF_FIELD_MU) || is_pop_field(field)))
         return fail(ctx, TF_ERR_ARG, "unknown field id");
+    TF_CK(ctx, tf_launch_flush(ctx));
     TF_CK(ctx, tf_launch_read_field(ctx, inst, field, ctx->d.stage));
     TF_CK(ctx, cudaMemcpyAsync(host, ctx->d.stage, ctx->N * sizeof(double),
                                cudaMemcpyDeviceToHost, ctx->stream));
@@ -275,6 +281,7 @@ int64_t tf_kernel_launches(const tf_ctx* ctx) { return ctx ? ctx->launches : -1;
 int tf_conserved(tf_ctx* ctx, int inst, double out[TF_NCONS]) {
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    TF_CK(ctx, tf_launch_flush(ctx));
     TF_CK(ctx, tf_launch_conserved(ctx, inst, ctx->d.red_out));
     TF_CK(ctx, cudaMemcpyAsync(out, ctx->d.red_out, TF_NCONS * sizeof(double),
                                cudaMemcpyDeviceToHost, ctx->stream));
@@ -296,6 +303,7 @@ static int spectrum_common(tf_ctx* ctx, int inst, int which, double* out, int n_
     if (out && n_shell != ctx->n_shell) return fail(ctx, TF_ERR_ARG, "n_shell mismatch");
     if (ctx->nx > kMaxFFT || ctx->ny > kMaxFFT)
         return fail(ctx, TF_ERR_ARG, "spectra support nx, ny <= 8192");
+    TF_CK(ctx, tf_launch_flush(ctx));
     TF_CK(ctx, tf_launch_spectrum(ctx, inst, which));
     std::vector<double> buf(ctx->n_shell + 1);
     TF_CK(ctx, cudaMemcpyAsync(buf.data(), ctx->d.shell_out, buf.size() * sizeof(double),
@@ -345,6 +353,7 @@ int tf_energy_spectrum(tf_ctx* ctx, int inst, double* E, int n_shell, double* E_
 int tf_phase_difference(tf_ctx* ctx, int inst, double out[6]) {
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    TF_CK(ctx, tf_launch_flush(ctx));
     TF_CK(ctx, tf_launch_phase_difference(ctx, inst, ctx->d.red_out));
     double s[6];
     TF_CK(ctx, cudaMemcpyAsync(s, ctx->d.red_out, 6 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -357,6 +366,7 @@ int tf_phase_difference(tf_ctx* ctx, int inst, double out[6]) {
 int tf_phi_stats(tf_ctx* ctx, int inst, double* mean, double* stddev) {
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
+    TF_CK(ctx, tf_launch_flush(ctx));
     TF_CK(ctx, tf_launch_phi_stats(ctx, inst, ctx->d.red_out));
     double s[2];
     TF_CK(ctx, cudaMemcpyAsync(s, ctx->d.red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -399,9 +409,15 @@ int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
     if (!ctx) return TF_ERR_ARG;
     if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
     int rc;
-    if (h_in && (rc = copy_state(ctx, const_cast<void*>(h_in), false)) != TF_OK) return rc;
+    if (h_in) {
+        ctx->fd_pending = false;  // the uploaded raw state is a plain state
+        if ((rc = copy_state(ctx, const_cast<void*>(h_in), false)) != TF_OK) return rc;
+    }
     if (n > 0) TF_CK(ctx, tf_launch_steps(ctx, n));
-    if (h_out && (rc = copy_state(ctx, h_out, true)) != TF_OK) return rc;
+    if (h_out) {
+        TF_CK(ctx, tf_launch_flush(ctx));
+        if ((rc = copy_state(ctx, h_out, true)) != TF_OK) return rc;
+    }
     TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
     return TF_OK;
 }
@@ -417,6 +433,7 @@ int tf_save(tf_ctx* ctx, const char* path) {
     if (!ctx) return TF_ERR_ARG;
     if (!path) return fail(ctx, TF_ERR_ARG, "null path");
     std::vector<char> buf(tf_state_bytes(ctx));
+    TF_CK(ctx, tf_launch_flush(ctx));
     int rc = copy_state(ctx, buf.data(), true);
     if (rc != TF_OK) return rc;
     TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -448,6 +465,8 @@ int tf_load(tf_ctx* ctx, const char* path) {
     ok = ok && std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
     std::fclose(fp);
     if (!ok) return fail(ctx, TF_ERR_IO, "checkpoint header or size does not match this context");
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->fd_pending = false;
     int rc = copy_state(ctx, buf.data(), false);
     if (rc != TF_OK) return rc;
     TF_CK(ctx, cudaStreamSynchronize(ctx->stream));

@@ -71,6 +71,8 @@ struct tf_ctx {
     DevBuffers d{};
     int fcur = 0;                    // population buffer holding the current state
     int pcur = 0;                    // phi/Q buffer holding the current state
+    int ucur = 0;                    // velocity buffer written by the last fused launch
+    bool fd_pending = false;         // fused path: sub-steps of the last step not yet applied
     int64_t steps = 0;
     int64_t launches = 0;            // kernels launched by this context
     int n_shell = 0;
@@ -85,9 +87,19 @@ size_t tf_layout(const tf_params& p0, int batch, DevBuffers* d, char* base);
 // Precompute the kernel parameter block of one instance.
 DevParams tf_make_devparams(const tf_params& p);
 
-// ---- step kernels (tf_step.cu) -------------------------------------------
-// Advance the whole batch by n steps on ctx->stream.
+// ---- step kernels (tf_step.cu, tf_fused.cu) ---------------------------------
+// Advance the whole batch by n steps on ctx->stream (fused path when
+// available, else the per-stage kernels).
 cudaError_t tf_launch_steps(tf_ctx* ctx, int64_t n);
+// Apply pending sub-steps so that the buffers hold the plain state.
+cudaError_t tf_launch_flush(tf_ctx* ctx);
+// Per-stage kernels: forces, LBM, then n_sub separate sub-step launches.
+cudaError_t tf_unfused_steps(tf_ctx* ctx, int64_t n);
+// Fused kernels (tf_fused.cu): one launch per step for n_sub == 5.
+bool tf_fused_supported(const tf_ctx* ctx);
+cudaError_t tf_fused_steps(tf_ctx* ctx, int64_t n);
+cudaError_t tf_fused_flush(tf_ctx* ctx);
+cudaError_t tf_configure_fused_kernels();
 // Evaluate mu, the fluid-1 stress, the Guo velocities, densities and the
 // non-drag force sum of the current state into d.mu, d.tau and macro_out
 // ([B][8][N]: u1x u1y u2x u2y rho1 rho2 (G1+G2)x (G1+G2)y).

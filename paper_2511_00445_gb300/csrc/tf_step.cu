@@ -190,6 +190,13 @@ dim3 site_grid(const tf_ctx* ctx) {
 }  // namespace
 
 cudaError_t tf_launch_steps(tf_ctx* ctx, int64_t n) {
+    if (tf_fused_supported(ctx)) return tf_fused_steps(ctx, n);
+    return tf_unfused_steps(ctx, n);
+}
+
+cudaError_t tf_launch_flush(tf_ctx* ctx) { return tf_fused_flush(ctx); }
+
+cudaError_t tf_unfused_steps(tf_ctx* ctx, int64_t n) {
     const dim3 grid = site_grid(ctx), block(BX, BY);
     DevBuffers& d = ctx->d;
     for (int64_t it = 0; it < n; ++it) {

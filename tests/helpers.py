@@ -31,7 +31,11 @@ def read_velocities(tf: B.TwoFluid, inst: int):
 
 
 def rel_err(got: np.ndarray, want: np.ndarray) -> float:
+    """max |got - want| / max |want - <want>|; a field with no spread (a
+    single site, a uniform state) is normalised by its magnitude instead."""
     spread = np.abs(want - want.mean()).max()
+    if spread == 0.0:
+        spread = np.abs(want).max()
     diff = np.abs(got - want).max()
     if spread == 0.0:
         return 0.0 if diff == 0.0 else float("inf")

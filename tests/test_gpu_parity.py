@@ -87,6 +87,32 @@ def test_step_parity(nx, ny, steps):
         assert e <= TOL_200, (k, e, errs)
 
 
+@pytest.mark.parametrize("n_sub,nx,ny", [(3, 16, 16), (1, 9, 7), (8, 20, 12)])
+def test_step_parity_unfused_path(n_sub, nx, ny):
+    """Sub-step counts other than five run the per-stage kernels."""
+    tf, ref, op = run_pair(CFG0.with_(nx=nx, ny=ny, n_sub=n_sub), 100)
+    errs = field_errors(tf, 0, ref, op)
+    for k, e in errs.items():
+        assert e <= TOL_200, (k, e, errs)
+
+
+def test_interleaved_steps_and_reads():
+    """Reads between steps complete the pending sub-steps and do not change
+    the trajectory: 1+2+3+4 steps with reads in between equal 10 steps."""
+    p = CFG0.with_(nx=40, ny=36, zeta=0.01)
+    a = make(p, seed=3)
+    b = make(p, seed=3)
+    for n in (1, 2, 3, 4):
+        a.step(n)
+        a.read_field(0, B.FIELD_PHI)
+        a.conserved(0)
+    b.step(10)
+    for fld in (B.FIELD_PHI, B.FIELD_QXX, B.FIELD_QXY, B.FIELD_F1 + 1, B.FIELD_F2 + 8,
+                B.FIELD_U1X, B.FIELD_U2Y):
+        assert np.array_equal(a.read_field(0, fld), b.read_field(0, fld)), fld
+    assert a.step_count() == b.step_count() == 10
+
+
 def test_step_parity_strong_coupling():
     """Large drag, activity, tumbling and elastic constant; unequal tau and
     densities; a non-symmetric initial condition."""
