@@ -178,6 +178,7 @@ int tf_create(const tf_params* params, int batch, void* d_workspace, size_t work
         e = cudaMemcpyAsync(ctx->d.prm, ctx->dparams.data(), batch * sizeof(DevParams),
                             cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = tf_launch_zero_state(ctx);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d.flags, 0, 64 * sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         delete ctx;
@@ -271,6 +272,15 @@ int tf_sync(tf_ctx* ctx) {
     if (!ctx) return TF_ERR_ARG;
     TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
     TF_CK(ctx, cudaGetLastError());
+    // Device status word: a kernel that gave up a bounded wait wrote a code.
+    int flag = 0;
+    TF_CK(ctx, cudaMemcpyAsync(&flag, ctx->d.flags, sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flag != 0) {
+        TF_CK(ctx, cudaMemsetAsync(ctx->d.flags, 0, sizeof(int), ctx->stream));
+        return fail(ctx, flag, "a device-side bounded wait timed out");
+    }
     return TF_OK;
 }
 

