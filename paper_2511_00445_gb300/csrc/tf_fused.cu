@@ -52,124 +52,187 @@ struct Geo {
     static constexpr int NLOAD = DO_FD ? 7 : 3;                  // planes read from global
     static constexpr size_t SMEM = (size_t)NPLANES * A * sizeof(float);
     static constexpr int RP_MAX = R_END + 2 * (NS_FUSED - 1);    // largest phi update radius
-    static constexpr int SLOTS = ((TX + 2 * RP_MAX) * (TY + 2 * RP_MAX) + NT - 1) / NT;
 };
 
-struct Sm {
-    float* p[8];   // phi mu u1x u1y u2x u2y qa qb
-};
+// Dynamic shared memory: eight planes of A floats each, in this order.
+extern __shared__ __align__(16) float tf_smem[];
 enum { P_PHI = 0, P_MU, P_U1X, P_U1Y, P_U2X, P_U2Y, P_QA, P_QB };
 
 // One forward-Euler sub-step: phi on the neighbourhood of radius rp, Q on rq.
-// Sites of a neighbourhood are numbered row-major and dealt to the threads
-// in order; each thread keeps its updated values in registers until all
-// threads have read the old ones.
-template <int RH, int W, int SLOTS>
-__device__ __forceinline__ void fd_substep(const DevParams& P, const Sm& s, int rp, int rq) {
-    float* __restrict__ phi = s.p[P_PHI];
-    float* __restrict__ mu = s.p[P_MU];
-    const float* __restrict__ u1x = s.p[P_U1X];
-    const float* __restrict__ u1y = s.p[P_U1Y];
-    const float* __restrict__ u2x = s.p[P_U2X];
-    const float* __restrict__ u2y = s.p[P_U2Y];
-    float* __restrict__ qa = s.p[P_QA];
-    float* __restrict__ qb = s.p[P_QB];
-    // (a) chemical potential on radius rp + 1 (needs phi on rp + 2)
+//
+// Each warp owns a band of consecutive rows of the neighbourhood across its
+// whole width: lane l holds the column slots q = l and q = l + 32, where slot
+// q is neighbourhood column q - 1 (slots 0 and w + 1 are the one-site halo).
+// A warp walks its band top to bottom keeping the previous, current and next
+// rows of the fields it needs in registers, so y-neighbours come from
+// registers, x-neighbours of read-only planes from shared memory and the
+// x-neighbours of the flux J_x by warp shuffles.  Rows are written back in
+// place as soon as they are computed; the rows just above and below a band
+// belong to other warps and are captured in registers before a barrier.
+__device__ __forceinline__ void shfl_lr(float v1, float v2, int lane, float& l1, float& r1,
+                                        float& l2, float& r2) {
+    const unsigned FULL = 0xffffffffu;
+    const float up1 = __shfl_up_sync(FULL, v1, 1), up2 = __shfl_up_sync(FULL, v2, 1);
+    const float dn1 = __shfl_down_sync(FULL, v1, 1), dn2 = __shfl_down_sync(FULL, v2, 1);
+    const float q31 = __shfl_sync(FULL, v1, 31), q32 = __shfl_sync(FULL, v2, 0);
+    l1 = up1;
+    r1 = lane == 31 ? q32 : dn1;
+    l2 = lane == 0 ? q31 : up2;
+    r2 = dn2;
+}
+
+template <int RH, int W, int A>
+__device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
+    float* __restrict__ phi = tf_smem + P_PHI * A;
+    float* __restrict__ mu = tf_smem + P_MU * A;
+    const float* __restrict__ u1x = tf_smem + P_U1X * A;
+    const float* __restrict__ u1y = tf_smem + P_U1Y * A;
+    const float* __restrict__ u2x = tf_smem + P_U2X * A;
+    const float* __restrict__ u2y = tf_smem + P_U2Y * A;
+    float* __restrict__ qa = tf_smem + P_QA * A;
+    float* __restrict__ qb = tf_smem + P_QB * A;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+
+    // (a) chemical potential on radius ra = rp + 1 (reads phi on ra + 1)
     {
-        const int r = rp + 1, w = TX + 2 * r, cnt = w * (TY + 2 * r);
-        int ly = threadIdx.x / w, lx = threadIdx.x - ly * w;
-        const int dly = NT / w, dlx = NT - dly * w;
-#pragma unroll 4
-        for (int idx = threadIdx.x; idx < cnt; idx += NT) {
-            const int c = (RH - r + ly) * W + RH - r + lx;
-            const float d = phi[c];
-            const float lapd = (phi[c + 1] + phi[c - 1]) + (phi[c + W] + phi[c - W]) - 4.f * d;
-            mu[c] = P.mu0 + d * (P.mu1 + d * (P.mu2 + d * P.mu3)) - P.kappa * lapd;
-            lx += dlx;
-            ly += dly;
-            if (lx >= w) {
-                lx -= w;
-                ly += 1;
+        const int ra = rp + 1, w = TX + 2 * ra, h = TY + 2 * ra, o = RH - ra;
+        const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
+        for (int y = y0; y < y1; ++y) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int x = lane + 32 * k;
+                if (x < w) {
+                    const int c = (o + y) * W + o + x;
+                    const float d = phi[c];
+                    const float lapd = (phi[c + 1] + phi[c - 1]) + (phi[c + W] + phi[c - W]) - 4.f * d;
+                    mu[c] = P.mu0 + d * (P.mu1 + d * (P.mu2 + d * P.mu3)) - P.kappa * lapd;
+                }
             }
         }
     }
     __syncthreads();
-    // (b) new phi on radius rp and new Q on radius rq, into registers
-    const int w = TX + 2 * rp, cnt = w * (TY + 2 * rp);
-    const int ly0 = threadIdx.x / w, lx0 = threadIdx.x - ly0 * w;
-    const int dly = NT / w, dlx = NT - dly * w;
-    float nphi[SLOTS], na[SLOTS], nb[SLOTS];
-    {
-        int ly = ly0, lx = lx0;
+
+    // (b) phi on radius rp, Q on radius rq
+    const int w = TX + 2 * rp, h = TY + 2 * rp, o = RH - rp;
+    const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
+    const int dq = rp - rq;                       // Q neighbourhood inside the phi one
+    int col[2];                                   // shared-memory column of each slot
+    bool cmp[2], cq[2];                           // slot computed for phi / for Q
 #pragma unroll
-        for (int k = 0; k < SLOTS; ++k) {
-            if (threadIdx.x + k * NT < cnt) {
-                const int c = (RH - rp + ly) * W + RH - rp + lx;
-                const int e = c + 1, wv = c - 1, n = c + W, so = c - W;
-                const float pe = P.phi_ref + phi[e], pw = P.phi_ref + phi[wv];
-                const float pn = P.phi_ref + phi[n], ps = P.phi_ref + phi[so];
-                const float jxe = pe * (u2x[e] + pe * (u1x[e] - u2x[e]));
-                const float jxw = pw * (u2x[wv] + pw * (u1x[wv] - u2x[wv]));
-                const float jyn = pn * (u2y[n] + pn * (u1y[n] - u2y[n]));
-                const float jys = ps * (u2y[so] + ps * (u1y[so] - u2y[so]));
-                const float lapmu = (mu[e] + mu[wv]) + (mu[n] + mu[so]) - 4.f * mu[c];
-                const float divJ = 0.5f * ((jxe - jxw) + (jyn - jys));
-                nphi[k] = phi[c] + P.dt_fd * (P.M * lapmu - divJ);
-                const int dy = ly - rp, dx = lx - rp;   // rq-region test (rq <= rp)
-                if (dx >= -rq && dx < TX + rq && dy >= -rq && dy < TY + rq) {
-                    const float a = qa[c], bq = qb[c];
-                    const float ae = qa[e], aw = qa[wv], an = qa[n], as = qa[so];
-                    const float be = qb[e], bw = qb[wv], bn = qb[n], bs = qb[so];
-                    const float lapa = (ae + aw) + (an + as) - 4.f * a;
-                    const float lapb = (be + bw) + (bn + bs) - 4.f * bq;
-                    const float cq = -(P.A_Q + P.C_Q * (a * a + bq * bq));
-                    const float h = cq * a + P.K * lapa;
-                    const float g = cq * bq + P.K * lapb;
-                    const float Wxx = 0.5f * (u1x[e] - u1x[wv]), Wxy = 0.5f * (u1x[n] - u1x[so]);
-                    const float Wyx = 0.5f * (u1y[e] - u1y[wv]), Wyy = 0.5f * (u1y[n] - u1y[so]);
-                    const float trE = Wxx + Wyy;
-                    const float e1 = 0.5f * (Wxx - Wyy);
-                    const float exy = 0.5f * (Wxy + Wyx);
-                    const float om = Wxy - Wyx;
-                    const float QE2 = 4.f * (a * e1 + bq * exy);
-                    const float ux = u1x[c], uy = u1y[c];
-                    const float adv_a = ux * 0.5f * (ae - aw) + uy * 0.5f * (an - as);
-                    const float adv_b = ux * 0.5f * (be - bw) + uy * 0.5f * (bn - bs);
-                    const float ra = -adv_a + P.lam * (trE * a + e1 - QE2 * a) + om * bq + P.GammaQ * h;
-                    const float rb = -adv_b + P.lam * (trE * bq + exy - QE2 * bq) - om * a + P.GammaQ * g;
-                    na[k] = a + P.dt_fd * ra;
-                    nb[k] = bq + P.dt_fd * rb;
-                }
+    for (int k = 0; k < 2; ++k) {
+        const int q = lane + 32 * k;
+        col[k] = o - 1 + min(q, w + 1);           // clamp idle slots onto the halo
+        cmp[k] = q >= 1 && q <= w;
+        cq[k] = cmp[k] && q - 1 >= dq && q - 1 < dq + TX + 2 * rq;
+    }
+    auto flux = [&](float pv, float v1, float v2) { return pv * (v2 + pv * (v1 - v2)); };
+    // Row state of the rolling window (two column slots each).
+    struct Row {
+        float mu[2], ax[2], ay[2], qa[2], qb[2], jy[2], ph[2], jx[2];
+    };
+    Row r0, r1, r2;                               // three rows: roles rotate by renaming
+    float e_ph[2], e_qa[2], e_qb[2];              // row y1 (below the band), captured early
+    auto load_row = [&](Row& R, int y, bool edge) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int c = (o + y) * W + col[k];
+            R.mu[k] = mu[c];
+            R.ax[k] = u1x[c];
+            R.ay[k] = u1y[c];
+            if (edge) {
+                R.ph[k] = e_ph[k];
+                R.qa[k] = e_qa[k];
+                R.qb[k] = e_qb[k];
+            } else {
+                R.ph[k] = phi[c];
+                R.qa[k] = qa[c];
+                R.qb[k] = qb[c];
             }
-            lx += dlx;
-            ly += dly;
-            if (lx >= w) {
-                lx -= w;
-                ly += 1;
+            const float pv = P.phi_ref + R.ph[k];
+            R.jy[k] = flux(pv, R.ay[k], u2y[c]);
+            R.jx[k] = flux(pv, R.ax[k], u2x[c]);
+        }
+    };
+    // Compute row y from (Pr, Cr, Nr) = rows y-1, y, y+1 and write it back.
+    auto do_row = [&](int y, const Row& Pr, const Row& Cr, const Row& Nr) {
+        float jl[2], jr[2];
+        shfl_lr(Cr.jx[0], Cr.jx[1], lane, jl[0], jr[0], jl[1], jr[1]);
+        const bool qrow = y >= dq && y < dq + TY + 2 * rq;
+        float nph[2], nqa[2], nqb[2];
+        bool wq[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int c = (o + y) * W + col[k];
+            const float lapmu = (mu[c + 1] + mu[c - 1]) + (Nr.mu[k] + Pr.mu[k]) - 4.f * Cr.mu[k];
+            const float divJ = 0.5f * ((jr[k] - jl[k]) + (Nr.jy[k] - Pr.jy[k]));
+            nph[k] = Cr.ph[k] + P.dt_fd * (P.M * lapmu - divJ);
+            wq[k] = qrow && cq[k];
+            nqa[k] = 0.f;
+            nqb[k] = 0.f;
+            if (wq[k]) {
+                const float a = Cr.qa[k], bq = Cr.qb[k];
+                const float ae = qa[c + 1], aw = qa[c - 1], be = qb[c + 1], bw = qb[c - 1];
+                const float lapa = (ae + aw) + (Nr.qa[k] + Pr.qa[k]) - 4.f * a;
+                const float lapb = (be + bw) + (Nr.qb[k] + Pr.qb[k]) - 4.f * bq;
+                const float cqf = -(P.A_Q + P.C_Q * (a * a + bq * bq));
+                const float hh = cqf * a + P.K * lapa;
+                const float g = cqf * bq + P.K * lapb;
+                const float Wxx = 0.5f * (u1x[c + 1] - u1x[c - 1]), Wxy = 0.5f * (Nr.ax[k] - Pr.ax[k]);
+                const float Wyx = 0.5f * (u1y[c + 1] - u1y[c - 1]), Wyy = 0.5f * (Nr.ay[k] - Pr.ay[k]);
+                const float trE = Wxx + Wyy;
+                const float e1 = 0.5f * (Wxx - Wyy);
+                const float exy = 0.5f * (Wxy + Wyx);
+                const float om = Wxy - Wyx;
+                const float QE2 = 4.f * (a * e1 + bq * exy);
+                const float ux = Cr.ax[k], uy = Cr.ay[k];
+                const float adv_a = ux * 0.5f * (ae - aw) + uy * 0.5f * (Nr.qa[k] - Pr.qa[k]);
+                const float adv_b = ux * 0.5f * (be - bw) + uy * 0.5f * (Nr.qb[k] - Pr.qb[k]);
+                const float ra = -adv_a + P.lam * (trE * a + e1 - QE2 * a) + om * bq + P.GammaQ * hh;
+                const float rb = -adv_b + P.lam * (trE * bq + exy - QE2 * bq) - om * a + P.GammaQ * g;
+                nqa[k] = a + P.dt_fd * ra;
+                nqb[k] = bq + P.dt_fd * rb;
             }
         }
-    }
-    __syncthreads();
-    // (c) write back in place
-    {
-        int ly = ly0, lx = lx0;
+        __syncwarp();   // every lane has read row y (x-neighbours) before it is overwritten
 #pragma unroll
-        for (int k = 0; k < SLOTS; ++k) {
-            if (threadIdx.x + k * NT < cnt) {
-                const int c = (RH - rp + ly) * W + RH - rp + lx;
-                phi[c] = nphi[k];
-                const int dy = ly - rp, dx = lx - rp;
-                if (dx >= -rq && dx < TX + rq && dy >= -rq && dy < TY + rq) {
-                    qa[c] = na[k];
-                    qb[c] = nb[k];
-                }
+        for (int k = 0; k < 2; ++k) {
+            const int c = (o + y) * W + col[k];
+            if (cmp[k]) phi[c] = nph[k];
+            if (wq[k]) {
+                qa[c] = nqa[k];
+                qb[c] = nqb[k];
             }
-            lx += dlx;
-            ly += dly;
-            if (lx >= w) {
-                lx -= w;
-                ly += 1;
-            }
+        }
+    };
+    if (y0 < y1) {
+        load_row(r0, y0 - 1, false);
+        load_row(r1, y0, false);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int ce = (o + y1) * W + col[k];
+            e_ph[k] = phi[ce];
+            e_qa[k] = qa[ce];
+            e_qb[k] = qb[ce];
+        }
+    }
+    __syncthreads();   // band edges captured before any row is overwritten
+    int y = y0;
+    for (; y + 3 <= y1; y += 3) {
+        load_row(r2, y + 1, false);
+        do_row(y, r0, r1, r2);
+        load_row(r0, y + 2, false);
+        do_row(y + 1, r1, r2, r0);
+        load_row(r1, y + 3, y + 3 == y1);
+        do_row(y + 2, r2, r0, r1);
+    }
+    if (y < y1) {
+        load_row(r2, y + 1, y + 1 == y1);
+        do_row(y, r0, r1, r2);
+        ++y;
+        if (y < y1) {
+            load_row(r0, y + 1, y + 1 == y1);
+            do_row(y, r1, r2, r0);
         }
     }
     __syncthreads();
@@ -207,34 +270,23 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
         const DevParams* __restrict__ prm, int nx, int ny, int* __restrict__ err) {
     using G = Geo<DO_FD, DO_LBM>;
     constexpr int RH = G::RH, W = G::W, H = G::H, A = G::A;
-    extern __shared__ __align__(16) float smem[];
     __shared__ __align__(8) uint64_t bar;
-    Sm s;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) s.p[k] = smem + k * A;
     const int b = blockIdx.z;
     const long long N = (long long)nx * ny;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const DevParams& P = prm[b];
+    const DevParams P = prm[b];
     // 16-byte bulk copies need every row start on a 16-byte boundary.
     const bool bulk = (nx & 3) == 0;
 
     // ---- stage 1: tile loads (and population prefetch)
-    const float* gsrc[G::NLOAD];
-    int sdst[G::NLOAD];
-    gsrc[0] = phi_in + b * N;
-    sdst[0] = P_PHI;
-    gsrc[1] = Q_in + 2 * b * N;
-    sdst[1] = P_QA;
-    gsrc[2] = Q_in + (2 * b + 1) * N;
-    sdst[2] = P_QB;
-    if constexpr (DO_FD) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            gsrc[3 + k] = u_in + (4 * b + k) * N;
-            sdst[3 + k] = P_U1X + k;
-        }
-    }
+    // Load task pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y.
+    auto src_plane = [&](int pl) -> const float* {
+        return pl == 0 ? phi_in + b * N
+                       : (pl < 3 ? Q_in + (2 * b + pl - 1) * N : u_in + (4 * b + pl - 3) * N);
+    };
+    auto dst_plane = [&](int pl) -> float* {
+        return tf_smem + (pl == 0 ? P_PHI : (pl < 3 ? P_QA + pl - 1 : P_U1X + pl - 3)) * A;
+    };
     if (bulk) {
         if (threadIdx.x == 0) {
             tfp::mbar_init(&bar, 1);
@@ -246,7 +298,7 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
         for (int t = threadIdx.x; t < G::NLOAD * H; t += NT) {
             const int pl = t / H, ly = t - pl * H;
             const int gy = wrapc(y0 - RH + ly, ny);
-            bulk_row(s.p[sdst[pl]] + ly * W, gsrc[pl], gy, x0 - RH, W, nx, &bar);
+            bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, W, nx, &bar);
         }
         if constexpr (DO_LBM) {
             const float* F = fsrc + 18 * b * N;
@@ -268,7 +320,7 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
             const int ly = i / W, lx = i - ly * W;
             const long long g = (long long)wrapc(y0 - RH + ly, ny) * nx + wrapc(x0 - RH + lx, nx);
 #pragma unroll
-            for (int pl = 0; pl < G::NLOAD; ++pl) s.p[sdst[pl]][i] = gsrc[pl][g];
+            for (int pl = 0; pl < G::NLOAD; ++pl) dst_plane(pl)[i] = src_plane(pl)[g];
         }
         __syncthreads();
     }
@@ -279,7 +331,7 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
         for (int st = 0; st < NS_FUSED; ++st) {
             const int rp = G::R_END + 2 * (NS_FUSED - 1 - st);
             const int rq = G::R_END + (NS_FUSED - 1 - st);
-            fd_substep<RH, W, G::SLOTS>(P, s, rp, rq);
+            fd_substep<RH, W, A>(P, rp, rq);
         }
     }
 
@@ -287,9 +339,9 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
     if constexpr (DO_LBM) {
         // ---- stage 3a: chemical potential and fluid-1 stress on radius 1
         {
-            const float* phi = s.p[P_PHI];
-            const float* qa = s.p[P_QA];
-            const float* qb = s.p[P_QB];
+            const float* phi = tf_smem + P_PHI * A;
+            const float* qa = tf_smem + P_QA * A;
+            const float* qb = tf_smem + P_QB * A;
             constexpr int w = TX + 2, cnt = w * (TY + 2);
             for (int idx = threadIdx.x; idx < cnt; idx += NT) {
                 const int ly = idx / w, lx = idx - ly * w;
@@ -298,21 +350,21 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
                     P, phi[c], phi[c + 1], phi[c - 1], phi[c + W], phi[c - W], qa[c], qa[c + 1],
                     qa[c - 1], qa[c + W], qa[c - W], qb[c], qb[c + 1], qb[c - 1], qb[c + W],
                     qb[c - W]);
-                s.p[P_MU][c] = r.mu;
-                s.p[P_U1X][c] = r.sxx;
-                s.p[P_U1Y][c] = r.sxy;
-                s.p[P_U2X][c] = r.syx;
-                s.p[P_U2Y][c] = r.syy;
+                tf_smem[P_MU * A + c] = r.mu;
+                tf_smem[P_U1X * A + c] = r.sxx;
+                tf_smem[P_U1Y * A + c] = r.sxy;
+                tf_smem[P_U2X * A + c] = r.syx;
+                tf_smem[P_U2Y * A + c] = r.syy;
             }
         }
         __syncthreads();
         // ---- stage 3b: interior forces, pull, moments, drag, collide, store
-        const float* phi = s.p[P_PHI];
-        const float* mu = s.p[P_MU];
-        const float* sxx = s.p[P_U1X];
-        const float* sxy = s.p[P_U1Y];
-        const float* syx = s.p[P_U2X];
-        const float* syy = s.p[P_U2Y];
+        const float* phi = tf_smem + P_PHI * A;
+        const float* mu = tf_smem + P_MU * A;
+        const float* sxx = tf_smem + P_U1X * A;
+        const float* sxy = tf_smem + P_U1Y * A;
+        const float* syx = tf_smem + P_U2X * A;
+        const float* syy = tf_smem + P_U2Y * A;
         const float* F1 = fsrc + 18 * b * N;
         const float* F2 = F1 + 9 * N;
         float* D1 = fdst + 18 * b * N;
@@ -367,9 +419,9 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
             if (x >= nx || y >= ny) continue;
             const int c = (RH + r) * W + RH + tx;
             const long long g = (long long)y * nx + x;
-            po[g] = s.p[P_PHI][c];
-            qo[g] = s.p[P_QA][c];
-            qo[N + g] = s.p[P_QB][c];
+            po[g] = tf_smem[P_PHI * A + c];
+            qo[g] = tf_smem[P_QA * A + c];
+            qo[N + g] = tf_smem[P_QB * A + c];
         }
     }
 }
