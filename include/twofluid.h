@@ -50,6 +50,7 @@ extern "C" {
 #define TF_ERR_TIMEOUT   (-4)  /* a bounded device wait ran out                  */
 #define TF_ERR_IO        (-5)  /* checkpoint file could not be read or written   */
 #define TF_ERR_WORKSPACE (-6)  /* workspace missing, too small or misaligned     */
+#define TF_ERR_TOO_LARGE (-7)  /* input larger than a fixed-footprint entry point accepts */
 
 /* ---- field ids for tf_read_field / tf_write_field -------------------- */
 #define TF_FIELD_PHI   0   /* concentration phi of the active fluid (r/w)        */
@@ -188,6 +189,39 @@ int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out);
 /* Checkpoint / resume of the whole context (header + raw state), bitwise. */
 int tf_save(tf_ctx* ctx, const char* path);
 int tf_load(tf_ctx* ctx, const char* path);
+
+/* ---- fixed-footprint entry point ------------------------------------- */
+/* The paper has no counterpart to this call; it exists for integration.
+ *
+ * Every other entry point works inside the workspace the caller handed to
+ * tf_create.  Some callers cannot provide device memory at the moment they
+ * need an answer: a plug-in living inside a host application whose memory
+ * pool owns the whole device, or a time-critical loop where cudaMalloc (which
+ * may synchronise the device, and fails once a framework's caching allocator
+ * has reserved the memory) is not allowed.  tf_phi_stats_noalloc gives such
+ * callers the concentration statistics of tf_phi_stats without any allocation:
+ * it calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Input: d_values, a device array of n FP32 values v_i (for example the
+ * stored deviations phi - phi_ref of a concentration field).  Output: d_out, a
+ * device array of 2 doubles receiving mean = phi_ref + <v> and the standard
+ * deviation of v, both summed in FP64.  The call only enqueues work on
+ * `stream` (a cudaStream_t passed as void*); synchronise before reading d_out.
+ *
+ * Scratch: the library keeps TF_NOALLOC_MAX_BLOCKS x 2 doubles (16 KiB) of
+ * per-block partial sums in one statically allocated device array, held by
+ * every GPU that loads the library until the process exits.  Each block sums
+ * 4096 values, so n is limited to TF_NOALLOC_MAX_ELEMS (4 194 304, e.g. one
+ * 2048 x 2048 field); larger n returns TF_ERR_TOO_LARGE, n <= 0 or a null
+ * pointer TF_ERR_ARG.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress with that device current) and caches
+ * it; make that first call before any stream capture.  All calls share the
+ * array: two calls whose kernels overlap on the GPU (different streams, or
+ * different host threads on one device) race and may return wrong values. */
+#define TF_NOALLOC_MAX_BLOCKS 1024
+#define TF_NOALLOC_MAX_ELEMS  (4096LL * TF_NOALLOC_MAX_BLOCKS)
+int tf_phi_stats_noalloc(const float* d_values, long long n, double phi_ref,
+                         double* d_out, void* stream);
 
 #ifdef __cplusplus
 }

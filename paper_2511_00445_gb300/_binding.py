@@ -23,6 +23,8 @@ TF_ERR_NONFINITE = -3
 TF_ERR_TIMEOUT = -4
 TF_ERR_IO = -5
 TF_ERR_WORKSPACE = -6
+TF_ERR_TOO_LARGE = -7
+NOALLOC_MAX_ELEMS = 4096 * 1024
 
 FIELD_PHI, FIELD_QXX, FIELD_QXY = 0, 1, 2
 FIELD_U1X, FIELD_U1Y, FIELD_U2X, FIELD_U2Y = 3, 4, 5, 6
@@ -37,7 +39,7 @@ EXPORTS = [
     "tf_write_field", "tf_set_equilibrium", "tf_read_field", "tf_step", "tf_sync",
     "tf_step_count", "tf_kernel_launches", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
     "tf_length_scale", "tf_energy_spectrum", "tf_phase_difference", "tf_phi_stats",
-    "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load",
+    "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load", "tf_phi_stats_noalloc",
 ]
 
 
@@ -135,6 +137,7 @@ def load_library() -> ctypes.CDLL:
         "tf_advance_host": (i, [vp, vp, i64, vp]),
         "tf_save": (i, [vp, ctypes.c_char_p]),
         "tf_load": (i, [vp, ctypes.c_char_p]),
+        "tf_phi_stats_noalloc": (i, [vp, ctypes.c_longlong, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

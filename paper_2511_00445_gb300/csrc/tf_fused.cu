@@ -51,7 +51,6 @@ struct Geo {
     static constexpr int NPLANES = 8;                            // phi mu u1x u1y u2x u2y qa qb
     static constexpr int NLOAD = DO_FD ? 7 : 3;                  // planes read from global
     static constexpr size_t SMEM = (size_t)NPLANES * A * sizeof(float);
-    static constexpr int RP_MAX = R_END + 2 * (NS_FUSED - 1);    // largest phi update radius
 };
 
 // Dynamic shared memory: eight planes of A floats each, in this order.
