@@ -23,6 +23,7 @@
 //     forces, pulled populations, drag solve, collision and stores.
 #include "tf_device.cuh"
 #include "tf_internal.h"
+#include "tf_pair.cuh"
 #include "tf_ptx.cuh"
 
 namespace {
@@ -60,28 +61,15 @@ enum { P_PHI = 0, P_MU, P_U1X, P_U1Y, P_U2X, P_U2Y, P_QA, P_QB };
 // One forward-Euler sub-step: phi on the neighbourhood of radius rp, Q on rq.
 //
 // Each warp owns a band of consecutive rows of the neighbourhood across its
-// whole width: lane l holds the column slots q = l and q = l + 32, where slot
-// q is neighbourhood column q - 1 (slots 0 and w + 1 are the one-site halo).
-// A warp walks its band top to bottom keeping the previous, current and next
-// rows of the fields it needs in registers, so y-neighbours come from
-// registers, x-neighbours of read-only planes from shared memory and the
-// x-neighbours of the flux J_x by warp shuffles.  Rows are written back in
-// place as soon as they are computed; the rows just above and below a band
-// belong to other warps and are captured in registers before a barrier.
-__device__ __forceinline__ void shfl_lr(float v1, float v2, int lane, float& l1, float& r1,
-                                        float& l2, float& r2) {
-    const unsigned FULL = 0xffffffffu;
-    const float up1 = __shfl_up_sync(FULL, v1, 1), up2 = __shfl_up_sync(FULL, v2, 1);
-    const float dn1 = __shfl_down_sync(FULL, v1, 1), dn2 = __shfl_down_sync(FULL, v2, 1);
-    const float q31 = __shfl_sync(FULL, v1, 31), q32 = __shfl_sync(FULL, v2, 0);
-    l1 = up1;
-    r1 = lane == 31 ? q32 : dn1;
-    l2 = lane == 0 ? q31 : up2;
-    r2 = dn2;
-}
-
+// whole width; lane l holds one pair of adjacent columns (64-bit shared loads,
+// paired FP32 arithmetic).  A warp walks its band top to bottom keeping rows
+// y-1, y, y+1 in registers (roles rotate by renaming), so y-neighbours come
+// from registers and x-neighbours from warp shuffles.  Rows are written back
+// in place after a warp sync; the rows just above and below a band belong to
+// other warps and are captured in registers before a barrier.
 template <int RH, int W, int A>
 __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
+    using namespace tfq;
     float* __restrict__ phi = tf_smem + P_PHI * A;
     float* __restrict__ mu = tf_smem + P_MU * A;
     const float* __restrict__ u1x = tf_smem + P_U1X * A;
@@ -92,21 +80,26 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
     float* __restrict__ qb = tf_smem + P_QB * A;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = NT / 32;
+    const f2 mu0 = S2(P.mu0), mu1 = S2(P.mu1), mu2 = S2(P.mu2), mu3 = S2(P.mu3);
+    const f2 kap = S2(-P.kappa), m4 = S2(-4.f), half = S2(0.5f), cref = S2(P.phi_ref);
 
     // (a) chemical potential on radius ra = rp + 1 (reads phi on ra + 1)
     {
         const int ra = rp + 1, w = TX + 2 * ra, h = TY + 2 * ra, o = RH - ra;
+        const PairCols pc(o, w, lane);
         const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
-        for (int y = y0; y < y1; ++y) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int x = lane + 32 * k;
-                if (x < w) {
-                    const int c = (o + y) * W + o + x;
-                    const float d = phi[c];
-                    const float lapd = (phi[c + 1] + phi[c - 1]) + (phi[c + W] + phi[c - W]) - 4.f * d;
-                    mu[c] = P.mu0 + d * (P.mu1 + d * (P.mu2 + d * P.mu3)) - P.kappa * lapd;
-                }
+        if (y0 < y1) {
+            const float* col = phi + pc.c0;
+            f2 pp = ld2(col + (o + y0 - 1) * W), pcur = ld2(col + (o + y0) * W);
+            for (int y = y0; y < y1; ++y) {
+                const f2 pn = ld2(col + (o + y + 1) * W);
+                f2 l, r;
+                nbr2(pcur, l, r);
+                const f2 lap = F2(m4, pcur, A2(A2(l, r), A2(pp, pn)));
+                const f2 poly = F2(pcur, F2(pcur, F2(pcur, mu3, mu2), mu1), mu0);
+                st_pair(mu + (o + y) * W + pc.c0, F2(kap, lap, poly), pc.in0, pc.in1);
+                pp = pcur;
+                pcur = pn;
             }
         }
     }
@@ -114,106 +107,94 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
 
     // (b) phi on radius rp, Q on radius rq
     const int w = TX + 2 * rp, h = TY + 2 * rp, o = RH - rp;
+    const PairCols pc(o, w, lane);
     const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
-    const int dq = rp - rq;                       // Q neighbourhood inside the phi one
-    int col[2];                                   // shared-memory column of each slot
-    bool cmp[2], cq[2];                           // slot computed for phi / for Q
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int q = lane + 32 * k;
-        col[k] = o - 1 + min(q, w + 1);           // clamp idle slots onto the halo
-        cmp[k] = q >= 1 && q <= w;
-        cq[k] = cmp[k] && q - 1 >= dq && q - 1 < dq + TX + 2 * rq;
-    }
-    auto flux = [&](float pv, float v1, float v2) { return pv * (v2 + pv * (v1 - v2)); };
-    // Row state of the rolling window (two column slots each).
+    const int oq = RH - rq, wq = TX + 2 * rq;     // Q neighbourhood (shared coordinates)
+    // (pc.in0 / in1 are false on surplus lanes; the Q neighbourhood lies inside)
+    const bool q0 = pc.in0 && pc.c0 >= oq && pc.c0 < oq + wq;
+    const bool q1 = pc.in1 && pc.c0 + 1 >= oq && pc.c0 + 1 < oq + wq;
+    const f2 dt = S2(P.dt_fd), Mm = S2(P.M), K2 = S2(P.K), lam = S2(P.lam), GQ = S2(P.GammaQ);
+    const f2 AQ = S2(-P.A_Q), CQ = S2(-P.C_Q), four = S2(4.f);
+    auto flux = [&](f2 pv, f2 v1, f2 v2) { return M2(pv, F2(pv, B2(v1, v2), v2)); };
     struct Row {
-        float mu[2], ax[2], ay[2], qa[2], qb[2], jy[2], ph[2], jx[2];
+        f2 mu, ax, ay, qa, qb, jy, ph, jx;
     };
     Row r0, r1, r2;                               // three rows: roles rotate by renaming
-    float e_ph[2], e_qa[2], e_qb[2];              // row y1 (below the band), captured early
+    f2 e_ph, e_qa, e_qb;                          // row y1 (below the band), captured early
     auto load_row = [&](Row& R, int y, bool edge) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int c = (o + y) * W + col[k];
-            R.mu[k] = mu[c];
-            R.ax[k] = u1x[c];
-            R.ay[k] = u1y[c];
-            if (edge) {
-                R.ph[k] = e_ph[k];
-                R.qa[k] = e_qa[k];
-                R.qb[k] = e_qb[k];
-            } else {
-                R.ph[k] = phi[c];
-                R.qa[k] = qa[c];
-                R.qb[k] = qb[c];
-            }
-            const float pv = P.phi_ref + R.ph[k];
-            R.jy[k] = flux(pv, R.ay[k], u2y[c]);
-            R.jx[k] = flux(pv, R.ax[k], u2x[c]);
+        const int c = (o + y) * W + pc.c0;
+        R.mu = ld2(mu + c);
+        R.ax = ld2(u1x + c);
+        R.ay = ld2(u1y + c);
+        if (edge) {
+            R.ph = e_ph;
+            R.qa = e_qa;
+            R.qb = e_qb;
+        } else {
+            R.ph = ld2(phi + c);
+            R.qa = ld2(qa + c);
+            R.qb = ld2(qb + c);
         }
+        const f2 pv = A2(cref, R.ph);
+        R.jy = flux(pv, R.ay, ld2(u2y + c));
+        R.jx = flux(pv, R.ax, ld2(u2x + c));
     };
     // Compute row y from (Pr, Cr, Nr) = rows y-1, y, y+1 and write it back.
     auto do_row = [&](int y, const Row& Pr, const Row& Cr, const Row& Nr) {
-        float jl[2], jr[2];
-        shfl_lr(Cr.jx[0], Cr.jx[1], lane, jl[0], jr[0], jl[1], jr[1]);
-        const bool qrow = y >= dq && y < dq + TY + 2 * rq;
-        float nph[2], nqa[2], nqb[2];
-        bool wq[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int c = (o + y) * W + col[k];
-            const float lapmu = (mu[c + 1] + mu[c - 1]) + (Nr.mu[k] + Pr.mu[k]) - 4.f * Cr.mu[k];
-            const float divJ = 0.5f * ((jr[k] - jl[k]) + (Nr.jy[k] - Pr.jy[k]));
-            nph[k] = Cr.ph[k] + P.dt_fd * (P.M * lapmu - divJ);
-            wq[k] = qrow && cq[k];
-            nqa[k] = 0.f;
-            nqb[k] = 0.f;
-            if (wq[k]) {
-                const float a = Cr.qa[k], bq = Cr.qb[k];
-                const float ae = qa[c + 1], aw = qa[c - 1], be = qb[c + 1], bw = qb[c - 1];
-                const float lapa = (ae + aw) + (Nr.qa[k] + Pr.qa[k]) - 4.f * a;
-                const float lapb = (be + bw) + (Nr.qb[k] + Pr.qb[k]) - 4.f * bq;
-                const float cqf = -(P.A_Q + P.C_Q * (a * a + bq * bq));
-                const float hh = cqf * a + P.K * lapa;
-                const float g = cqf * bq + P.K * lapb;
-                const float Wxx = 0.5f * (u1x[c + 1] - u1x[c - 1]), Wxy = 0.5f * (Nr.ax[k] - Pr.ax[k]);
-                const float Wyx = 0.5f * (u1y[c + 1] - u1y[c - 1]), Wyy = 0.5f * (Nr.ay[k] - Pr.ay[k]);
-                const float trE = Wxx + Wyy;
-                const float e1 = 0.5f * (Wxx - Wyy);
-                const float exy = 0.5f * (Wxy + Wyx);
-                const float om = Wxy - Wyx;
-                const float QE2 = 4.f * (a * e1 + bq * exy);
-                const float ux = Cr.ax[k], uy = Cr.ay[k];
-                const float adv_a = ux * 0.5f * (ae - aw) + uy * 0.5f * (Nr.qa[k] - Pr.qa[k]);
-                const float adv_b = ux * 0.5f * (be - bw) + uy * 0.5f * (Nr.qb[k] - Pr.qb[k]);
-                const float ra = -adv_a + P.lam * (trE * a + e1 - QE2 * a) + om * bq + P.GammaQ * hh;
-                const float rb = -adv_b + P.lam * (trE * bq + exy - QE2 * bq) - om * a + P.GammaQ * g;
-                nqa[k] = a + P.dt_fd * ra;
-                nqb[k] = bq + P.dt_fd * rb;
-            }
+        f2 l, r;
+        nbr2(Cr.jx, l, r);
+        const f2 divJ = M2(half, A2(B2(r, l), B2(Nr.jy, Pr.jy)));
+        nbr2(Cr.mu, l, r);
+        const f2 lapmu = F2(m4, Cr.mu, A2(A2(l, r), A2(Nr.mu, Pr.mu)));
+        const f2 nph = F2(dt, F2(Mm, lapmu, make_float2(-divJ.x, -divJ.y)), Cr.ph);
+        const int row = o + y;
+        const bool qrow = row >= oq && row < oq + TY + 2 * rq;
+        f2 nqa = Cr.qa, nqb = Cr.qb;
+        if (qrow) {
+            f2 al, ar, bl, br, uxl, uxr, uyl, uyr;
+            nbr2(Cr.qa, al, ar);
+            nbr2(Cr.qb, bl, br);
+            nbr2(Cr.ax, uxl, uxr);
+            nbr2(Cr.ay, uyl, uyr);
+            const f2 a = Cr.qa, bq = Cr.qb;
+            const f2 lapa = F2(m4, a, A2(A2(al, ar), A2(Nr.qa, Pr.qa)));
+            const f2 lapb = F2(m4, bq, A2(A2(bl, br), A2(Nr.qb, Pr.qb)));
+            const f2 cqf = F2(CQ, F2(a, a, M2(bq, bq)), AQ);        // -(A_Q + C_Q q^2)
+            const f2 hh = F2(cqf, a, M2(K2, lapa));
+            const f2 g = F2(cqf, bq, M2(K2, lapb));
+            const f2 Wxx = M2(half, B2(uxr, uxl)), Wxy = M2(half, B2(Nr.ax, Pr.ax));
+            const f2 Wyx = M2(half, B2(uyr, uyl)), Wyy = M2(half, B2(Nr.ay, Pr.ay));
+            const f2 trE = A2(Wxx, Wyy);
+            const f2 e1 = M2(half, B2(Wxx, Wyy));
+            const f2 exy = M2(half, A2(Wxy, Wyx));
+            const f2 om = B2(Wxy, Wyx);
+            const f2 QE2 = M2(four, F2(a, e1, M2(bq, exy)));
+            // -(u1 . grad) a and b, central differences
+            const f2 adv_a = M2(half, F2(Cr.ax, B2(ar, al), M2(Cr.ay, B2(Nr.qa, Pr.qa))));
+            const f2 adv_b = M2(half, F2(Cr.ax, B2(br, bl), M2(Cr.ay, B2(Nr.qb, Pr.qb))));
+            // lam (trE a + e1 - QE2 a) + om b + Gamma h - adv
+            const f2 sa = F2(lam, A2(B2(M2(trE, a), M2(QE2, a)), e1), M2(om, bq));
+            const f2 sb = F2(lam, A2(B2(M2(trE, bq), M2(QE2, bq)), exy), N2(M2(om, a)));
+            const f2 ra = B2(F2(GQ, hh, sa), adv_a);
+            const f2 rb = B2(F2(GQ, g, sb), adv_b);
+            nqa = F2(dt, ra, a);
+            nqb = F2(dt, rb, bq);
         }
-        __syncwarp();   // every lane has read row y (x-neighbours) before it is overwritten
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int c = (o + y) * W + col[k];
-            if (cmp[k]) phi[c] = nph[k];
-            if (wq[k]) {
-                qa[c] = nqa[k];
-                qb[c] = nqb[k];
-            }
+        __syncwarp();   // every lane has read row y before it is overwritten
+        const int c = row * W + pc.c0;
+        st_pair(phi + c, nph, pc.in0, pc.in1);
+        if (qrow) {
+            st_pair(qa + c, nqa, q0, q1);
+            st_pair(qb + c, nqb, q0, q1);
         }
     };
     if (y0 < y1) {
         load_row(r0, y0 - 1, false);
         load_row(r1, y0, false);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int ce = (o + y1) * W + col[k];
-            e_ph[k] = phi[ce];
-            e_qa[k] = qa[ce];
-            e_qb[k] = qb[ce];
-        }
+        const int ce = (o + y1) * W + pc.c0;
+        e_ph = ld2(phi + ce);
+        e_qa = ld2(qa + ce);
+        e_qb = ld2(qb + ce);
     }
     __syncthreads();   // band edges captured before any row is overwritten
     int y = y0;
@@ -336,24 +317,44 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
 
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     if constexpr (DO_LBM) {
+        using namespace tfq;
         // ---- stage 3a: chemical potential and fluid-1 stress on radius 1
+        // (paired column walk like the sub-steps; results go to the mu plane
+        // and to the four u planes, free after the sub-steps)
         {
             const float* phi = tf_smem + P_PHI * A;
             const float* qa = tf_smem + P_QA * A;
             const float* qb = tf_smem + P_QB * A;
-            constexpr int w = TX + 2, cnt = w * (TY + 2);
-            for (int idx = threadIdx.x; idx < cnt; idx += NT) {
-                const int ly = idx / w, lx = idx - ly * w;
-                const int c = (RH - 1 + ly) * W + RH - 1 + lx;
-                const tfd::SiteStress r = tfd::site_stress(
-                    P, phi[c], phi[c + 1], phi[c - 1], phi[c + W], phi[c - W], qa[c], qa[c + 1],
-                    qa[c - 1], qa[c + W], qa[c - W], qb[c], qb[c + 1], qb[c - 1], qb[c + W],
-                    qb[c - W]);
-                tf_smem[P_MU * A + c] = r.mu;
-                tf_smem[P_U1X * A + c] = r.sxx;
-                tf_smem[P_U1Y * A + c] = r.sxy;
-                tf_smem[P_U2X * A + c] = r.syx;
-                tf_smem[P_U2Y * A + c] = r.syy;
+            constexpr int o = RH - 1, w = TX + 2, h = TY + 2, NW = NT / 32;
+            const PairCols pc(o, w, tx);
+            constexpr int bh = (h + NW - 1) / NW;
+            const int y0 = ty * bh, y1 = min(h, y0 + bh);
+            if (y0 < y1) {
+                const int col = pc.c0;
+                f2 dp = ld2(phi + (o + y0 - 1) * W + col), dc = ld2(phi + (o + y0) * W + col);
+                f2 ap = ld2(qa + (o + y0 - 1) * W + col), ac = ld2(qa + (o + y0) * W + col);
+                f2 bp = ld2(qb + (o + y0 - 1) * W + col), bc = ld2(qb + (o + y0) * W + col);
+                for (int y = y0; y < y1; ++y) {
+                    const int cn = (o + y + 1) * W + col, cc = (o + y) * W + col;
+                    const f2 dn = ld2(phi + cn), an = ld2(qa + cn), bn = ld2(qb + cn);
+                    f2 dl, dr, al, ar, bl, br;
+                    nbr2(dc, dl, dr);
+                    nbr2(ac, al, ar);
+                    nbr2(bc, bl, br);
+                    const PairStress r =
+                        stress2(P, dc, dl, dr, dn, dp, ac, al, ar, an, ap, bc, bl, br, bn, bp);
+                    st_pair(tf_smem + P_MU * A + cc, r.mu, pc.in0, pc.in1);
+                    st_pair(tf_smem + P_U1X * A + cc, r.sxx, pc.in0, pc.in1);
+                    st_pair(tf_smem + P_U1Y * A + cc, r.sxy, pc.in0, pc.in1);
+                    st_pair(tf_smem + P_U2X * A + cc, r.syx, pc.in0, pc.in1);
+                    st_pair(tf_smem + P_U2Y * A + cc, r.syy, pc.in0, pc.in1);
+                    dp = dc;
+                    dc = dn;
+                    ap = ac;
+                    ac = an;
+                    bp = bc;
+                    bc = bn;
+                }
             }
         }
         __syncthreads();
@@ -365,7 +366,7 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
         const float* syx = tf_smem + P_U2X * A;
         const float* syy = tf_smem + P_U2Y * A;
         const float* F1 = fsrc + 18 * b * N;
-        const float* F2 = F1 + 9 * N;
+        const float* F2p = F1 + 9 * N;
         float* D1 = fdst + 18 * b * N;
         float* D2 = D1 + 9 * N;
         float* uo = u_out + 4 * b * N;
@@ -374,39 +375,31 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
             const int x = x0 + tx, y = y0 + r;
             if (x >= nx || y >= ny) continue;
             const int c = (RH + r) * W + RH + tx;
-            const float d = phi[c];
-            const tfd::SiteForce Fo = tfd::site_force(
-                P, d, phi[c + 1], phi[c - 1], phi[c + W], phi[c - W], mu[c], mu[c + 1],
-                mu[c - 1], mu[c + W], mu[c - W], sxx[c + 1], sxx[c - 1], sxy[c + W], sxy[c - W],
-                syx[c + 1], syx[c - 1], syy[c + W], syy[c - W]);
             const int xp = x + 1 < nx ? x + 1 : 0, xm = x > 0 ? x - 1 : nx - 1;
             const int yp = y + 1 < ny ? y + 1 : 0, ym = y > 0 ? y - 1 : ny - 1;
-            float f1[9], f2[9];
+            f2 f[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
                 const int sy = d2q9_cy(i) == 0 ? y : (d2q9_cy(i) > 0 ? ym : yp);
                 const long long src = (long long)sy * nx + sx;
-                f1[i] = F1[i * N + src];
-                f2[i] = F2[i * N + src];
+                f[i] = P2(F1[i * N + src], F2p[i * N + src]);
             }
-            float dr1, m1x, m1y, dr2, m2x, m2y;
-            tfd::moments(f1, dr1, m1x, m1y);
-            tfd::moments(f2, dr2, m2x, m2y);
-            const tfd::Velocities v = tfd::drag_solve(P, P.phi_ref + d, 1.f + dr1, m1x, m1y,
-                                                      1.f + dr2, m2x, m2y, Fo);
-            tfd::collide(f1, dr1, v.u1x, v.u1y, v.F1x, v.F1y, P.omega1, P.guo1);
-            tfd::collide(f2, dr2, v.u2x, v.u2y, v.F2x, v.F2y, P.omega2, P.guo2);
+            f2 u1, u2;
+            lbm_site2(P, phi[c], P2(phi[c - 1], phi[c + 1]), P2(phi[c - W], phi[c + W]), mu[c],
+                      P2(mu[c - 1], mu[c + 1]), P2(mu[c - W], mu[c + W]), P2(sxx[c - 1], sxx[c + 1]),
+                      P2(sxy[c - W], sxy[c + W]), P2(syx[c - 1], syx[c + 1]),
+                      P2(syy[c - W], syy[c + W]), f, u1, u2);
             const long long g = (long long)y * nx + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                D1[i * N + g] = f1[i];
-                D2[i * N + g] = f2[i];
+                D1[i * N + g] = f[i].x;
+                D2[i * N + g] = f[i].y;
             }
-            uo[g] = v.u1x;
-            uo[N + g] = v.u1y;
-            uo[2 * N + g] = v.u2x;
-            uo[3 * N + g] = v.u2y;
+            uo[g] = u1.x;
+            uo[N + g] = u1.y;
+            uo[2 * N + g] = u2.x;
+            uo[3 * N + g] = u2.y;
         }
     }
     if constexpr (DO_FD) {

@@ -1,0 +1,178 @@
+// Paired FP32 arithmetic for the fused step: each lane carries two adjacent
+// columns, and every operation is applied to both with its own correctly
+// rounded scalar instruction (__fadd_rn, __fsub_rn, __fmul_rn, __fmaf_rn).
+// These are never contracted or reassociated, so the prologue, epilogue and
+// steady-state kernels produce bitwise the same values for the same inputs,
+// and every value equals the IEEE result of the written operation order.
+//
+// The packed FP32x2 forms (the __f*2_rn intrinsics, or add/sub/mul/fma.rn.f32x2
+// in inline PTX) were tried here and rejected: in this kernel a few sites per
+// sub-step came out one ulp away from the written order, consistently with an
+// unrounded product feeding a subtraction, and where that happened moved with
+// code layout, so two kernels running the same sub-step disagreed.
+#pragma once
+
+#include "tf_internal.h"
+
+namespace tfq {
+
+typedef float2 f2;
+__device__ __forceinline__ f2 S2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ f2 P2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f2 A2(f2 a, f2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ f2 B2(f2 a, f2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+__device__ __forceinline__ f2 M2(f2 a, f2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+// a * b + c with a single rounding per element
+__device__ __forceinline__ f2 F2(f2 a, f2 b, f2 c) {
+    return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ f2 N2(f2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// Left / right x-neighbours of a lane's column pair (2P, 2P+1): the outer
+// ones come from the adjacent lanes.
+__device__ __forceinline__ void nbr2(f2 v, f2& l, f2& r) {
+    const float up = __shfl_up_sync(0xffffffffu, v.y, 1);
+    const float dn = __shfl_down_sync(0xffffffffu, v.x, 1);
+    l = make_float2(up, v.x);
+    r = make_float2(v.y, dn);
+}
+
+// Column pair of this lane for a neighbourhood whose columns start at shared
+// column o and span w: lanes cover pairs from the one holding column o - 1 to
+// the one holding column o + w (the one-column halo).  Surplus lanes repeat
+// the last pair so that their loads stay in bounds, but their shuffled
+// neighbours are not the pair's true neighbours: they never write (in0, in1
+// false).  in0 / in1: the pair's columns inside the neighbourhood.
+struct PairCols {
+    int c0;
+    bool in0, in1;
+    __device__ __forceinline__ PairCols(int o, int w, int lane) {
+        const int pb = (o - 1) >> 1, pl = (o + w) >> 1;
+        const bool own = pb + lane <= pl;
+        c0 = 2 * min(pb + lane, pl);
+        in0 = own && c0 >= o && c0 < o + w;
+        in1 = own && c0 + 1 >= o && c0 + 1 < o + w;
+    }
+};
+
+__device__ __forceinline__ void st_pair(float* p, f2 v, bool in0, bool in1) {
+    if (in0 && in1) {
+        *reinterpret_cast<float2*>(p) = v;
+    } else {
+        if (in0) p[0] = v.x;
+        if (in1) p[1] = v.y;
+    }
+}
+
+// Chemical potential and fluid-1 stress (elastic + active) for a column pair,
+// from the pair's values (d = phi - phi_ref, a = Q_xx, b = Q_xy) and their
+// x-neighbours (l, r) and y-neighbours (s = row below, n = row above).  Same
+// algebra as tfd::site_stress.
+struct PairStress {
+    f2 mu, sxx, sxy, syx, syy;
+};
+
+__device__ __forceinline__ PairStress stress2(const DevParams& P, f2 d, f2 dl, f2 dr, f2 dn,
+                                              f2 ds, f2 a, f2 al, f2 ar, f2 an, f2 as, f2 b,
+                                              f2 bl, f2 br, f2 bn, f2 bs) {
+    const f2 m4 = S2(-4.f), half = S2(0.5f);
+    PairStress o;
+    const f2 lapd = F2(m4, d, A2(A2(dr, dl), A2(dn, ds)));
+    const f2 poly = F2(d, F2(d, F2(d, S2(P.mu3), S2(P.mu2)), S2(P.mu1)), S2(P.mu0));
+    o.mu = F2(S2(-P.kappa), lapd, poly);
+    const f2 lapa = F2(m4, a, A2(A2(ar, al), A2(an, as)));
+    const f2 lapb = F2(m4, b, A2(A2(br, bl), A2(bn, bs)));
+    const f2 dxa = M2(half, B2(ar, al)), dya = M2(half, B2(an, as));
+    const f2 dxb = M2(half, B2(br, bl)), dyb = M2(half, B2(bn, bs));
+    const f2 cq = F2(S2(-P.C_Q), F2(a, a, M2(b, b)), S2(-P.A_Q));
+    const f2 K = S2(P.K), k2 = S2(2.f * P.K), lam = S2(P.lam);
+    const f2 h = F2(cq, a, M2(K, lapa));
+    const f2 g = F2(cq, b, M2(K, lapb));
+    const f2 Txx = M2(k2, F2(dxa, dxa, M2(dxb, dxb)));
+    const f2 Tyy = M2(k2, F2(dya, dya, M2(dyb, dyb)));
+    const f2 Txy = M2(k2, F2(dxa, dya, M2(dxb, dyb)));
+    const f2 l2qh = M2(S2(4.f * P.lam), F2(a, h, M2(b, g)));     // 2 lam (Q:H)
+    const f2 anti = M2(S2(2.f), B2(M2(a, g), M2(b, h)));
+    const f2 phv = A2(S2(P.phi_ref), d);
+    const f2 zp = M2(S2(P.zeta), phv);
+    const f2 za = M2(zp, a), zb = M2(zp, b);
+    o.sxx = A2(B2(F2(l2qh, a, N2(M2(lam, h))), Txx), za);
+    o.syy = B2(B2(F2(lam, h, N2(M2(l2qh, a))), Tyy), za);
+    const f2 sym = A2(B2(F2(l2qh, b, N2(M2(lam, g))), Txy), zb);
+    o.sxy = A2(sym, anti);
+    o.syx = B2(sym, anti);
+    return o;
+}
+
+// One interior site of the LBM stage with the two fluids paired:
+// forces G from the stress / mu / phi neighbourhood (same algebra as
+// tfd::site_force), moments, implicit-drag Guo velocities (tfd::drag_solve)
+// and the BGK + Guo collision of both fluids (tfd::collide).  f[i] holds
+// (fluid 1, fluid 2) deviations of direction i and is updated in place; the
+// Guo velocities are returned as u1 = (u1x, u1y), u2 = (u2x, u2y).
+__device__ __forceinline__ void lbm_site2(const DevParams& P, float d, f2 dlr_x /*(dw, de)*/,
+                                          f2 dns_y /*(ds, dn)*/, float m0, f2 mwe, f2 msn,
+                                          f2 sxx_we, f2 sxy_sn, f2 syx_we, f2 syy_sn,
+                                          f2 (&f)[9], f2& u1, f2& u2) {
+    const f2 half = S2(0.5f);
+    const float c = P.phi_ref;
+    // capillary force F_ch = [phi_+ (mu_0 - mu_+) - phi_- (mu_0 - mu_-)] / 2 per axis,
+    // components paired as (x, y)
+    const f2 mm = P2(mwe.x, msn.x), mp = P2(mwe.y, msn.y);     // (mu_w, mu_s), (mu_e, mu_n)
+    const f2 dm = P2(dlr_x.x, dns_y.x), dp = P2(dlr_x.y, dns_y.y);
+    const f2 M0 = S2(m0);
+    const f2 fch = M2(half, B2(F2(S2(c), B2(mm, mp), M2(dp, B2(M0, mp))), M2(dm, B2(M0, mm))));
+    const f2 divs = M2(half, P2(__fadd_rn(__fsub_rn(sxx_we.y, sxx_we.x), __fsub_rn(sxy_sn.y, sxy_sn.x)),
+                                __fadd_rn(__fsub_rn(syx_we.y, syx_we.x), __fsub_rn(syy_sn.y, syy_sn.x))));
+    const float phv = __fadd_rn(c, d);
+    const float om = __fsub_rn(__fsub_rn(1.f, c), d);
+    const f2 G1 = F2(S2(phv), fch, divs);
+    const f2 G2 = M2(S2(om), fch);
+    // moments of both fluids: (drho1, drho2), (m1x, m2x), (m1y, m2y)
+    const f2 dr = A2(A2(A2(A2(f[0], f[1]), A2(f[2], f[3])), A2(A2(f[4], f[5]), A2(f[6], f[7]))), f[8]);
+    const f2 mx = A2(B2(f[1], f[3]), A2(B2(f[5], f[6]), B2(f[8], f[7])));
+    const f2 my = A2(B2(f[2], f[4]), B2(A2(f[5], f[6]), A2(f[7], f[8])));
+    // implicit drag: (rho1 + g/2) u1 - g/2 u2 = m1 + G1/2, -g/2 u1 + (rho2 + g/2) u2 = m2 + G2/2
+    const float gd = __fmul_rn(__fmul_rn(P.gamma, phv), __fsub_rn(1.f, phv));
+    const float ad = __fmul_rn(0.5f, gd);
+    const f2 rho = A2(S2(1.f), dr);
+    const float det = __fmaf_rn(rho.x, rho.y, __fmul_rn(ad, __fadd_rn(rho.x, rho.y)));
+    const float inv = __frcp_rn(det);
+    const f2 r1 = F2(half, G1, P2(mx.x, my.x));                 // (r1x, r1y)
+    const f2 r2 = F2(half, G2, P2(mx.y, my.y));                 // (r2x, r2y)
+    u1 = M2(F2(S2(__fadd_rn(rho.y, ad)), r1, M2(S2(ad), r2)), S2(inv));
+    u2 = M2(F2(S2(ad), r1, M2(S2(__fadd_rn(rho.x, ad)), r2)), S2(inv));
+    const f2 du = M2(S2(gd), B2(u2, u1));
+    const f2 F1 = A2(G1, du), Fv2 = B2(G2, du);
+    // collision, fluids paired: components as (fluid 1, fluid 2)
+    const f2 UX = P2(u1.x, u2.x), UY = P2(u1.y, u2.y);
+    const f2 FX = P2(F1.x, Fv2.x), FY = P2(F1.y, Fv2.y);
+    const f2 OM = P2(P.omega1, P.omega2), GU = P2(P.guo1, P.guo2);
+    const f2 usq15 = M2(S2(1.5f), F2(UX, UX, M2(UY, UY)));
+    const f2 uF3 = M2(S2(3.f), F2(UX, FX, M2(UY, FY)));
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = d2q9_cx(i), cy = d2q9_cy(i);
+        f2 cu, cF;
+        if (cx == 0 && cy == 0) {
+            cu = S2(0.f);
+            cF = S2(0.f);
+        } else if (cy == 0) {
+            cu = cx > 0 ? UX : N2(UX);
+            cF = cx > 0 ? FX : N2(FX);
+        } else if (cx == 0) {
+            cu = cy > 0 ? UY : N2(UY);
+            cF = cy > 0 ? FY : N2(FY);
+        } else {
+            cu = cx > 0 ? (cy > 0 ? A2(UX, UY) : B2(UX, UY)) : (cy > 0 ? B2(UY, UX) : N2(A2(UX, UY)));
+            cF = cx > 0 ? (cy > 0 ? A2(FX, FY) : B2(FX, FY)) : (cy > 0 ? B2(FY, FX) : N2(A2(FX, FY)));
+        }
+        const f2 w = S2(d2q9_w(i));
+        const f2 deq = M2(w, F2(rho, B2(M2(cu, F2(S2(4.5f), cu, S2(3.f))), usq15), dr));
+        const f2 src = M2(M2(GU, w), F2(S2(9.f), M2(cu, cF), B2(M2(S2(3.f), cF), uF3)));
+        f[i] = A2(F2(N2(OM), B2(f[i], deq), f[i]), src);
+    }
+}
+
+}  // namespace tfq
