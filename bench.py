@@ -10,7 +10,13 @@ Beris-Edwards sub-steps).  The state (~44 MB) fits in L2, so L2 is flushed
 CUDA events on the solver's stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sweep256|single2048]
+                    [--workload sweep256|single1024|single2048] [--storage f32|f16|bf16]
+
+--storage f16|bf16 stores the populations as 16-bit deviations (FP32
+arithmetic).  Such a run also times the FP32 storage on the same workload
+(speedup) and reports how far the two trajectories are apart after
+--error-steps steps from one initial state (fields, L and the energy
+spectrum of instance 0).
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own copy of
 the workload with its own seed (independent ensemble members, weak scaling);
@@ -34,12 +40,16 @@ if ROOT not in sys.path:
 
 METRIC = "coupled-step MLUPS & % HBM roofline; surrogate/FP16 vs plain FP32 at stated error"
 UNIT = "MLUPS"
-BYTES_PER_SITE = 168  # FP32: 18 populations read + written (144 B) + phi, Q read + written (24 B)
+# Algorithmic bytes per site and step: 18 populations read + written (FP32:
+# 144 B, 16-bit storage: 72 B) + phi, Q read + written (24 B).
+BYTES_PER_SITE = {"f32": 168, "f16": 96, "bf16": 96}
 FLUSH_BYTES = 256 << 20
 
 WORKLOADS = {
     "sweep256": dict(nx=256, ny=256, zetas=[0.0, 0.002, 0.005, 0.01],
                      name="zeta sweep {0,0.002,0.005,0.01} x 256x256, FP32, lambda 0.7, K 0.04"),
+    "single1024": dict(nx=1024, ny=1024, zetas=[0.005],
+                       name="single 1024x1024, FP32, zeta 0.005, lambda 0.7, K 0.04"),
     "single2048": dict(nx=2048, ny=2048, zetas=[0.005],
                        name="single 2048x2048, FP32, zeta 0.005, lambda 0.7, K 0.04"),
 }
@@ -151,9 +161,9 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str):
+def recorded_traffic(kernel: str, workload: str, storage: str = "f32"):
     """DRAM bytes per launch from a committed ncu summary, only if it was
-    taken from the current kernel sources."""
+    taken from the current kernel sources (and the same population storage)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         lines = open(path).read().splitlines()
@@ -162,7 +172,8 @@ def recorded_traffic(kernel: str, workload: str):
     sha = kernel_source_sha()
     for ln in lines:
         kv = dict(tok.split("=", 1) for tok in ln.split() if "=" in tok)
-        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha") == sha:
+        if (kv.get("kernel") == kernel and kv.get("workload") == workload
+                and kv.get("source_sha") == sha and kv.get("storage", "f32") == storage):
             return float(kv["bytes_per_launch"])
     return None
 
@@ -226,6 +237,71 @@ def run_reference(args, wl):
 
 
 # -------------------------------------------------------------- our arm
+def time_steps(tf, flush, steps: int, warmup: int, world: int, dev, clocks=None):
+    """W untimed steps, then K steps each timed alone with CUDA events on the
+    solver stream after an L2 flush; barrier + synchronize on both sides."""
+    import torch
+    stream = tf.stream
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.zero_()
+            tf.step(1)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    if clocks is not None:
+        clocks.start()
+    launches0 = tf.kernel_launches()
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            tf.step(1)
+            b.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    launches = tf.kernel_launches() - launches0
+    clk = clocks.stop() if clocks is not None else None
+    return [a.elapsed_time(b) for a, b in evs], launches, clk
+
+
+def trajectory_gap(B, params, seed: int, steps: int, storage: int, dev) -> dict:
+    """Instance 0 of the workload advanced `steps` steps from one initial
+    state with FP32 storage and with `storage`: max field differences
+    normalised by the FP32 field's spread, and the relative differences of
+    L (Eq. 27), <|u_c|^2>/2 and the energy spectrum (Eq. 22) shells."""
+    import numpy as np
+    runs = {}
+    for mode in (B.STORE_F32, storage):
+        tf = B.TwoFluid([params[0].with_(storage=mode)], device=dev)
+        tf.init_fields(seed=seed, phi0=0.5, dphi=0.01, S0=0.01)
+        tf.step(steps)
+        flds = {k: tf.read_field(0, f) for k, f in (
+            ("phi", B.FIELD_PHI), ("Qxx", B.FIELD_QXX), ("Qxy", B.FIELD_QXY),
+            ("u1x", B.FIELD_U1X), ("u1y", B.FIELD_U1Y), ("u2x", B.FIELD_U2X), ("u2y", B.FIELD_U2Y))}
+        E, Et = tf.energy_spectrum(0)
+        runs[mode] = (flds, tf.length_scale(0), E, Et)
+        tf.close()
+    (f0, L0, E0, Et0), (f1, L1, E1, Et1) = runs[B.STORE_F32], runs[storage]
+
+    def gap(a, b):
+        sp = float(np.abs(a - a.mean()).max()) or float(np.abs(a).max()) or 1.0
+        return float(np.abs(b - a).max()) / sp
+    uscale = max(float(np.abs(f0[k] - f0[k].mean()).max()) for k in ("u1x", "u1y", "u2x", "u2y"))
+    ugap = {k: float(np.abs(f1[k] - f0[k]).max()) / uscale for k in ("u1x", "u1y", "u2x", "u2y")}
+    live = E0 > 1e-3 * E0.max()
+    return {"steps": steps, "phi": gap(f0["phi"], f1["phi"]),
+            "Q": max(gap(f0["Qxx"], f1["Qxx"]), gap(f0["Qxy"], f1["Qxy"])),
+            "u": max(ugap.values()), "L_rel": abs(L1 - L0) / L0,
+            "E_total_rel": abs(Et1 - Et0) / Et0,
+            "E_shell_rel_max": float((np.abs(E1 - E0)[live] / E0[live]).max()),
+            "normalisation": "max |X_16 - X_32| / max |X_32 - <X_32>| (u: largest u spread)"}
+
+
 def run_ours(args, wl):
     import torch
 
@@ -244,38 +320,15 @@ def run_ours(args, wl):
         torch.cuda.set_device(local)
     from paper_2511_00445_gb300 import _binding as B
     dev = torch.device("cuda", local)
-    params = [B.SolverParams(nx=wl["nx"], ny=wl["ny"], zeta=z) for z in wl["zetas"]]
+    storage = B.STORAGE_NAMES[args.storage]
+    params = [B.SolverParams(nx=wl["nx"], ny=wl["ny"], zeta=z, storage=storage) for z in wl["zetas"]]
     sites = wl["nx"] * wl["ny"] * len(params)
+    seed = rank_seed(0, rank)
     tf = B.TwoFluid(params, device=dev)
-    tf.init_fields(seed=rank_seed(0, rank), phi0=0.5, dphi=0.01, S0=0.01)
-    stream = tf.stream
+    tf.init_fields(seed=seed, phi0=0.5, dphi=0.01, S0=0.01)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.zero_()
-            tf.step(1)
-    torch.cuda.synchronize(dev)
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
     clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    clocks.start()
-    launches0 = tf.kernel_launches()
-    with torch.cuda.stream(stream):
-        for a, b in evs:
-            flush.zero_()
-            a.record(stream)
-            tf.step(1)
-            b.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    launches = tf.kernel_launches() - launches0
-    clk = clocks.stop()
-    ms = [a.elapsed_time(b) for a, b in evs]
+    ms, launches, clk = time_steps(tf, flush, args.steps, args.warmup, world, dev, clocks)
     sec_local = sum(ms) / 1e3
     sec = reduce_max(sec_local, world, dev)
     value, _ = aggregate([sec] * world, sites, args.steps)
@@ -284,13 +337,14 @@ def run_ours(args, wl):
     c = tf.conserved(0)  # finite state check after the timed region
 
     peak, peak_kind = measured_peaks()
+    bps = BYTES_PER_SITE[args.storage]
     # With five sub-steps every timed step is one launch of the fused kernel.
     kernel_name = "k_fused<1,1>" if launches == args.steps else "tf_step (per-stage kernels)"
-    achieved = BYTES_PER_SITE * sites / (statistics.mean(ms) / 1e3) / 1e9
-    traffic = recorded_traffic(kernel_name, args.workload)
+    achieved = bps * sites / (statistics.mean(ms) / 1e3) / 1e9
+    traffic = recorded_traffic(kernel_name, args.workload, args.storage)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": kernel_name, "bytes_per_site": BYTES_PER_SITE,
+                "kernel": kernel_name, "bytes_per_site": bps,
                 "launches_per_step": launches / args.steps}
 
     # End to end through the host-buffer entry point: raw state in from pinned
@@ -313,6 +367,21 @@ def run_ours(args, wl):
         e2e = {"value": sites * k_e2e * world / el / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
                "api": "tf_advance_host (raw state in, 1 step, raw state out)"}
+    tf.close()
+
+    # 16-bit storage: FP32 storage on the same workload, timed the same way,
+    # and the distance between the two trajectories.
+    precision = None
+    if storage != B.STORE_F32:
+        ref = B.TwoFluid([p.with_(storage=B.STORE_F32) for p in params], device=dev)
+        ref.init_fields(seed=seed, phi0=0.5, dphi=0.01, S0=0.01)
+        ms32, _, _ = time_steps(ref, flush, args.steps, args.warmup, world, dev)
+        ref.close()
+        sec32 = reduce_max(sum(ms32) / 1e3, world, dev)
+        value32, _ = aggregate([sec32] * world, sites, args.steps)
+        precision = {"storage": args.storage, "f32_value": value32, "speedup_vs_f32": value / value32,
+                     "gap_vs_f32": trajectory_gap(B, params, seed, args.error_steps, storage, dev)
+                     if rank == 0 else None}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -323,20 +392,24 @@ def run_ours(args, wl):
                          f"({el:.1f} s) after one warm-up step"}
 
     if rank == 0:
+        name = wl["name"] if storage == B.STORE_F32 else wl["name"].replace(
+            "FP32", f"FP32 arithmetic, {args.storage.upper()} population storage")
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded SplitMix64 initial condition of Sec. III)",
-            "config": {"workload": wl["name"], "sites_per_step": sites, "instances": len(params),
+            "config": {"workload": name, "sites_per_step": sites, "instances": len(params),
+                       "storage": args.storage,
                        "l2": "flushed (256 MiB write) before every timed step",
                        "timing": "CUDA events per step on the solver stream"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches,
             "state_check": {"nonfinite": c[7], "sum_phi": c[0]},
         }
+        if precision is not None:
+            out["precision"] = precision
         print(json.dumps(out), flush=True)
-    tf.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -351,6 +424,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
+                    help="population storage (arithmetic is FP32 in every mode)")
+    ap.add_argument("--error-steps", type=int, default=200,
+                    help="steps of the FP32-vs-16-bit trajectory comparison")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -69,7 +69,16 @@ extern "C" {
  * c5..c8 = (1,1), (-1,1), (-1,-1), (1,-1). */
 
 /* ---- storage precision of the populations ---------------------------- */
-#define TF_STORE_F32   0   /* FP32 deviations f_i - w_i                       */
+/* The device keeps each population as its deviation d_i = f_i - w_i from the
+ * rest equilibrium of unit density (w_i the D2Q9 weights).  All arithmetic
+ * is FP32 whatever the storage; only the stored value is rounded.  The paper
+ * (Sec. III) computes in one precision throughout; the 16-bit modes have no
+ * counterpart there. */
+#define TF_STORE_F32   0   /* FP32 d_i                                              */
+#define TF_STORE_F16   1   /* FP16 of d_i * 2^12 (round to nearest even); the
+                              exact power-of-two scale keeps |d_i| from 1.5e-8 up
+                              in the normal range; |d_i| must stay below 16      */
+#define TF_STORE_BF16  2   /* BF16 of d_i (round to nearest even)                  */
 
 /* Per-instance parameters (Sec. III parameter list; lattice units). */
 typedef struct tf_params {
@@ -116,7 +125,9 @@ int tf_init_fields(tf_ctx* ctx, int inst, uint64_t seed, double phi0,
                    double dphi, double S0);
 
 /* Overwrite a stored field of one instance from a host array (synchronous).
- * Writable: TF_FIELD_PHI, QXX, QXY and the 18 populations. */
+ * Writable: TF_FIELD_PHI, QXX, QXY and the 18 populations.  Values are
+ * rounded to FP32 and, for a population under a 16-bit storage mode, then
+ * to that mode (the population arrays hold f_i itself, not d_i). */
 int tf_write_field(tf_ctx* ctx, int inst, int field, const double* host);
 
 /* Set both fluids' populations to the equilibrium with rest densities
@@ -126,7 +137,8 @@ int tf_set_equilibrium(tf_ctx* ctx, int inst, const double* u1, const double* u2
 
 /* Read one field of one instance into a host array of nx*ny doubles.
  * Derived fields (velocities, densities, mu) are evaluated on the current
- * state exactly as the next step would evaluate them.  Synchronous. */
+ * state exactly as the next step would evaluate them.  A population reads
+ * back as w_i + (its stored deviation widened to FP32).  Synchronous. */
 int tf_read_field(tf_ctx* ctx, int inst, int field, double* host);
 
 /* Advance every instance by n >= 0 coupled lattice steps.  Asynchronous on

@@ -31,6 +31,9 @@ FIELD_U1X, FIELD_U1Y, FIELD_U2X, FIELD_U2Y = 3, 4, 5, 6
 FIELD_RHO1, FIELD_RHO2, FIELD_MU = 7, 8, 9
 FIELD_F1, FIELD_F2 = 16, 32
 STORE_F32 = 0
+STORE_F16 = 1
+STORE_BF16 = 2
+STORAGE_NAMES = {"f32": STORE_F32, "f16": STORE_F16, "bf16": STORE_BF16}
 NCONS = 8
 
 # Every symbol include/twofluid.h declares, in declaration order.

@@ -39,7 +39,8 @@ int fail_cuda(tf_ctx* ctx, const char* where, cudaError_t e) {
 const char* check_params(const tf_params& p) {
     if (p.nx < 1 || p.ny < 1 || p.nx > kMaxDim || p.ny > kMaxDim) return "nx, ny must be in [1, 32768]";
     if (p.n_sub < 1 || p.n_sub > 64) return "n_sub must be in [1, 64]";
-    if (p.storage != TF_STORE_F32) return "unsupported storage mode";
+    if (p.storage != TF_STORE_F32 && p.storage != TF_STORE_F16 && p.storage != TF_STORE_BF16)
+        return "storage must be TF_STORE_F32, TF_STORE_F16 or TF_STORE_BF16";
     if (!(p.tau1 > 0.5) || !(p.tau2 > 0.5)) return "tau1, tau2 must exceed 1/2";
     if (!(p.rho1 > 0) || !(p.rho2 > 0)) return "rho1, rho2 must be positive";
     const double v[] = {p.gamma, p.zeta, p.lambda, p.K, p.Gamma_Q, p.A_Q,
@@ -111,7 +112,7 @@ size_t tf_layout(const tf_params& p0, int batch, DevBuffers* d, char* base) {
         return p;
     };
     DevBuffers t{};
-    for (int k = 0; k < 2; ++k) t.f[k] = (float*)take(18 * B * N * sizeof(float));
+    for (int k = 0; k < 2; ++k) t.f[k] = take(18 * B * N * tf_pop_bytes(p0.storage));
     for (int k = 0; k < 2; ++k) t.phi[k] = (float*)take(B * N * sizeof(float));
     for (int k = 0; k < 2; ++k) t.Q[k] = (float*)take(2 * B * N * sizeof(float));
     for (int k = 0; k < 2; ++k) t.u[k] = (float*)take(4 * B * N * sizeof(float));
@@ -392,14 +393,14 @@ int tf_phi_stats(tf_ctx* ctx, int inst, double* mean, double* stddev) {
 size_t tf_state_bytes(const tf_ctx* ctx) {
     if (!ctx) return 0;
     const size_t N = (size_t)ctx->N, B = (size_t)ctx->batch;
-    return (18 + 1 + 2) * B * N * sizeof(float);
+    return 18 * B * N * tf_pop_bytes(ctx->storage) + (1 + 2) * B * N * sizeof(float);
 }
 
-// Raw state blob: populations [B][18][N], phi [B][N], Q [B][2][N] (FP32).
+// Raw state blob: populations [B][18][N] (storage type), phi [B][N], Q [B][2][N] (FP32).
 static int copy_state(tf_ctx* ctx, void* host, bool to_host) {
     const size_t N = (size_t)ctx->N, B = (size_t)ctx->batch;
     char* h = (char*)host;
-    const size_t sf = 18 * B * N * sizeof(float), sp = B * N * sizeof(float),
+    const size_t sf = 18 * B * N * tf_pop_bytes(ctx->storage), sp = B * N * sizeof(float),
                  sq = 2 * B * N * sizeof(float);
     void* dev[3] = {ctx->d.f[ctx->fcur], ctx->d.phi[ctx->pcur], ctx->d.Q[ctx->pcur]};
     const size_t sz[3] = {sf, sp, sq};

@@ -231,19 +231,20 @@ __device__ __forceinline__ void bulk_row(float* dst, const float* plane, int gy,
     }
 }
 
-__device__ __forceinline__ void prefetch_row(const float* plane, int gy, int xs, int len, int nx) {
+template <typename T>
+__device__ __forceinline__ void prefetch_row(const T* plane, int gy, int xs, int len, int nx) {
     int off = 0;
     while (off < len) {
         const int gx = wrapc(xs + off, nx);
         const int n = min(len - off, nx - gx);
-        tfp::prefetch_l2(plane + (long long)gy * nx + gx, (uint32_t)n * 4u);
+        tfp::prefetch_l2(plane + (long long)gy * nx + gx, (uint32_t)(n * sizeof(T)));
         off += n;
     }
 }
 
-template <bool DO_FD, bool DO_LBM>
+template <bool DO_FD, bool DO_LBM, class S>
 __global__ void __launch_bounds__(NT, 2)
-k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
+k_fused(const typename S::T* __restrict__ fsrc, typename S::T* __restrict__ fdst,
         const float* __restrict__ phi_in, float* __restrict__ phi_out,
         const float* __restrict__ Q_in, float* __restrict__ Q_out,
         const float* __restrict__ u_in, float* __restrict__ u_out,
@@ -257,6 +258,9 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
     const DevParams P = prm[b];
     // 16-byte bulk copies need every row start on a 16-byte boundary.
     const bool bulk = (nx & 3) == 0;
+    // Population prefetch: rows of PF elements (16 bytes) at 16-byte boundaries.
+    constexpr int PF = 16 / (int)sizeof(typename S::T);
+    const bool pref = nx % PF == 0;
 
     // ---- stage 1: tile loads (and population prefetch)
     // Load task pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y.
@@ -280,11 +284,11 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
             const int gy = wrapc(y0 - RH + ly, ny);
             bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, W, nx, &bar);
         }
-        if constexpr (DO_LBM) {
-            const float* F = fsrc + 18 * b * N;
+        if (DO_LBM && pref) {
+            const typename S::T* F = fsrc + 18 * b * N;
             for (int t = threadIdx.x; t < 18 * (TY + 2); t += NT) {
                 const int i = t / (TY + 2), r = t - i * (TY + 2);
-                prefetch_row(F + (long long)i * N, wrapc(y0 - 1 + r, ny), x0 - 4, TX + 8, nx);
+                prefetch_row(F + (long long)i * N, wrapc(y0 - 1 + r, ny), x0 - PF, TX + 2 * PF, nx);
             }
         }
         const bool ok = tfp::wait_bounded(&bar, 0, kWaitPolls);
@@ -365,10 +369,10 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
         const float* sxy = tf_smem + P_U1Y * A;
         const float* syx = tf_smem + P_U2X * A;
         const float* syy = tf_smem + P_U2Y * A;
-        const float* F1 = fsrc + 18 * b * N;
-        const float* F2p = F1 + 9 * N;
-        float* D1 = fdst + 18 * b * N;
-        float* D2 = D1 + 9 * N;
+        const typename S::T* F1 = fsrc + 18 * b * N;
+        const typename S::T* F2p = F1 + 9 * N;
+        typename S::T* D1 = fdst + 18 * b * N;
+        typename S::T* D2 = D1 + 9 * N;
         float* uo = u_out + 4 * b * N;
 #pragma unroll 1
         for (int r = ty; r < TY; r += NT / 32) {
@@ -383,7 +387,7 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
                 const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
                 const int sy = d2q9_cy(i) == 0 ? y : (d2q9_cy(i) > 0 ? ym : yp);
                 const long long src = (long long)sy * nx + sx;
-                f[i] = P2(F1[i * N + src], F2p[i * N + src]);
+                f[i] = P2(S::load(F1 + i * N + src), S::load(F2p + i * N + src));
             }
             f2 u1, u2;
             lbm_site2(P, phi[c], P2(phi[c - 1], phi[c + 1]), P2(phi[c - W], phi[c + W]), mu[c],
@@ -393,8 +397,8 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
             const long long g = (long long)y * nx + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                D1[i * N + g] = f[i].x;
-                D2[i * N + g] = f[i].y;
+                S::store(D1 + i * N + g, f[i].x);
+                S::store(D2 + i * N + g, f[i].y);
             }
             uo[g] = u1.x;
             uo[N + g] = u1.y;
@@ -418,21 +422,41 @@ k_fused(const float* __restrict__ fsrc, float* __restrict__ fdst,
     }
 }
 
-template <bool DO_FD, bool DO_LBM>
-cudaError_t configure() {
-    return cudaFuncSetAttribute(k_fused<DO_FD, DO_LBM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <bool DO_FD, bool DO_LBM, class S>
+cudaError_t configure_one() {
+    return cudaFuncSetAttribute(k_fused<DO_FD, DO_LBM, S>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geo<DO_FD, DO_LBM>::SMEM);
+}
+
+template <class S>
+cudaError_t configure() {
+    cudaError_t e = configure_one<true, true, S>();
+    if (e == cudaSuccess) e = configure_one<false, true, S>();
+    if (e == cudaSuccess) e = configure_one<true, false, S>();
+    return e;
+}
+
+template <bool DO_FD, bool DO_LBM, class S>
+void launch_as(tf_ctx* ctx) {
+    using G = Geo<DO_FD, DO_LBM>;
+    using T = typename S::T;
+    DevBuffers& d = ctx->d;
+    const dim3 grid((ctx->nx + TX - 1) / TX, (ctx->ny + TY - 1) / TY, ctx->batch);
+    const int fc = ctx->fcur, pc = ctx->pcur, uc = ctx->ucur;
+    k_fused<DO_FD, DO_LBM, S><<<grid, NT, G::SMEM, ctx->stream>>>(
+        static_cast<const T*>(d.f[fc]), static_cast<T*>(d.f[fc ^ 1]), d.phi[pc], d.phi[pc ^ 1],
+        d.Q[pc], d.Q[pc ^ 1], d.u[uc], d.u[uc ^ 1], d.prm, ctx->nx, ctx->ny, d.flags);
 }
 
 template <bool DO_FD, bool DO_LBM>
 cudaError_t launch(tf_ctx* ctx) {
-    using G = Geo<DO_FD, DO_LBM>;
-    DevBuffers& d = ctx->d;
-    const dim3 grid((ctx->nx + TX - 1) / TX, (ctx->ny + TY - 1) / TY, ctx->batch);
-    const int fc = ctx->fcur, pc = ctx->pcur, uc = ctx->ucur;
-    k_fused<DO_FD, DO_LBM><<<grid, NT, G::SMEM, ctx->stream>>>(
-        d.f[fc], d.f[fc ^ 1], d.phi[pc], d.phi[pc ^ 1], d.Q[pc], d.Q[pc ^ 1], d.u[uc],
-        d.u[uc ^ 1], d.prm, ctx->nx, ctx->ny, d.flags);
+    if (ctx->storage == TF_STORE_F16)
+        launch_as<DO_FD, DO_LBM, PopF16>(ctx);
+    else if (ctx->storage == TF_STORE_BF16)
+        launch_as<DO_FD, DO_LBM, PopBF16>(ctx);
+    else
+        launch_as<DO_FD, DO_LBM, PopF32>(ctx);
     if (DO_LBM) {
         ctx->fcur ^= 1;
         ctx->ucur ^= 1;
@@ -447,9 +471,9 @@ cudaError_t launch(tf_ctx* ctx) {
 bool tf_fused_supported(const tf_ctx* ctx) { return ctx->n_sub == NS_FUSED; }
 
 cudaError_t tf_configure_fused_kernels() {
-    cudaError_t e = configure<true, true>();
-    if (e == cudaSuccess) e = configure<false, true>();
-    if (e == cudaSuccess) e = configure<true, false>();
+    cudaError_t e = configure<PopF32>();
+    if (e == cudaSuccess) e = configure<PopF16>();
+    if (e == cudaSuccess) e = configure<PopBF16>();
     return e;
 }
 

@@ -2,6 +2,8 @@
 // Not part of the public ABI (see include/twofluid.h).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -28,6 +30,49 @@ __host__ __device__ constexpr double d2q9_wd(int i) {
     return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
+// ---------------------------------------------------------------------------
+// Population storage (TF_STORE_*): the stored value is the deviation
+// d_i = f_i - w_i, widened to FP32 on load and rounded to nearest on store.
+// FP16 carries d_i * 2^12 (an exact scale both ways) so that deviations down
+// to 1.5e-8 stay normal.  Zero bits are d_i = 0 in every mode.
+// ---------------------------------------------------------------------------
+struct PopF32 {
+    typedef float T;
+    static constexpr int kMode = TF_STORE_F32;
+    __device__ static float load(const T* p) { return *p; }
+    __device__ static void store(T* p, float d) { *p = d; }
+};
+struct PopF16 {
+    typedef __half T;
+    static constexpr int kMode = TF_STORE_F16;
+    __device__ static float load(const T* p) { return __fmul_rn(__half2float(*p), 0x1p-12f); }
+    __device__ static void store(T* p, float d) { *p = __float2half_rn(__fmul_rn(d, 0x1p12f)); }
+};
+struct PopBF16 {
+    typedef __nv_bfloat16 T;
+    static constexpr int kMode = TF_STORE_BF16;
+    __device__ static float load(const T* p) { return __bfloat162float(*p); }
+    __device__ static void store(T* p, float d) { *p = __float2bfloat16_rn(d); }
+};
+
+// Bytes per stored population element.
+inline size_t tf_pop_bytes(int storage) { return storage == TF_STORE_F32 ? 4 : 2; }
+
+// Run-time dispatch for kernels off the hot path (storage uniform per launch).
+__device__ __forceinline__ float pop_load(const void* base, long long i, int storage) {
+    if (storage == TF_STORE_F16) return PopF16::load(static_cast<const __half*>(base) + i);
+    if (storage == TF_STORE_BF16) return PopBF16::load(static_cast<const __nv_bfloat16*>(base) + i);
+    return PopF32::load(static_cast<const float*>(base) + i);
+}
+__device__ __forceinline__ void pop_store(void* base, long long i, float d, int storage) {
+    if (storage == TF_STORE_F16)
+        PopF16::store(static_cast<__half*>(base) + i, d);
+    else if (storage == TF_STORE_BF16)
+        PopBF16::store(static_cast<__nv_bfloat16*>(base) + i, d);
+    else
+        PopF32::store(static_cast<float*>(base) + i, d);
+}
+
 // Per-instance parameters in the form the kernels use (FP32, precomputed).
 // mu(phi_ref + d) = A_ch f'(phi_ref + d) - kappa lap(d) with the cubic
 // A_ch f'(c + d) = mu0 + mu1 d + mu2 d^2 + mu3 d^3 expanded about c.
@@ -43,7 +88,8 @@ struct DevParams {
 
 // Device buffers carved out of the caller's workspace.
 struct DevBuffers {
-    float* f[2];       // populations [B][18][N] (pull layout: post-collision of the previous step)
+    void* f[2];        // populations [B][18][N] in the storage type (pull layout:
+                       // post-collision deviations of the previous step)
     float* phi[2];     // phi - phi_ref  [B][N]
     float* Q[2];       // Q_xx, Q_xy     [B][2][N]
     float* u[2];       // u1x, u1y, u2x, u2y [B][4][N]

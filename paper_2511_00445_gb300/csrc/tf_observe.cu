@@ -64,9 +64,9 @@ __global__ void __launch_bounds__(RB) k_finish(const double* __restrict__ part, 
 
 // ---------------------------------------------------------------- init
 __global__ void __launch_bounds__(RB)
-k_init(float* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q, long long N, int b0,
+k_init(void* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q, long long N, int b0,
        int b1, uint64_t seed, double phi0, double dphi, double S0,
-       const DevParams* __restrict__ prm) {
+       const DevParams* __restrict__ prm, int storage) {
     const long long i = (long long)blockIdx.x * RB + threadIdx.x;
     if (i >= N) return;
     const double up = uniform01(seed, 0, i);
@@ -79,8 +79,9 @@ k_init(float* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q, lo
         Q[2 * b * N + i] = (float)(S0 * cs);
         Q[(2 * b + 1) * N + i] = (float)(S0 * sn);
         for (int k = 0; k < 9; ++k) {
-            f[(18 * b + k) * N + i] = (float)(d2q9_wd(k) * ((double)P.rho1 - 1.0));
-            f[(18 * b + 9 + k) * N + i] = (float)(d2q9_wd(k) * ((double)P.rho2 - 1.0));
+            pop_store(f, (18 * b + k) * N + i, (float)(d2q9_wd(k) * ((double)P.rho1 - 1.0)), storage);
+            pop_store(f, (18 * b + 9 + k) * N + i, (float)(d2q9_wd(k) * ((double)P.rho2 - 1.0)),
+                      storage);
         }
     }
 }
@@ -89,9 +90,9 @@ k_init(float* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q, lo
 // field: 0 phi, 1 Qxx, 2 Qxy, 16+i / 32+i populations (given pre-collision
 // f_i(x); stored at x - c_i in the pull layout).
 __global__ void __launch_bounds__(RB)
-k_write(float* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q,
+k_write(void* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q,
         const double* __restrict__ src, int nx, int ny, int b, int field,
-        const DevParams* __restrict__ prm) {
+        const DevParams* __restrict__ prm, int storage) {
     const long long N = (long long)nx * ny;
     const long long i = (long long)blockIdx.x * RB + threadIdx.x;
     if (i >= N) return;
@@ -105,13 +106,14 @@ k_write(float* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q,
         const int k = field - (fl ? TF_FIELD_F2 : TF_FIELD_F1);
         const int x = (int)(i % nx), y = (int)(i / nx);
         const int sx = tfd::wrap(x - d2q9_cx(k), nx), sy = tfd::wrap(y - d2q9_cy(k), ny);
-        f[(18 * b + 9 * fl + k) * N + (long long)sy * nx + sx] = (float)(v - d2q9_wd(k));
+        pop_store(f, (18 * b + 9 * fl + k) * N + (long long)sy * nx + sx, (float)(v - d2q9_wd(k)),
+                  storage);
     }
 }
 
 __global__ void __launch_bounds__(RB)
-k_set_eq(float* __restrict__ f, const double* __restrict__ u1, const double* __restrict__ u2,
-         int nx, int ny, int b, const DevParams* __restrict__ prm) {
+k_set_eq(void* __restrict__ f, const double* __restrict__ u1, const double* __restrict__ u2,
+         int nx, int ny, int b, const DevParams* __restrict__ prm, int storage) {
     const long long N = (long long)nx * ny;
     const long long i = (long long)blockIdx.x * RB + threadIdx.x;
     if (i >= N) return;
@@ -126,16 +128,16 @@ k_set_eq(float* __restrict__ f, const double* __restrict__ u1, const double* __r
             const double w = d2q9_wd(k);
             const double dev = w * (rho - 1.0) + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
             const int sx = tfd::wrap(x - d2q9_cx(k), nx), sy = tfd::wrap(y - d2q9_cy(k), ny);
-            f[(18 * b + 9 * fl + k) * N + (long long)sy * nx + sx] = (float)dev;
+            pop_store(f, (18 * b + 9 * fl + k) * N + (long long)sy * nx + sx, (float)dev, storage);
         }
     }
 }
 
 // ---------------------------------------------------------- field reads
 __global__ void __launch_bounds__(RB)
-k_read(const float* __restrict__ f, const float* __restrict__ phi, const float* __restrict__ Q,
+k_read(const void* __restrict__ f, const float* __restrict__ phi, const float* __restrict__ Q,
        const float* __restrict__ mac, const float* __restrict__ mu, double* __restrict__ dst,
-       int nx, int ny, int b, int field, const DevParams* __restrict__ prm) {
+       int nx, int ny, int b, int field, const DevParams* __restrict__ prm, int storage) {
     const long long N = (long long)nx * ny;
     const long long i = (long long)blockIdx.x * RB + threadIdx.x;
     if (i >= N) return;
@@ -153,7 +155,8 @@ k_read(const float* __restrict__ f, const float* __restrict__ phi, const float* 
         const int k = field - (fl ? TF_FIELD_F2 : TF_FIELD_F1);
         const int x = (int)(i % nx), y = (int)(i / nx);
         const int sx = tfd::wrap(x - d2q9_cx(k), nx), sy = tfd::wrap(y - d2q9_cy(k), ny);
-        v = d2q9_wd(k) + (double)f[(18 * b + 9 * fl + k) * N + (long long)sy * nx + sx];
+        v = d2q9_wd(k) +
+            (double)pop_load(f, (18 * b + 9 * fl + k) * N + (long long)sy * nx + sx, storage);
     }
     dst[i] = v;
 }
@@ -164,9 +167,9 @@ k_read(const float* __restrict__ f, const float* __restrict__ phi, const float* 
 // non-finite count.  The sum over sites of pulled values equals the sum of
 // stored values, so densities and momenta need no streaming here.
 __global__ void __launch_bounds__(RB)
-k_conserved(const float* __restrict__ f, const float* __restrict__ phi,
+k_conserved(const void* __restrict__ f, const float* __restrict__ phi,
             const float* __restrict__ Q, const float* __restrict__ mac, long long N, int b,
-            double* __restrict__ part) {
+            double* __restrict__ part, int storage) {
     double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < N;
          i += (long long)gridDim.x * RB) {
@@ -174,8 +177,8 @@ k_conserved(const float* __restrict__ f, const float* __restrict__ phi,
         int bad = 0;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            d1[k] = f[(18 * b + k) * N + i];
-            d2[k] = f[(18 * b + 9 + k) * N + i];
+            d1[k] = pop_load(f, (18 * b + k) * N + i, storage);
+            d2[k] = pop_load(f, (18 * b + 9 + k) * N + i, storage);
             bad += !isfinite(d1[k]) + !isfinite(d2[k]);
         }
         const float p = phi[b * N + i], qa = Q[2 * b * N + i], qb = Q[(2 * b + 1) * N + i];
@@ -404,7 +407,7 @@ cudaError_t tf_launch_zero_state(tf_ctx* ctx) {
     const DevBuffers& d = ctx->d;
     const size_t N = (size_t)ctx->N, B = (size_t)ctx->batch;
     for (int k = 0; k < 2; ++k) {
-        cudaMemsetAsync(d.f[k], 0, 18 * B * N * sizeof(float), ctx->stream);
+        cudaMemsetAsync(d.f[k], 0, 18 * B * N * tf_pop_bytes(ctx->storage), ctx->stream);
         cudaMemsetAsync(d.phi[k], 0, B * N * sizeof(float), ctx->stream);
         cudaMemsetAsync(d.Q[k], 0, 2 * B * N * sizeof(float), ctx->stream);
         cudaMemsetAsync(d.u[k], 0, 4 * B * N * sizeof(float), ctx->stream);
@@ -418,7 +421,7 @@ cudaError_t tf_launch_init(tf_ctx* ctx, int inst, uint64_t seed, double phi0, do
     const DevBuffers& d = ctx->d;
     k_init<<<nblk(ctx->N), RB, 0, ctx->stream>>>(d.f[ctx->fcur], d.phi[ctx->pcur],
                                                  d.Q[ctx->pcur], ctx->N, b0, b1, seed, phi0, dphi,
-                                                 S0, d.prm);
+                                                 S0, d.prm, ctx->storage);
     return cudaGetLastError();
 }
 
@@ -426,14 +429,14 @@ cudaError_t tf_launch_write_field(tf_ctx* ctx, int inst, int field, const double
     const DevBuffers& d = ctx->d;
     k_write<<<nblk(ctx->N), RB, 0, ctx->stream>>>(d.f[ctx->fcur], d.phi[ctx->pcur],
                                                   d.Q[ctx->pcur], dsrc, ctx->nx, ctx->ny, inst,
-                                                  field, d.prm);
+                                                  field, d.prm, ctx->storage);
     return cudaGetLastError();
 }
 
 cudaError_t tf_launch_set_equilibrium(tf_ctx* ctx, int inst, const double* du1,
                                       const double* du2) {
     k_set_eq<<<nblk(ctx->N), RB, 0, ctx->stream>>>(ctx->d.f[ctx->fcur], du1, du2, ctx->nx,
-                                                   ctx->ny, inst, ctx->d.prm);
+                                                   ctx->ny, inst, ctx->d.prm, ctx->storage);
     return cudaGetLastError();
 }
 
@@ -445,7 +448,7 @@ cudaError_t tf_launch_read_field(tf_ctx* ctx, int inst, int field, double* ddst)
     }
     k_read<<<nblk(ctx->N), RB, 0, ctx->stream>>>(d.f[ctx->fcur], d.phi[ctx->pcur], d.Q[ctx->pcur],
                                                  d.macro, d.mu, ddst, ctx->nx, ctx->ny, inst,
-                                                 field, d.prm);
+                                                 field, d.prm, ctx->storage);
     return cudaGetLastError();
 }
 
@@ -455,7 +458,7 @@ cudaError_t tf_launch_conserved(tf_ctx* ctx, int inst, double* dout8) {
     if (e != cudaSuccess) return e;
     k_conserved<<<ctx->red_blocks, RB, 0, ctx->stream>>>(d.f[ctx->fcur], d.phi[ctx->pcur],
                                                         d.Q[ctx->pcur], d.macro, ctx->N, inst,
-                                                        d.red_part);
+                                                        d.red_part, ctx->storage);
     k_finish<8><<<1, RB, 0, ctx->stream>>>(d.red_part, ctx->red_blocks, dout8);
     return cudaGetLastError();
 }

@@ -7,7 +7,8 @@
 //   k_sub x n_sub : Cahn-Hilliard + Beris-Edwards forward-Euler sub-step with
 //              the stored velocities
 //
-// Storage: populations as FP32 deviations d_i = f_i - w_i in the pull layout
+// Storage: populations as deviations d_i = f_i - w_i (FP32, or a 16-bit mode
+// widened to FP32 on load, see PopF16 / PopBF16) in the pull layout
 // (the buffer holds post-collision values of the previous step; the
 // pre-collision f_i(x) is read from x - c_i); phi as d = phi - phi_ref.
 #include "tf_device.cuh"
@@ -48,9 +49,9 @@ k_fields(const float* __restrict__ phi, const float* __restrict__ Q, float* __re
 // rho1, rho2 and G1 + G2 into `macro` planes: u1x u1y u2x u2y rho1 rho2 Gx Gy).
 template <int MODE>
 __global__ void __launch_bounds__(BX* BY)
-k_lbm(const float* __restrict__ fsrc, float* __restrict__ fdst, const float* __restrict__ phi,
+k_lbm(const void* __restrict__ fsrc, void* __restrict__ fdst, const float* __restrict__ phi,
       const float* __restrict__ mu, const float* __restrict__ tau, float* __restrict__ u,
-      const DevParams* __restrict__ prm, int nx, int ny) {
+      const DevParams* __restrict__ prm, int nx, int ny, int storage) {
     const int x = blockIdx.x * BX + threadIdx.x;
     const int y = blockIdx.y * BY + threadIdx.y;
     const int b = blockIdx.z;
@@ -71,15 +72,14 @@ k_lbm(const float* __restrict__ fsrc, float* __restrict__ fdst, const float* __r
                         t[e], t[w], t[N + n], t[N + s], t[2 * N + e], t[2 * N + w], t[3 * N + n],
                         t[3 * N + s]);
     float f1[9], f2[9];
-    const float* F1 = fsrc + 18 * b * N;
-    const float* F2 = F1 + 9 * N;
+    const long long F1 = 18 * b * N, F2 = F1 + 9 * N;   // element offsets of the two fluids
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
         const int sy = d2q9_cy(i) == 0 ? y : (d2q9_cy(i) > 0 ? ym : yp);
         const long long src = (long long)sy * nx + sx;
-        f1[i] = F1[i * N + src];
-        f2[i] = F2[i * N + src];
+        f1[i] = pop_load(fsrc, F1 + i * N + src, storage);
+        f2[i] = pop_load(fsrc, F2 + i * N + src, storage);
     }
     float dr1, m1x, m1y, dr2, m2x, m2y;
     tfd::moments(f1, dr1, m1x, m1y);
@@ -95,12 +95,10 @@ k_lbm(const float* __restrict__ fsrc, float* __restrict__ fdst, const float* __r
         u0[3 * N + c] = v.u2y;
         tfd::collide(f1, dr1, v.u1x, v.u1y, v.F1x, v.F1y, P.omega1, P.guo1);
         tfd::collide(f2, dr2, v.u2x, v.u2y, v.F2x, v.F2y, P.omega2, P.guo2);
-        float* D1 = fdst + 18 * b * N;
-        float* D2 = D1 + 9 * N;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            D1[i * N + c] = f1[i];
-            D2[i * N + c] = f2[i];
+            pop_store(fdst, F1 + i * N + c, f1[i], storage);
+            pop_store(fdst, F2 + i * N + c, f2[i], storage);
         }
     } else {
         float* u0 = u + 8 * b * N;
@@ -204,7 +202,7 @@ cudaError_t tf_unfused_steps(tf_ctx* ctx, int64_t n) {
         k_fields<<<grid, block, 0, ctx->stream>>>(d.phi[pc], d.Q[pc], d.mu, d.tau, d.prm, ctx->nx,
                                                   ctx->ny);
         k_lbm<0><<<grid, block, 0, ctx->stream>>>(d.f[fc], d.f[fc ^ 1], d.phi[pc], d.mu, d.tau,
-                                                  d.u[0], d.prm, ctx->nx, ctx->ny);
+                                                  d.u[0], d.prm, ctx->nx, ctx->ny, ctx->storage);
         ctx->fcur ^= 1;
         int p = pc;
         for (int s = 0; s < ctx->n_sub; ++s) {
@@ -225,7 +223,8 @@ cudaError_t tf_launch_macro(tf_ctx* ctx, float* macro_out) {
     k_fields<<<grid, block, 0, ctx->stream>>>(d.phi[ctx->pcur], d.Q[ctx->pcur], d.mu, d.tau, d.prm,
                                               ctx->nx, ctx->ny);
     k_lbm<1><<<grid, block, 0, ctx->stream>>>(d.f[ctx->fcur], nullptr, d.phi[ctx->pcur], d.mu,
-                                              d.tau, macro_out, d.prm, ctx->nx, ctx->ny);
+                                              d.tau, macro_out, d.prm, ctx->nx, ctx->ny,
+                                              ctx->storage);
     ctx->launches += 2;
     return cudaGetLastError();
 }

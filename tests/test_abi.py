@@ -76,6 +76,23 @@ def test_workspace_bytes_host_checks(lib):
     assert lib.tf_workspace_bytes(_arr(good), 0) == 0
 
 
+def test_storage_modes_size_the_workspace(lib):
+    """16-bit population storage halves the two population buffers; the
+    storage constants agree with the header; instances must share a mode."""
+    hdr = open(HEADER).read()
+    consts = dict((k, int(v)) for k, v in re.findall(r"#define (TF_STORE_\w+)\s+(\d+)", hdr))
+    assert consts == {"TF_STORE_F32": B.STORE_F32, "TF_STORE_F16": B.STORE_F16,
+                      "TF_STORE_BF16": B.STORE_BF16}
+    p = B.SolverParams(nx=64, ny=48)
+    n32 = lib.tf_workspace_bytes(_arr(p), 1)
+    n16 = lib.tf_workspace_bytes(_arr(p.with_(storage=B.STORE_F16)), 1)
+    nb16 = lib.tf_workspace_bytes(_arr(p.with_(storage=B.STORE_BF16)), 1)
+    assert n16 == nb16 > 0
+    pops = 2 * 18 * 64 * 48 * 2          # two buffers, 18 planes, 2 bytes saved per element
+    assert n32 - n16 == pops             # every population plane is a multiple of 256 bytes here
+    assert lib.tf_workspace_bytes(_arr(p, p.with_(storage=B.STORE_F16)), 2) == 0
+
+
 def test_create_rejects_bad_workspace_before_any_device_call(lib):
     good = B.SolverParams(nx=16, ny=16)
     arr = _arr(good)
