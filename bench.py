@@ -10,7 +10,12 @@ Beris-Edwards sub-steps).  The state (~44 MB) fits in L2, so L2 is flushed
 CUDA events on the solver's stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sweep256|single1024|single2048] [--storage f32|f16|bf16]
+                    [--workload sweep256|single1024|single2048|ensemble48]
+                    [--storage f32|f16|bf16]
+
+--workload ensemble48 steps 48 instances of three sizes (the parameter-sweep
+ensemble) with the persistent ensemble launch after its autotuner ran, and
+also times the same instances stepped context by context.
 
 --storage f16|bf16 stores the populations as 16-bit deviations (FP32
 arithmetic).  Such a run also times the FP32 storage on the same workload
@@ -52,7 +57,27 @@ WORKLOADS = {
                        name="single 1024x1024, FP32, zeta 0.005, lambda 0.7, K 0.04"),
     "single2048": dict(nx=2048, ny=2048, zetas=[0.005],
                        name="single 2048x2048, FP32, zeta 0.005, lambda 0.7, K 0.04"),
+    # 48 instances: sizes {128, 256, 512}^2 (16 each); parameter combination
+    # c = b mod 27 over zeta x lambda x K (lexicographic); seed b.
+    "ensemble48": dict(nx=512, ny=512, zetas=[0.005], ensemble=True,
+                       name="ensemble of 48: 16 x 128^2 + 16 x 256^2 + 16 x 512^2, FP32, "
+                            "zeta {0.001,0.005,0.01} x lambda {0.3,0.7,1.1} x K {0.02,0.04,0.08}"),
 }
+ENS_ZETA, ENS_LAMBDA, ENS_K = (0.001, 0.005, 0.01), (0.3, 0.7, 1.1), (0.02, 0.04, 0.08)
+
+
+def ensemble_members(B, storage):
+    """Per size group: the instances' parameters and seeds (b = 0..47)."""
+    groups = []
+    for gi, n in enumerate((128, 256, 512)):
+        plist, seeds = [], []
+        for b in range(16 * gi, 16 * gi + 16):
+            c = b % 27
+            plist.append(B.SolverParams(nx=n, ny=n, zeta=ENS_ZETA[c // 9], lam=ENS_LAMBDA[(c // 3) % 3],
+                                        K=ENS_K[c % 3], storage=storage))
+            seeds.append(b)
+        groups.append((plist, seeds))
+    return groups
 
 
 # --------------------------------------------------------------- ranks
@@ -414,6 +439,119 @@ def run_ours(args, wl):
         torch.distributed.destroy_process_group()
 
 
+def run_ensemble(args, wl):
+    """48 instances of three sizes in one persistent launch per K steps
+    (after the autotuner picked the tile shape), against the same instances
+    stepped context by context with one launch per group and step."""
+    import torch
+
+    from paper_2511_00445_gb300 import build as bld
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    bld.build()
+    from paper_2511_00445_gb300 import _binding as B
+    dev = torch.device("cuda", local)
+    storage = B.STORAGE_NAMES[args.storage]
+    spec = ensemble_members(B, storage)
+
+    def make():
+        grp = []
+        for plist, seeds in spec:
+            tf = B.TwoFluid(plist, device=dev)
+            for k, sd in enumerate(seeds):
+                tf.init_fields(seed=rank_seed(sd, rank), phi0=0.5, dphi=0.01, S0=0.01, inst=k)
+            grp.append(tf)
+        return grp
+    sites = sum(p.nx * p.ny for plist, _ in spec for p in plist)
+    grp = make()
+    ens = B.Ensemble(grp)
+    ens.autotune(max(2, min(8, args.warmup)))
+    ens.step(args.warmup)
+    ens.sync()
+    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    l0 = ens.launches()
+    with torch.cuda.stream(ens.stream):
+        a.record(ens.stream)
+        ens.step(args.steps)
+        b.record(ens.stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    launches = ens.launches() - l0
+    clk = clocks.stop()
+    ens.sync()
+    sec = reduce_max(a.elapsed_time(b) / 1e3, world, dev)
+    value, _ = aggregate([sec] * world, sites, args.steps)
+    cfg = ens.config()
+    c = grp[2].conserved(0)
+    ens.close()
+    for tf in grp:
+        tf.close()
+
+    # The same instances stepped per context: one launch per group and step.
+    grp = make()
+    for tf in grp:
+        tf.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(grp[0].stream):
+        a2.record(grp[0].stream)
+        for _ in range(args.steps):
+            for tf in grp:
+                tf.step(1)
+        b2.record(grp[0].stream)
+    torch.cuda.synchronize(dev)
+    sec_pc = reduce_max(a2.elapsed_time(b2) / 1e3, world, dev)
+    value_pc, _ = aggregate([sec_pc] * world, sites, args.steps)
+    for tf in grp:
+        tf.close()
+
+    peak, peak_kind = measured_peaks()
+    bps = BYTES_PER_SITE[args.storage]
+    achieved = bps * sites / (sec / args.steps) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "k_ens (persistent, all steps in one launch)", "bytes_per_site": bps,
+                "launches_per_step": launches / args.steps}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        mlups, n, el = oracle_sample(256, 256, 0.005, 0, budget_s=args.cpu_seconds)
+        cpu = {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 numpy oracle, one 256x256 member of the ensemble, {n} steps "
+                         f"({el:.1f} s) after one warm-up step"}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded SplitMix64 initial condition of Sec. III, seed = member index)",
+            "config": {"workload": wl["name"], "sites_per_step": sites, "instances": 48,
+                       "storage": args.storage,
+                       "l2": "not flushed: the state (~1.2 GB) is far larger than L2",
+                       "timing": "CUDA events around the one persistent launch of all K steps",
+                       "autotuned": cfg},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": None, "clocks": clk, "gpu_launches": launches,
+            "per_context": {"value": value_pc, "unit": UNIT,
+                            "how": "same 48 instances as 3 contexts, one launch per context and step",
+                            "ensemble_speedup": value / value_pc},
+            "state_check": {"nonfinite": c[7], "sum_phi": c[0]},
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +572,8 @@ def main(argv=None):
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif wl.get("ensemble"):
+        run_ensemble(args, wl)
     else:
         run_ours(args, wl)
 

@@ -202,6 +202,73 @@ int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out);
 int tf_save(tf_ctx* ctx, const char* path);
 int tf_load(tf_ctx* ctx, const char* path);
 
+/* ---- ensembles: several contexts stepped by one persistent launch ----- */
+/* The paper explores its parameters (activity zeta, tumbling lambda, Frank
+ * constant K; Sec. IV) through many separate runs; it has no counterpart to
+ * this batching layer.  An ensemble steps several contexts ("groups", each a
+ * batch of instances sharing one grid size) together: one lattice step of
+ * every member instance is one pass of a persistent cooperative kernel over
+ * a ragged work-list of 32 x TY tiles that CTAs take in turn from an atomic
+ * counter, and one launch runs many steps separated by a grid barrier.  Every
+ * wait in that kernel is bounded; a wait that runs out stops the launch and
+ * reports TF_ERR_TIMEOUT through the members' tf_sync.  A launch shape seen
+ * before is replayed from a cached CUDA graph.
+ *
+ * The ensemble does not own the members' state: between ensemble calls the
+ * members' own entry points (tf_read_field, observables, tf_save, ...) see
+ * the current state, and reads complete pending sub-steps exactly as for a
+ * context stepped alone (trajectories are bitwise the same either way).
+ * Members must not be stepped through tf_step or tf_advance_host, nor
+ * destroyed, while the ensemble exists. */
+typedef struct tf_ensemble tf_ensemble;
+#define TF_ENS_MAX_GROUPS 64
+#define TF_ENS_CANDIDATES 6    /* autotuner candidates, see tf_ensemble_config */
+
+/* Device workspace bytes for an ensemble of n_groups (1..64) groups; 0 when
+ * n_groups is out of range. */
+size_t tf_ensemble_workspace_bytes(int n_groups);
+
+/* Group n_groups contexts.  Every member must use n_sub = 5 (the fused
+ * step), the same storage mode, and `stream` as its stream.  Pending
+ * sub-steps of the members are completed first.  `d_workspace`: at least
+ * tf_ensemble_workspace_bytes(n_groups) bytes, 256-byte aligned, caller-owned,
+ * alive until tf_ensemble_destroy.  Starts with tile height 32 and two CTAs
+ * per SM. */
+int tf_ensemble_create(tf_ctx* const* groups, int n_groups, void* d_workspace,
+                       size_t workspace_bytes, void* stream, tf_ensemble** out);
+int tf_ensemble_destroy(tf_ensemble* ens);
+const char* tf_ensemble_last_error(const tf_ensemble* ens);
+
+/* Advance every member instance by n >= 0 steps: an LBM-only first pass
+ * when the members hold a completed state, then ONE persistent launch for
+ * the remaining steps.  Asynchronous on the ensemble's stream. */
+int tf_ensemble_step(tf_ensemble* ens, int64_t n);
+
+/* Wait for the ensemble's work and report the members' device status
+ * (TF_ERR_TIMEOUT after a bounded wait ran out). */
+int tf_ensemble_sync(tf_ensemble* ens);
+
+/* Tile-shape autotuner: candidate k = 0..5 is tile height {32, 24, 16}[k/2]
+ * with {2, 1}[k%2] resident CTAs per SM.  Each candidate runs one launch of
+ * `steps_per_candidate` (>= 1) real steps timed with CUDA events; the fastest
+ * becomes the configuration.  Every candidate computes bitwise the same
+ * trajectory, so the tuning steps are ordinary steps: the ensemble advances
+ * by 6 * steps_per_candidate steps (plus the first pass if one is due).
+ * Synchronous. */
+int tf_ensemble_autotune(tf_ensemble* ens, int steps_per_candidate);
+
+/* Current configuration: tile height, CTAs per SM, grid size of the
+ * persistent launch, tiles per step; us_per_step (may be NULL) receives the
+ * TF_ENS_CANDIDATES autotuner timings in microseconds per step (0 before
+ * tf_ensemble_autotune).  *graphs = 1 when launches replay CUDA graphs, 0
+ * when they are issued directly (stream capture unavailable). */
+int tf_ensemble_config(const tf_ensemble* ens, int* tile_y, int* ctas_per_sm, int* grid,
+                       int64_t* tiles_per_step, double* us_per_step, int* graphs);
+
+/* Kernel launches issued by this ensemble so far (a graph replay counts its
+ * one kernel). */
+int64_t tf_ensemble_launches(const tf_ensemble* ens);
+
 /* ---- fixed-footprint entry point ------------------------------------- */
 /* The paper has no counterpart to this call; it exists for integration.
  *

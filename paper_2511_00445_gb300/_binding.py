@@ -42,8 +42,12 @@ EXPORTS = [
     "tf_write_field", "tf_set_equilibrium", "tf_read_field", "tf_step", "tf_sync",
     "tf_step_count", "tf_kernel_launches", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
     "tf_length_scale", "tf_energy_spectrum", "tf_phase_difference", "tf_phi_stats",
-    "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load", "tf_phi_stats_noalloc",
+    "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load",
+    "tf_ensemble_workspace_bytes", "tf_ensemble_create", "tf_ensemble_destroy",
+    "tf_ensemble_last_error", "tf_ensemble_step", "tf_ensemble_sync", "tf_ensemble_autotune",
+    "tf_ensemble_config", "tf_ensemble_launches", "tf_phi_stats_noalloc",
 ]
+ENS_CANDIDATES = 6
 
 
 class TFParams(ctypes.Structure):
@@ -140,6 +144,16 @@ def load_library() -> ctypes.CDLL:
         "tf_advance_host": (i, [vp, vp, i64, vp]),
         "tf_save": (i, [vp, ctypes.c_char_p]),
         "tf_load": (i, [vp, ctypes.c_char_p]),
+        "tf_ensemble_workspace_bytes": (sz, [i]),
+        "tf_ensemble_create": (i, [ctypes.POINTER(vp), i, vp, sz, vp, ctypes.POINTER(vp)]),
+        "tf_ensemble_destroy": (i, [vp]),
+        "tf_ensemble_last_error": (ctypes.c_char_p, [vp]),
+        "tf_ensemble_step": (i, [vp, i64]),
+        "tf_ensemble_sync": (i, [vp]),
+        "tf_ensemble_autotune": (i, [vp, i]),
+        "tf_ensemble_config": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                   ctypes.POINTER(i64), dp, ctypes.POINTER(i)]),
+        "tf_ensemble_launches": (i64, [vp]),
         "tf_phi_stats_noalloc": (i, [vp, ctypes.c_longlong, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -293,3 +307,67 @@ class TwoFluid:
 
     def load(self, path: str):
         self._check(self.lib.tf_load(self.ctx, path.encode()))
+
+
+class Ensemble:
+    """Several TwoFluid groups (each one grid size) stepped by one persistent
+    launch per call, behind the tf_ensemble_* entry points.  The groups keep
+    their own state and observables; they must share the ensemble's stream
+    and must not be stepped on their own while the ensemble exists."""
+
+    def __init__(self, groups: Sequence[TwoFluid]):
+        import torch
+        self.lib = load_library()
+        self.groups = list(groups)
+        n = len(self.groups)
+        nbytes = self.lib.tf_ensemble_workspace_bytes(n)
+        if nbytes == 0:
+            raise TwoFluidError(TF_ERR_ARG, "bad group count")
+        self.stream = self.groups[0].stream
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.groups[0].device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        arr = (ctypes.c_void_p * n)(*[g.ctx.value for g in self.groups])
+        ens = ctypes.c_void_p()
+        rc = self.lib.tf_ensemble_create(arr, n, ctypes.c_void_p(aligned), nbytes,
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ens))
+        if rc != TF_OK:
+            raise TwoFluidError(rc, "tf_ensemble_create failed")
+        self.ens = ens
+
+    def _check(self, rc: int):
+        if rc != TF_OK:
+            raise TwoFluidError(rc, self.lib.tf_ensemble_last_error(self.ens).decode())
+
+    def close(self):
+        if getattr(self, "ens", None):
+            self.lib.tf_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n: int = 1):
+        self._check(self.lib.tf_ensemble_step(self.ens, n))
+
+    def sync(self):
+        self._check(self.lib.tf_ensemble_sync(self.ens))
+
+    def autotune(self, steps_per_candidate: int = 4):
+        self._check(self.lib.tf_ensemble_autotune(self.ens, steps_per_candidate))
+
+    def config(self) -> dict:
+        ty, cps, grid, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        tiles = ctypes.c_int64()
+        us = np.zeros(ENS_CANDIDATES)
+        self._check(self.lib.tf_ensemble_config(self.ens, ctypes.byref(ty), ctypes.byref(cps),
+                                                ctypes.byref(grid), ctypes.byref(tiles), _dptr(us),
+                                                ctypes.byref(gr)))
+        return {"tile_y": ty.value, "ctas_per_sm": cps.value, "grid": grid.value,
+                "tiles_per_step": tiles.value, "us_per_step": us.tolist(), "graphs": bool(gr.value),
+                "note": self.lib.tf_ensemble_last_error(self.ens).decode()}
+
+    def launches(self) -> int:
+        return int(self.lib.tf_ensemble_launches(self.ens))

@@ -1,0 +1,533 @@
+// Ensembles (declared in include/twofluid.h): several contexts of possibly
+// different grid sizes stepped together by one persistent cooperative kernel.
+//
+// Work-list: tile t of a step is found by scanning the groups' first-tile
+// offsets (per tile height); within a group the tiles are numbered instance
+// by instance, row-major.  CTAs take tiles from a per-step atomic ticket
+// counter (dynamic balance across uneven instance sizes), run the same
+// per-tile code as the per-context kernel (tf_fused.cuh), and meet at a grid
+// barrier between steps.  Every spin is bounded; a CTA that gives up raises
+// the abort word so that the others leave too, and the code lands in the
+// members' device status words.
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tf_fused.cuh"
+
+namespace {
+
+constexpr int kTileY[3] = {32, 24, 16};       // candidate tile heights
+constexpr int kCandidates = TF_ENS_CANDIDATES; // tile height x CTAs per SM {2, 1}
+constexpr uint32_t kBarrierPolls = 1u << 23;   // x ~128 ns sleeps: about one second
+constexpr int64_t kMaxStepsPerLaunch = 1024;
+
+struct EnsGroup {
+    void* f[2];              // population buffers: [0] = the group's current one at ensemble parity 0
+    float* phi[2];
+    float* Q[2];
+    float* u[2];
+    const DevParams* prm;
+    int* err;                // the group's device status word
+    int nx, ny, batch, tiles_x;
+    long long begin[3];      // first tile of the group for tile heights 32, 24, 16
+};
+
+struct EnsCtl {
+    unsigned int ticket[2];  // per-step tile counters (steps alternate)
+    unsigned int arrive;     // grid-barrier arrivals
+    unsigned int gen;        // grid-barrier generation
+    int abort;               // set by a CTA that gave up a wait
+    int pad[3];
+};
+
+template <int TY>
+constexpr int ty_index() {
+    return TY == 32 ? 0 : (TY == 24 ? 1 : 2);
+}
+
+// All CTAs of the launch meet here.  Thread 0 of each CTA arrives on a
+// global counter; the last arrival resets the counter and the finished
+// step's ticket slot, then bumps the generation the others spin on.
+__device__ __forceinline__ bool grid_barrier(EnsCtl* ctl, int k, int* err) {
+    __shared__ int s_ok;
+    // Next step reads this step's stores through bulk copies (async proxy).
+    tfp::fence_proxy_async_global();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int gen = *reinterpret_cast<volatile unsigned int*>(&ctl->gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&ctl->arrive, 1u);
+        if (arrived == gridDim.x - 1) {
+            ctl->arrive = 0;
+            ctl->ticket[k & 1] = 0;
+            __threadfence();
+            atomicAdd(&ctl->gen, 1u);
+        } else {
+            uint32_t it = 0;
+            while (*reinterpret_cast<volatile unsigned int*>(&ctl->gen) == gen) {
+                if (*reinterpret_cast<volatile int*>(&ctl->abort)) {
+                    ok = 0;
+                    break;
+                }
+                if (++it > kBarrierPolls) {
+                    atomicExch(err, TF_ERR_TIMEOUT);
+                    atomicExch(&ctl->abort, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    tfp::fence_proxy_async_global();
+    return s_ok != 0;
+}
+
+// `steps` lattice steps of every tile of every group.  Parities fpar, ppar,
+// upar select the current population, phi/Q and velocity buffers at step 0;
+// each step flips the ones it writes.
+template <bool DO_FD, bool DO_LBM, class S, int TY>
+__global__ void __launch_bounds__(NT, 2)
+k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int steps, int fpar,
+      int ppar, int upar, EnsCtl* ctl) {
+    constexpr int TI = ty_index<TY>();
+    using T = typename S::T;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ long long s_ticket;
+    if (threadIdx.x == 0) {
+        tfp::mbar_init(&bar, 1);
+        tfp::fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (int k = 0; k < steps; ++k) {
+        const int fp = fpar ^ (DO_LBM ? (k & 1) : 0);
+        const int pp = ppar ^ (DO_FD ? (k & 1) : 0);
+        const int up = upar ^ (DO_LBM ? (k & 1) : 0);
+        for (;;) {
+            if (threadIdx.x == 0)
+                s_ticket = *reinterpret_cast<volatile int*>(&ctl->abort)
+                               ? total
+                               : (long long)atomicAdd(&ctl->ticket[k & 1], 1u);
+            __syncthreads();
+            const long long t = s_ticket;
+            __syncthreads();
+            if (t >= total) break;
+            int g = 0;
+            while (g + 1 < n_groups && groups[g + 1].begin[TI] <= t) ++g;
+            const EnsGroup& G = groups[g];
+            const long long local = t - G.begin[TI];
+            const long long per = (long long)G.tiles_x * ((G.ny + TY - 1) / TY);
+            const int b = (int)(local / per);
+            const long long r = local - (long long)b * per;
+            const int tyi = (int)(r / G.tiles_x), txi = (int)(r - (long long)tyi * G.tiles_x);
+            const TileArgs<S> a{static_cast<const T*>(G.f[fp]), static_cast<T*>(G.f[fp ^ 1]),
+                                G.phi[pp], G.phi[pp ^ 1], G.Q[pp], G.Q[pp ^ 1], G.u[up],
+                                G.u[up ^ 1], G.prm, G.nx, G.ny, G.err};
+            if (!fused_tile<DO_FD, DO_LBM, S, TY, true>(a, b, txi * TX, tyi * TY, &bar, phase)) {
+                if (threadIdx.x == 0) atomicExch(&ctl->abort, 1);
+                return;
+            }
+            if ((G.nx & 3) == 0) ++phase;   // the tile went through the mbarrier
+            __syncthreads();
+        }
+        if (k + 1 < steps && !grid_barrier(ctl, k, groups[0].err)) return;
+    }
+}
+
+enum Mode { kPrologue = 0, kSteady = 1 };
+
+typedef void (*EnsKernel)(const EnsGroup*, int, long long, int, int, int, int, EnsCtl*);
+
+template <class S>
+EnsKernel pick(int mode, int ti) {
+    if (mode == kPrologue) return k_ens<false, true, S, 32>;
+    if (ti == 0) return k_ens<true, true, S, 32>;
+    if (ti == 1) return k_ens<true, true, S, 24>;
+    return k_ens<true, true, S, 16>;
+}
+
+EnsKernel kernel_for(int storage, int mode, int ti) {
+    if (storage == TF_STORE_F16) return pick<PopF16>(mode, ti);
+    if (storage == TF_STORE_BF16) return pick<PopBF16>(mode, ti);
+    return pick<PopF32>(mode, ti);
+}
+
+size_t smem_for(int mode, int ti) {
+    if (mode == kPrologue) return Geo<false, true, 32>::SMEM;
+    if (ti == 0) return Geo<true, true, 32>::SMEM;
+    if (ti == 1) return Geo<true, true, 24>::SMEM;
+    return Geo<true, true, 16>::SMEM;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct tf_ensemble {
+    std::vector<tf_ctx*> groups;
+    std::vector<int> base_f, base_p, base_u;   // member buffer index at ensemble parity 0
+    std::vector<EnsGroup> host_groups;
+    cudaStream_t stream = nullptr;
+    int storage = TF_STORE_F32;
+    EnsGroup* d_groups = nullptr;
+    EnsCtl* d_ctl = nullptr;
+    long long tiles[3] = {0, 0, 0};
+    int cfg = 0;                               // autotuner candidate in use
+    int fpar = 0, ppar = 0, upar = 0;
+    bool pending = false;                      // sub-steps of the last step not yet applied
+    int sm_count = 0;
+    double us[kCandidates] = {};
+    bool graphs = true;
+    std::map<std::tuple<int, int64_t, int, int, int, int>, cudaGraphExec_t> cache;
+    int64_t launches = 0;
+    std::string last_error;
+};
+
+namespace {
+
+int efail(tf_ensemble* e, int code, const std::string& msg) {
+    if (e) e->last_error = msg;
+    return code;
+}
+
+int efail_cuda(tf_ensemble* e, const char* where, cudaError_t err) {
+    return efail(e, TF_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(err));
+}
+
+#define TF_ECK(e, call)                                          \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return efail_cuda(e, #call, e_);  \
+    } while (0)
+
+int grid_for(tf_ensemble* e, int mode, int cfg) {
+    const int ti = mode == kPrologue ? 0 : cfg / 2;
+    const int want = mode == kPrologue ? 2 : 2 - cfg % 2;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(e->storage, mode, ti), NT,
+                                                      smem_for(mode, ti)) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    long long g = (long long)(want < per_sm ? want : per_sm) * e->sm_count;
+    const long long tiles = e->tiles[ti];
+    return (int)(g < tiles ? g : tiles);
+}
+
+// Zero the control block, then one cooperative launch of `steps` steps on
+// `grid` CTAs (grid_for; computed outside any stream capture).
+cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid) {
+    const int ti = mode == kPrologue ? 0 : cfg / 2;
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    cudaError_t err = cudaMemsetAsync(e->d_ctl, 0, sizeof(EnsCtl), e->stream);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(NT);
+    lc.dynamicSmemBytes = smem_for(mode, ti);
+    lc.stream = e->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    const EnsGroup* g = e->d_groups;
+    const int ng = (int)e->groups.size();
+    const long long total = e->tiles[ti];
+    return cudaLaunchKernelEx(&lc, kernel_for(e->storage, mode, ti), g, ng, total, steps, e->fpar,
+                              e->ppar, e->upar, e->d_ctl);
+}
+
+// Issue one launch, from the graph cache when this shape was captured before.
+int issue(tf_ensemble* e, int mode, int steps) {
+    const auto key = std::make_tuple(mode, (int64_t)steps, e->fpar, e->ppar, e->upar,
+                                     mode == kPrologue ? 0 : e->cfg);
+    const int grid = grid_for(e, mode, e->cfg);
+    auto it = e->cache.find(key);
+    if (it != e->cache.end()) {
+        TF_ECK(e, cudaGraphLaunch(it->second, e->stream));
+    } else {
+        bool done = false;
+        if (e->graphs) {
+            cudaGraph_t graph = nullptr;
+            cudaError_t e0 = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+            cudaError_t e1 = cudaErrorUnknown, e2 = cudaErrorUnknown, e3 = cudaErrorUnknown;
+            if (e0 == cudaSuccess) {
+                e1 = enqueue(e, mode, steps, e->cfg, grid);
+                e2 = cudaStreamEndCapture(e->stream, &graph);
+                cudaGraphExec_t exec = nullptr;
+                if (e1 == cudaSuccess && e2 == cudaSuccess && graph) {
+                    e3 = cudaGraphInstantiate(&exec, graph, 0);
+                    if (e3 == cudaSuccess) {
+                        e->cache[key] = exec;
+                        TF_ECK(e, cudaGraphLaunch(exec, e->stream));
+                        done = true;
+                    }
+                }
+                if (graph) cudaGraphDestroy(graph);
+            }
+            if (!done) {
+                // Launch directly from now on; keep the reason for tf_ensemble_last_error.
+                const cudaError_t why = e0 != cudaSuccess ? e0 : (e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3));
+                e->last_error = std::string("graph capture unavailable (") +
+                                (e0 != cudaSuccess ? "begin" : e1 != cudaSuccess ? "launch" : e2 != cudaSuccess ? "end" : "instantiate") +
+                                "): " + cudaGetErrorString(why);
+                cudaGetLastError();
+                e->graphs = false;
+            }
+        }
+        if (!done) TF_ECK(e, enqueue(e, mode, steps, e->cfg, grid));
+    }
+    e->launches += 1;
+    if (mode == kPrologue) {
+        e->fpar ^= 1;
+        e->upar ^= 1;
+        e->pending = true;
+    } else {
+        e->fpar ^= steps & 1;
+        e->ppar ^= steps & 1;
+        e->upar ^= steps & 1;
+    }
+    return TF_OK;
+}
+
+// Members' host-side state mirrors the ensemble's after every call.
+void publish(tf_ensemble* e, int64_t steps) {
+    for (size_t g = 0; g < e->groups.size(); ++g) {
+        tf_ctx* c = e->groups[g];
+        c->fcur = e->base_f[g] ^ e->fpar;
+        c->pcur = e->base_p[g] ^ e->ppar;
+        c->ucur = e->base_u[g] ^ e->upar;
+        c->fd_pending = e->pending;
+        c->steps += steps;
+    }
+}
+
+// (Re)build the descriptors from the members' current buffers, completing
+// every member's pending sub-steps first, and upload them.
+int normalise(tf_ensemble* e) {
+    for (tf_ctx* c : e->groups) TF_ECK(e, tf_launch_flush(c));
+    long long begin[3] = {0, 0, 0};
+    for (size_t g = 0; g < e->groups.size(); ++g) {
+        tf_ctx* c = e->groups[g];
+        DevBuffers& d = c->d;
+        EnsGroup& G = e->host_groups[g];
+        e->base_f[g] = c->fcur;
+        e->base_p[g] = c->pcur;
+        e->base_u[g] = c->ucur;
+        for (int k = 0; k < 2; ++k) {
+            G.f[k] = d.f[c->fcur ^ k];
+            G.phi[k] = d.phi[c->pcur ^ k];
+            G.Q[k] = d.Q[c->pcur ^ k];
+            G.u[k] = d.u[c->ucur ^ k];
+        }
+        G.prm = d.prm;
+        G.err = d.flags;
+        G.nx = c->nx;
+        G.ny = c->ny;
+        G.batch = c->batch;
+        G.tiles_x = (c->nx + TX - 1) / TX;
+        for (int ti = 0; ti < 3; ++ti) {
+            G.begin[ti] = begin[ti];
+            begin[ti] += (long long)c->batch * G.tiles_x * ((c->ny + kTileY[ti] - 1) / kTileY[ti]);
+        }
+    }
+    for (int ti = 0; ti < 3; ++ti) e->tiles[ti] = begin[ti];
+    TF_ECK(e, cudaMemcpyAsync(e->d_groups, e->host_groups.data(),
+                              e->host_groups.size() * sizeof(EnsGroup), cudaMemcpyHostToDevice,
+                              e->stream));
+    TF_ECK(e, cudaStreamSynchronize(e->stream));   // host_groups may change on the next call
+    e->fpar = e->ppar = e->upar = 0;
+    e->pending = false;
+    return TF_OK;
+}
+
+// A member read between ensemble calls completes its own pending sub-steps;
+// then the members no longer agree with the ensemble's parities.
+bool members_in_step(const tf_ensemble* e) {
+    for (size_t g = 0; g < e->groups.size(); ++g) {
+        const tf_ctx* c = e->groups[g];
+        if (c->fd_pending != e->pending || c->fcur != (e->base_f[g] ^ e->fpar) ||
+            c->pcur != (e->base_p[g] ^ e->ppar) || c->ucur != (e->base_u[g] ^ e->upar))
+            return false;
+    }
+    return true;
+}
+
+template <bool DO_FD, bool DO_LBM, class S, int TY>
+cudaError_t set_smem() {
+    return cudaFuncSetAttribute(k_ens<DO_FD, DO_LBM, S, TY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Geo<DO_FD, DO_LBM, TY>::SMEM);
+}
+
+template <class S>
+cudaError_t configure_storage() {
+    cudaError_t e = set_smem<false, true, S, 32>();
+    if (e == cudaSuccess) e = set_smem<true, true, S, 32>();
+    if (e == cudaSuccess) e = set_smem<true, true, S, 24>();
+    if (e == cudaSuccess) e = set_smem<true, true, S, 16>();
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tf_ensemble_workspace_bytes(int n_groups) {
+    if (n_groups < 1 || n_groups > TF_ENS_MAX_GROUPS) return 0;
+    return align256((size_t)n_groups * sizeof(EnsGroup)) + align256(sizeof(EnsCtl));
+}
+
+int tf_ensemble_create(tf_ctx* const* groups, int n_groups, void* d_workspace,
+                       size_t workspace_bytes, void* stream, tf_ensemble** out) {
+    if (!out) return TF_ERR_ARG;
+    *out = nullptr;
+    if (!groups || n_groups < 1 || n_groups > TF_ENS_MAX_GROUPS) return TF_ERR_ARG;
+    const size_t need = tf_ensemble_workspace_bytes(n_groups);
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255) || workspace_bytes < need)
+        return TF_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int g = 0; g < n_groups; ++g) {
+        const tf_ctx* c = groups[g];
+        if (!c || c->n_sub != NS_FUSED || c->stream != st || c->storage != groups[0]->storage)
+            return TF_ERR_ARG;
+        for (int h = 0; h < g; ++h)
+            if (groups[h] == c) return TF_ERR_ARG;
+    }
+    tf_ensemble* e = new (std::nothrow) tf_ensemble();
+    if (!e) return TF_ERR_ARG;
+    e->groups.assign(groups, groups + n_groups);
+    e->base_f.assign(n_groups, 0);
+    e->base_p.assign(n_groups, 0);
+    e->base_u.assign(n_groups, 0);
+    e->host_groups.assign(n_groups, EnsGroup{});
+    e->stream = st;
+    e->storage = groups[0]->storage;
+    char* ws = static_cast<char*>(d_workspace);
+    e->d_groups = reinterpret_cast<EnsGroup*>(ws);
+    e->d_ctl = reinterpret_cast<EnsCtl*>(ws + align256((size_t)n_groups * sizeof(EnsGroup)));
+    int dev = 0, coop = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (err == cudaSuccess) err = configure_storage<PopF32>();
+    if (err == cudaSuccess) err = configure_storage<PopF16>();
+    if (err == cudaSuccess) err = configure_storage<PopBF16>();
+    if (err != cudaSuccess || !coop) {
+        delete e;
+        return TF_ERR_CUDA;
+    }
+    const int rc = normalise(e);
+    if (rc != TF_OK) {
+        delete e;
+        return rc;
+    }
+    *out = e;
+    return TF_OK;
+}
+
+int tf_ensemble_destroy(tf_ensemble* e) {
+    if (!e) return TF_ERR_ARG;
+    cudaStreamSynchronize(e->stream);
+    for (auto& kv : e->cache) cudaGraphExecDestroy(kv.second);
+    delete e;
+    return TF_OK;
+}
+
+const char* tf_ensemble_last_error(const tf_ensemble* e) {
+    return e ? e->last_error.c_str() : "null ensemble";
+}
+
+int tf_ensemble_step(tf_ensemble* e, int64_t n) {
+    if (!e) return TF_ERR_ARG;
+    if (n < 0) return efail(e, TF_ERR_ARG, "negative step count");
+    if (n == 0) return TF_OK;
+    if (!members_in_step(e)) {
+        const int rc = normalise(e);
+        if (rc != TF_OK) return rc;
+    }
+    int64_t left = n;
+    int rc = TF_OK;
+    if (!e->pending) {
+        rc = issue(e, kPrologue, 1);
+        left -= 1;
+    }
+    while (rc == TF_OK && left > 0) {
+        const int64_t k = left < kMaxStepsPerLaunch ? left : kMaxStepsPerLaunch;
+        rc = issue(e, kSteady, (int)k);
+        left -= k;
+    }
+    publish(e, n - left);
+    return rc;
+}
+
+int tf_ensemble_sync(tf_ensemble* e) {
+    if (!e) return TF_ERR_ARG;
+    TF_ECK(e, cudaStreamSynchronize(e->stream));
+    for (tf_ctx* c : e->groups) {
+        const int rc = tf_sync(c);
+        if (rc != TF_OK) return efail(e, rc, std::string("member: ") + tf_last_error(c));
+    }
+    return TF_OK;
+}
+
+int tf_ensemble_autotune(tf_ensemble* e, int steps_per_candidate) {
+    if (!e) return TF_ERR_ARG;
+    if (steps_per_candidate < 1 || steps_per_candidate > kMaxStepsPerLaunch)
+        return efail(e, TF_ERR_ARG, "steps_per_candidate must be in [1, 1024]");
+    int rc = TF_OK;
+    if (!members_in_step(e) && (rc = normalise(e)) != TF_OK) return rc;
+    int64_t done = 0;
+    if (!e->pending) {
+        if ((rc = issue(e, kPrologue, 1)) != TF_OK) return rc;
+        done += 1;
+    }
+    cudaEvent_t t0, t1;
+    TF_ECK(e, cudaEventCreate(&t0));
+    TF_ECK(e, cudaEventCreate(&t1));
+    int best = e->cfg;
+    for (int c = 0; c < kCandidates && rc == TF_OK; ++c) {
+        e->cfg = c;
+        cudaEventRecord(t0, e->stream);
+        rc = issue(e, kSteady, steps_per_candidate);
+        cudaEventRecord(t1, e->stream);
+        done += steps_per_candidate;
+        float ms = 0.f;
+        if (rc == TF_OK && cudaEventSynchronize(t1) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess)
+            e->us[c] = 1e3 * ms / steps_per_candidate;
+        if (e->us[c] > 0 && (e->us[best] <= 0 || e->us[c] < e->us[best])) best = c;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    e->cfg = best;
+    publish(e, done);
+    if (rc != TF_OK) return rc;
+    return tf_ensemble_sync(e);
+}
+
+int tf_ensemble_config(const tf_ensemble* e, int* tile_y, int* ctas_per_sm, int* grid,
+                       int64_t* tiles_per_step, double* us_per_step, int* graphs) {
+    if (!e) return TF_ERR_ARG;
+    const int ti = e->cfg / 2;
+    if (tile_y) *tile_y = kTileY[ti];
+    if (ctas_per_sm) *ctas_per_sm = 2 - e->cfg % 2;
+    if (grid) *grid = grid_for(const_cast<tf_ensemble*>(e), kSteady, e->cfg);
+    if (tiles_per_step) *tiles_per_step = e->tiles[ti];
+    if (us_per_step)
+        for (int c = 0; c < kCandidates; ++c) us_per_step[c] = e->us[c];
+    if (graphs) *graphs = e->graphs ? 1 : 0;
+    return TF_OK;
+}
+
+int64_t tf_ensemble_launches(const tf_ensemble* e) { return e ? e->launches : -1; }
+
+}  // extern "C"

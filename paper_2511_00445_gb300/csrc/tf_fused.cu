@@ -1,432 +1,29 @@
-// Fused coupled step: one kernel launch per lattice step in steady state.
-//
-// The lattice step n -> n+1 is regrouped as
-//     LBM(0) | FD(0) + LBM(1) | FD(1) + LBM(2) | ... | FD(n-1)
-// where LBM(k) = forces from (phi^k, Q^k), pull streaming, implicit-drag Guo
-// velocities and BGK+Guo collision (Sec. III), and FD(k) = the n_sub
-// Cahn-Hilliard / Beris-Edwards forward-Euler sub-steps with the velocities
-// u^k of LBM(k).  Between launches the device holds f*^k (pull layout),
-// phi^k, Q^k and u^k with FD(k) pending; the first launch of a run is the
-// LBM-only prologue and an FD-only epilogue restores the plain state
-// (f*, phi^{k+1}, Q^{k+1}) before any read.
-//
-// One CTA owns a TX x TY interior tile of one instance:
-//  1. the phi, Q and u planes of the tile plus a halo are brought into shared
-//     memory by bulk copies (one per row segment, periodic wrap handled by
-//     splitting segments), and the population rows the tile will pull are
-//     bulk-prefetched into L2 so that they stream from HBM during step 2;
-//  2. FD(k) runs in shared memory on shrinking neighbourhoods of the tile
-//     (phi loses two sites of halo per sub-step through lap(mu), Q one site);
-//     each sub-step computes mu, then the new phi and Q into registers, then
-//     writes them back in place, separated by barriers;
-//  3. mu and the fluid-1 stress on radius 1, then per interior site the
-//     forces, pulled populations, drag solve, collision and stores.
-#include "tf_device.cuh"
-#include "tf_internal.h"
-#include "tf_pair.cuh"
-#include "tf_ptx.cuh"
+// Fused coupled step of one context: one kernel launch per lattice step in
+// steady state (the step regrouping, tile stages and shared-memory layout are
+// described in tf_fused.cuh).  Launch sequence per run: LBM-only prologue,
+// steady-state launches, FD-only epilogue before any read.
+#include "tf_fused.cuh"
 
 namespace {
 
-constexpr int TX = 32, TY = 32;
-constexpr int NT = 256;        // threads per CTA: 32 x 8
-constexpr int NS_FUSED = 5;    // sub-steps handled by the fused kernel (Sec. III)
-constexpr uint32_t kWaitPolls = 1u << 22;
-
-__device__ __forceinline__ int wrapc(int v, int n) {
-    // v may lie several periods outside [0, n) for tiny grids
-    v %= n;
-    return v < 0 ? v + n : v;
-}
-
-constexpr int round4(int v) { return (v + 3) & ~3; }
-
-template <bool DO_FD, bool DO_LBM>
-struct Geo {
-    static constexpr int R_END = DO_LBM ? 2 : 0;                  // phi/Q radius after FD
-    static constexpr int RH_NEED = R_END + (DO_FD ? 2 * NS_FUSED : 0);
-    static constexpr int RH = round4(RH_NEED < 4 ? 4 : RH_NEED);  // loaded halo, 16-byte aligned
-    static constexpr int W = TX + 2 * RH;
-    static constexpr int H = TY + 2 * RH;
-    static constexpr int A = W * H;                              // floats per smem plane
-    static constexpr int NPLANES = 8;                            // phi mu u1x u1y u2x u2y qa qb
-    static constexpr int NLOAD = DO_FD ? 7 : 3;                  // planes read from global
-    static constexpr size_t SMEM = (size_t)NPLANES * A * sizeof(float);
-};
-
-// Dynamic shared memory: eight planes of A floats each, in this order.
-extern __shared__ __align__(16) float tf_smem[];
-enum { P_PHI = 0, P_MU, P_U1X, P_U1Y, P_U2X, P_U2Y, P_QA, P_QB };
-
-// One forward-Euler sub-step: phi on the neighbourhood of radius rp, Q on rq.
-//
-// Each warp owns a band of consecutive rows of the neighbourhood across its
-// whole width; lane l holds one pair of adjacent columns (64-bit shared loads,
-// paired FP32 arithmetic).  A warp walks its band top to bottom keeping rows
-// y-1, y, y+1 in registers (roles rotate by renaming), so y-neighbours come
-// from registers and x-neighbours from warp shuffles.  Rows are written back
-// in place after a warp sync; the rows just above and below a band belong to
-// other warps and are captured in registers before a barrier.
-template <int RH, int W, int A>
-__device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
-    using namespace tfq;
-    float* __restrict__ phi = tf_smem + P_PHI * A;
-    float* __restrict__ mu = tf_smem + P_MU * A;
-    const float* __restrict__ u1x = tf_smem + P_U1X * A;
-    const float* __restrict__ u1y = tf_smem + P_U1Y * A;
-    const float* __restrict__ u2x = tf_smem + P_U2X * A;
-    const float* __restrict__ u2y = tf_smem + P_U2Y * A;
-    float* __restrict__ qa = tf_smem + P_QA * A;
-    float* __restrict__ qb = tf_smem + P_QB * A;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = NT / 32;
-    const f2 mu0 = S2(P.mu0), mu1 = S2(P.mu1), mu2 = S2(P.mu2), mu3 = S2(P.mu3);
-    const f2 kap = S2(-P.kappa), m4 = S2(-4.f), half = S2(0.5f), cref = S2(P.phi_ref);
-
-    // (a) chemical potential on radius ra = rp + 1 (reads phi on ra + 1)
-    {
-        const int ra = rp + 1, w = TX + 2 * ra, h = TY + 2 * ra, o = RH - ra;
-        const PairCols pc(o, w, lane);
-        const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
-        if (y0 < y1) {
-            const float* col = phi + pc.c0;
-            f2 pp = ld2(col + (o + y0 - 1) * W), pcur = ld2(col + (o + y0) * W);
-            for (int y = y0; y < y1; ++y) {
-                const f2 pn = ld2(col + (o + y + 1) * W);
-                f2 l, r;
-                nbr2(pcur, l, r);
-                const f2 lap = F2(m4, pcur, A2(A2(l, r), A2(pp, pn)));
-                const f2 poly = F2(pcur, F2(pcur, F2(pcur, mu3, mu2), mu1), mu0);
-                st_pair(mu + (o + y) * W + pc.c0, F2(kap, lap, poly), pc.in0, pc.in1);
-                pp = pcur;
-                pcur = pn;
-            }
-        }
-    }
-    __syncthreads();
-
-    // (b) phi on radius rp, Q on radius rq
-    const int w = TX + 2 * rp, h = TY + 2 * rp, o = RH - rp;
-    const PairCols pc(o, w, lane);
-    const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
-    const int oq = RH - rq, wq = TX + 2 * rq;     // Q neighbourhood (shared coordinates)
-    // (pc.in0 / in1 are false on surplus lanes; the Q neighbourhood lies inside)
-    const bool q0 = pc.in0 && pc.c0 >= oq && pc.c0 < oq + wq;
-    const bool q1 = pc.in1 && pc.c0 + 1 >= oq && pc.c0 + 1 < oq + wq;
-    const f2 dt = S2(P.dt_fd), Mm = S2(P.M), K2 = S2(P.K), lam = S2(P.lam), GQ = S2(P.GammaQ);
-    const f2 AQ = S2(-P.A_Q), CQ = S2(-P.C_Q), four = S2(4.f);
-    auto flux = [&](f2 pv, f2 v1, f2 v2) { return M2(pv, F2(pv, B2(v1, v2), v2)); };
-    struct Row {
-        f2 mu, ax, ay, qa, qb, jy, ph, jx;
-    };
-    Row r0, r1, r2;                               // three rows: roles rotate by renaming
-    f2 e_ph, e_qa, e_qb;                          // row y1 (below the band), captured early
-    auto load_row = [&](Row& R, int y, bool edge) {
-        const int c = (o + y) * W + pc.c0;
-        R.mu = ld2(mu + c);
-        R.ax = ld2(u1x + c);
-        R.ay = ld2(u1y + c);
-        if (edge) {
-            R.ph = e_ph;
-            R.qa = e_qa;
-            R.qb = e_qb;
-        } else {
-            R.ph = ld2(phi + c);
-            R.qa = ld2(qa + c);
-            R.qb = ld2(qb + c);
-        }
-        const f2 pv = A2(cref, R.ph);
-        R.jy = flux(pv, R.ay, ld2(u2y + c));
-        R.jx = flux(pv, R.ax, ld2(u2x + c));
-    };
-    // Compute row y from (Pr, Cr, Nr) = rows y-1, y, y+1 and write it back.
-    auto do_row = [&](int y, const Row& Pr, const Row& Cr, const Row& Nr) {
-        f2 l, r;
-        nbr2(Cr.jx, l, r);
-        const f2 divJ = M2(half, A2(B2(r, l), B2(Nr.jy, Pr.jy)));
-        nbr2(Cr.mu, l, r);
-        const f2 lapmu = F2(m4, Cr.mu, A2(A2(l, r), A2(Nr.mu, Pr.mu)));
-        const f2 nph = F2(dt, F2(Mm, lapmu, make_float2(-divJ.x, -divJ.y)), Cr.ph);
-        const int row = o + y;
-        const bool qrow = row >= oq && row < oq + TY + 2 * rq;
-        f2 nqa = Cr.qa, nqb = Cr.qb;
-        if (qrow) {
-            f2 al, ar, bl, br, uxl, uxr, uyl, uyr;
-            nbr2(Cr.qa, al, ar);
-            nbr2(Cr.qb, bl, br);
-            nbr2(Cr.ax, uxl, uxr);
-            nbr2(Cr.ay, uyl, uyr);
-            const f2 a = Cr.qa, bq = Cr.qb;
-            const f2 lapa = F2(m4, a, A2(A2(al, ar), A2(Nr.qa, Pr.qa)));
-            const f2 lapb = F2(m4, bq, A2(A2(bl, br), A2(Nr.qb, Pr.qb)));
-            const f2 cqf = F2(CQ, F2(a, a, M2(bq, bq)), AQ);        // -(A_Q + C_Q q^2)
-            const f2 hh = F2(cqf, a, M2(K2, lapa));
-            const f2 g = F2(cqf, bq, M2(K2, lapb));
-            const f2 Wxx = M2(half, B2(uxr, uxl)), Wxy = M2(half, B2(Nr.ax, Pr.ax));
-            const f2 Wyx = M2(half, B2(uyr, uyl)), Wyy = M2(half, B2(Nr.ay, Pr.ay));
-            const f2 trE = A2(Wxx, Wyy);
-            const f2 e1 = M2(half, B2(Wxx, Wyy));
-            const f2 exy = M2(half, A2(Wxy, Wyx));
-            const f2 om = B2(Wxy, Wyx);
-            const f2 QE2 = M2(four, F2(a, e1, M2(bq, exy)));
-            // -(u1 . grad) a and b, central differences
-            const f2 adv_a = M2(half, F2(Cr.ax, B2(ar, al), M2(Cr.ay, B2(Nr.qa, Pr.qa))));
-            const f2 adv_b = M2(half, F2(Cr.ax, B2(br, bl), M2(Cr.ay, B2(Nr.qb, Pr.qb))));
-            // lam (trE a + e1 - QE2 a) + om b + Gamma h - adv
-            const f2 sa = F2(lam, A2(B2(M2(trE, a), M2(QE2, a)), e1), M2(om, bq));
-            const f2 sb = F2(lam, A2(B2(M2(trE, bq), M2(QE2, bq)), exy), N2(M2(om, a)));
-            const f2 ra = B2(F2(GQ, hh, sa), adv_a);
-            const f2 rb = B2(F2(GQ, g, sb), adv_b);
-            nqa = F2(dt, ra, a);
-            nqb = F2(dt, rb, bq);
-        }
-        __syncwarp();   // every lane has read row y before it is overwritten
-        const int c = row * W + pc.c0;
-        st_pair(phi + c, nph, pc.in0, pc.in1);
-        if (qrow) {
-            st_pair(qa + c, nqa, q0, q1);
-            st_pair(qb + c, nqb, q0, q1);
-        }
-    };
-    if (y0 < y1) {
-        load_row(r0, y0 - 1, false);
-        load_row(r1, y0, false);
-        const int ce = (o + y1) * W + pc.c0;
-        e_ph = ld2(phi + ce);
-        e_qa = ld2(qa + ce);
-        e_qb = ld2(qb + ce);
-    }
-    __syncthreads();   // band edges captured before any row is overwritten
-    int y = y0;
-    for (; y + 3 <= y1; y += 3) {
-        load_row(r2, y + 1, false);
-        do_row(y, r0, r1, r2);
-        load_row(r0, y + 2, false);
-        do_row(y + 1, r1, r2, r0);
-        load_row(r1, y + 3, y + 3 == y1);
-        do_row(y + 2, r2, r0, r1);
-    }
-    if (y < y1) {
-        load_row(r2, y + 1, y + 1 == y1);
-        do_row(y, r0, r1, r2);
-        ++y;
-        if (y < y1) {
-            load_row(r0, y + 1, y + 1 == y1);
-            do_row(y, r1, r2, r0);
-        }
-    }
-    __syncthreads();
-}
-
-// Copy `len` floats of row gy starting at column xs (periodic in x) from a
-// global plane into shared memory, splitting the segment at the wrap.
-__device__ __forceinline__ void bulk_row(float* dst, const float* plane, int gy, int xs, int len,
-                                         int nx, uint64_t* bar) {
-    int off = 0;
-    while (off < len) {
-        const int gx = wrapc(xs + off, nx);
-        const int n = min(len - off, nx - gx);
-        tfp::bulk_g2s(dst + off, plane + (long long)gy * nx + gx, (uint32_t)n * 4u, bar);
-        off += n;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void prefetch_row(const T* plane, int gy, int xs, int len, int nx) {
-    int off = 0;
-    while (off < len) {
-        const int gx = wrapc(xs + off, nx);
-        const int n = min(len - off, nx - gx);
-        tfp::prefetch_l2(plane + (long long)gy * nx + gx, (uint32_t)(n * sizeof(T)));
-        off += n;
-    }
-}
-
+// One tile per CTA: tile (blockIdx.x, blockIdx.y) of instance blockIdx.z.
 template <bool DO_FD, bool DO_LBM, class S>
-__global__ void __launch_bounds__(NT, 2)
-k_fused(const typename S::T* __restrict__ fsrc, typename S::T* __restrict__ fdst,
-        const float* __restrict__ phi_in, float* __restrict__ phi_out,
-        const float* __restrict__ Q_in, float* __restrict__ Q_out,
-        const float* __restrict__ u_in, float* __restrict__ u_out,
-        const DevParams* __restrict__ prm, int nx, int ny, int* __restrict__ err) {
-    using G = Geo<DO_FD, DO_LBM>;
-    constexpr int RH = G::RH, W = G::W, H = G::H, A = G::A;
+__global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
     __shared__ __align__(8) uint64_t bar;
-    const int b = blockIdx.z;
-    const long long N = (long long)nx * ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const DevParams P = prm[b];
-    // 16-byte bulk copies need every row start on a 16-byte boundary.
-    const bool bulk = (nx & 3) == 0;
-    // Population prefetch: rows of PF elements (16 bytes) at 16-byte boundaries.
-    constexpr int PF = 16 / (int)sizeof(typename S::T);
-    const bool pref = nx % PF == 0;
-
-    // ---- stage 1: tile loads (and population prefetch)
-    // Load task pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y.
-    auto src_plane = [&](int pl) -> const float* {
-        return pl == 0 ? phi_in + b * N
-                       : (pl < 3 ? Q_in + (2 * b + pl - 1) * N : u_in + (4 * b + pl - 3) * N);
-    };
-    auto dst_plane = [&](int pl) -> float* {
-        return tf_smem + (pl == 0 ? P_PHI : (pl < 3 ? P_QA + pl - 1 : P_U1X + pl - 3)) * A;
-    };
-    if (bulk) {
-        if (threadIdx.x == 0) {
-            tfp::mbar_init(&bar, 1);
-            tfp::fence_mbar_init();
-        }
-        __syncthreads();
-        if (threadIdx.x == 0)
-            tfp::mbar_arrive_expect_tx(&bar, (uint32_t)(G::NLOAD * A * sizeof(float)));
-        for (int t = threadIdx.x; t < G::NLOAD * H; t += NT) {
-            const int pl = t / H, ly = t - pl * H;
-            const int gy = wrapc(y0 - RH + ly, ny);
-            bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, W, nx, &bar);
-        }
-        if (DO_LBM && pref) {
-            const typename S::T* F = fsrc + 18 * b * N;
-            for (int t = threadIdx.x; t < 18 * (TY + 2); t += NT) {
-                const int i = t / (TY + 2), r = t - i * (TY + 2);
-                prefetch_row(F + (long long)i * N, wrapc(y0 - 1 + r, ny), x0 - PF, TX + 2 * PF, nx);
-            }
-        }
-        const bool ok = tfp::wait_bounded(&bar, 0, kWaitPolls);
-        if (__syncthreads_or(!ok)) {
-            // A bulk copy did not complete: report, give in-flight copies a
-            // bounded chance to land in this CTA's shared memory, and leave.
-            if (threadIdx.x == 0) atomicExch(err, TF_ERR_TIMEOUT);
-            tfp::wait_bounded(&bar, 0, kWaitPolls);
-            return;
-        }
-    } else {
-        for (int i = threadIdx.x; i < A; i += NT) {
-            const int ly = i / W, lx = i - ly * W;
-            const long long g = (long long)wrapc(y0 - RH + ly, ny) * nx + wrapc(x0 - RH + lx, nx);
-#pragma unroll
-            for (int pl = 0; pl < G::NLOAD; ++pl) dst_plane(pl)[i] = src_plane(pl)[g];
-        }
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        tfp::mbar_init(&bar, 1);
+        tfp::fence_mbar_init();
     }
-
-    // ---- stage 2: sub-steps of the pending FD
-    if constexpr (DO_FD) {
-#pragma unroll 1
-        for (int st = 0; st < NS_FUSED; ++st) {
-            const int rp = G::R_END + 2 * (NS_FUSED - 1 - st);
-            const int rq = G::R_END + (NS_FUSED - 1 - st);
-            fd_substep<RH, W, A>(P, rp, rq);
-        }
-    }
-
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    if constexpr (DO_LBM) {
-        using namespace tfq;
-        // ---- stage 3a: chemical potential and fluid-1 stress on radius 1
-        // (paired column walk like the sub-steps; results go to the mu plane
-        // and to the four u planes, free after the sub-steps)
-        {
-            const float* phi = tf_smem + P_PHI * A;
-            const float* qa = tf_smem + P_QA * A;
-            const float* qb = tf_smem + P_QB * A;
-            constexpr int o = RH - 1, w = TX + 2, h = TY + 2, NW = NT / 32;
-            const PairCols pc(o, w, tx);
-            constexpr int bh = (h + NW - 1) / NW;
-            const int y0 = ty * bh, y1 = min(h, y0 + bh);
-            if (y0 < y1) {
-                const int col = pc.c0;
-                f2 dp = ld2(phi + (o + y0 - 1) * W + col), dc = ld2(phi + (o + y0) * W + col);
-                f2 ap = ld2(qa + (o + y0 - 1) * W + col), ac = ld2(qa + (o + y0) * W + col);
-                f2 bp = ld2(qb + (o + y0 - 1) * W + col), bc = ld2(qb + (o + y0) * W + col);
-                for (int y = y0; y < y1; ++y) {
-                    const int cn = (o + y + 1) * W + col, cc = (o + y) * W + col;
-                    const f2 dn = ld2(phi + cn), an = ld2(qa + cn), bn = ld2(qb + cn);
-                    f2 dl, dr, al, ar, bl, br;
-                    nbr2(dc, dl, dr);
-                    nbr2(ac, al, ar);
-                    nbr2(bc, bl, br);
-                    const PairStress r =
-                        stress2(P, dc, dl, dr, dn, dp, ac, al, ar, an, ap, bc, bl, br, bn, bp);
-                    st_pair(tf_smem + P_MU * A + cc, r.mu, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U1X * A + cc, r.sxx, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U1Y * A + cc, r.sxy, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U2X * A + cc, r.syx, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U2Y * A + cc, r.syy, pc.in0, pc.in1);
-                    dp = dc;
-                    dc = dn;
-                    ap = ac;
-                    ac = an;
-                    bp = bc;
-                    bc = bn;
-                }
-            }
-        }
-        __syncthreads();
-        // ---- stage 3b: interior forces, pull, moments, drag, collide, store
-        const float* phi = tf_smem + P_PHI * A;
-        const float* mu = tf_smem + P_MU * A;
-        const float* sxx = tf_smem + P_U1X * A;
-        const float* sxy = tf_smem + P_U1Y * A;
-        const float* syx = tf_smem + P_U2X * A;
-        const float* syy = tf_smem + P_U2Y * A;
-        const typename S::T* F1 = fsrc + 18 * b * N;
-        const typename S::T* F2p = F1 + 9 * N;
-        typename S::T* D1 = fdst + 18 * b * N;
-        typename S::T* D2 = D1 + 9 * N;
-        float* uo = u_out + 4 * b * N;
-#pragma unroll 1
-        for (int r = ty; r < TY; r += NT / 32) {
-            const int x = x0 + tx, y = y0 + r;
-            if (x >= nx || y >= ny) continue;
-            const int c = (RH + r) * W + RH + tx;
-            const int xp = x + 1 < nx ? x + 1 : 0, xm = x > 0 ? x - 1 : nx - 1;
-            const int yp = y + 1 < ny ? y + 1 : 0, ym = y > 0 ? y - 1 : ny - 1;
-            f2 f[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
-                const int sy = d2q9_cy(i) == 0 ? y : (d2q9_cy(i) > 0 ? ym : yp);
-                const long long src = (long long)sy * nx + sx;
-                f[i] = P2(S::load(F1 + i * N + src), S::load(F2p + i * N + src));
-            }
-            f2 u1, u2;
-            lbm_site2(P, phi[c], P2(phi[c - 1], phi[c + 1]), P2(phi[c - W], phi[c + W]), mu[c],
-                      P2(mu[c - 1], mu[c + 1]), P2(mu[c - W], mu[c + W]), P2(sxx[c - 1], sxx[c + 1]),
-                      P2(sxy[c - W], sxy[c + W]), P2(syx[c - 1], syx[c + 1]),
-                      P2(syy[c - W], syy[c + W]), f, u1, u2);
-            const long long g = (long long)y * nx + x;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                S::store(D1 + i * N + g, f[i].x);
-                S::store(D2 + i * N + g, f[i].y);
-            }
-            uo[g] = u1.x;
-            uo[N + g] = u1.y;
-            uo[2 * N + g] = u2.x;
-            uo[3 * N + g] = u2.y;
-        }
-    }
-    if constexpr (DO_FD) {
-        // ---- store phi^{k+1}, Q^{k+1} of the interior
-        float* po = phi_out + b * N;
-        float* qo = Q_out + 2 * b * N;
-        for (int r = ty; r < TY; r += NT / 32) {
-            const int x = x0 + tx, y = y0 + r;
-            if (x >= nx || y >= ny) continue;
-            const int c = (RH + r) * W + RH + tx;
-            const long long g = (long long)y * nx + x;
-            po[g] = tf_smem[P_PHI * A + c];
-            qo[g] = tf_smem[P_QA * A + c];
-            qo[N + g] = tf_smem[P_QB * A + c];
-        }
-    }
+    __syncthreads();
+    fused_tile<DO_FD, DO_LBM, S, TY_DEFAULT>(a, blockIdx.z, blockIdx.x * TX,
+                                             blockIdx.y * TY_DEFAULT, &bar, 0);
 }
 
 template <bool DO_FD, bool DO_LBM, class S>
 cudaError_t configure_one() {
     return cudaFuncSetAttribute(k_fused<DO_FD, DO_LBM, S>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Geo<DO_FD, DO_LBM>::SMEM);
+                                (int)Geo<DO_FD, DO_LBM, TY_DEFAULT>::SMEM);
 }
 
 template <class S>
@@ -439,14 +36,15 @@ cudaError_t configure() {
 
 template <bool DO_FD, bool DO_LBM, class S>
 void launch_as(tf_ctx* ctx) {
-    using G = Geo<DO_FD, DO_LBM>;
+    using G = Geo<DO_FD, DO_LBM, TY_DEFAULT>;
     using T = typename S::T;
     DevBuffers& d = ctx->d;
-    const dim3 grid((ctx->nx + TX - 1) / TX, (ctx->ny + TY - 1) / TY, ctx->batch);
+    const dim3 grid((ctx->nx + TX - 1) / TX, (ctx->ny + TY_DEFAULT - 1) / TY_DEFAULT, ctx->batch);
     const int fc = ctx->fcur, pc = ctx->pcur, uc = ctx->ucur;
-    k_fused<DO_FD, DO_LBM, S><<<grid, NT, G::SMEM, ctx->stream>>>(
-        static_cast<const T*>(d.f[fc]), static_cast<T*>(d.f[fc ^ 1]), d.phi[pc], d.phi[pc ^ 1],
-        d.Q[pc], d.Q[pc ^ 1], d.u[uc], d.u[uc ^ 1], d.prm, ctx->nx, ctx->ny, d.flags);
+    const TileArgs<S> a{static_cast<const T*>(d.f[fc]), static_cast<T*>(d.f[fc ^ 1]),
+                        d.phi[pc], d.phi[pc ^ 1], d.Q[pc], d.Q[pc ^ 1], d.u[uc], d.u[uc ^ 1],
+                        d.prm, ctx->nx, ctx->ny, d.flags};
+    k_fused<DO_FD, DO_LBM, S><<<grid, NT, G::SMEM, ctx->stream>>>(a);
 }
 
 template <bool DO_FD, bool DO_LBM>

@@ -34,24 +34,34 @@ __host__ __device__ constexpr double d2q9_wd(int i) {
 // Population storage (TF_STORE_*): the stored value is the deviation
 // d_i = f_i - w_i, widened to FP32 on load and rounded to nearest on store.
 // FP16 carries d_i * 2^12 (an exact scale both ways) so that deviations down
-// to 1.5e-8 stay normal.  Zero bits are d_i = 0 in every mode.
+// to 1.5e-8 stay normal.  Zero bits are d_i = 0 in every mode.  load_cg reads
+// through L2 only (ld.global.cg): for data other CTAs of the same launch wrote.
 // ---------------------------------------------------------------------------
 struct PopF32 {
     typedef float T;
     static constexpr int kMode = TF_STORE_F32;
     __device__ static float load(const T* p) { return *p; }
+    __device__ static float load_cg(const T* p) { return __ldcg(p); }
     __device__ static void store(T* p, float d) { *p = d; }
 };
 struct PopF16 {
     typedef __half T;
     static constexpr int kMode = TF_STORE_F16;
     __device__ static float load(const T* p) { return __fmul_rn(__half2float(*p), 0x1p-12f); }
+    __device__ static float load_cg(const T* p) {
+        const unsigned short v = __ldcg(reinterpret_cast<const unsigned short*>(p));
+        return __fmul_rn(__half2float(__ushort_as_half(v)), 0x1p-12f);
+    }
     __device__ static void store(T* p, float d) { *p = __float2half_rn(__fmul_rn(d, 0x1p12f)); }
 };
 struct PopBF16 {
     typedef __nv_bfloat16 T;
     static constexpr int kMode = TF_STORE_BF16;
     __device__ static float load(const T* p) { return __bfloat162float(*p); }
+    __device__ static float load_cg(const T* p) {
+        const unsigned short v = __ldcg(reinterpret_cast<const unsigned short*>(p));
+        return __bfloat162float(__ushort_as_bfloat16(v));
+    }
     __device__ static void store(T* p, float d) { *p = __float2bfloat16_rn(d); }
 };
 

@@ -1,0 +1,138 @@
+"""Ensembles (tf_ensemble_*): groups of different grid sizes stepped by one
+persistent cooperative launch over a ragged tile work-list.
+
+Every site's arithmetic is the same whichever tile (and tile height) it falls
+in, so an ensemble must reproduce, bit for bit, the same groups stepped one
+context at a time; that is the oracle for this layer (the per-context path is
+itself checked against the FP64 oracle in test_gpu_parity.py).
+"""
+import numpy as np
+import pytest
+
+from paper_2511_00445_gb300 import _binding as B
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = (B.FIELD_PHI, B.FIELD_QXX, B.FIELD_QXY, B.FIELD_U1X, B.FIELD_U2Y, B.FIELD_F1 + 0,
+          B.FIELD_F1 + 6, B.FIELD_F2 + 3, B.FIELD_F2 + 8)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2511_00445_gb300 import build
+    build.build()
+
+
+def groups_spec(storage=B.STORE_F32):
+    """Three groups: ragged 40x36 (two instances), 64x48, and 33x17 whose
+    rows are not 16-byte multiples (per-element tile loads)."""
+    base = B.SolverParams(storage=storage)
+    return [
+        [base.with_(nx=40, ny=36, zeta=0.01), base.with_(nx=40, ny=36, zeta=0.002, lam=1.1)],
+        [base.with_(nx=64, ny=48, zeta=0.005, K=0.08)],
+        [base.with_(nx=33, ny=17, zeta=0.01, lam=0.3)],
+    ]
+
+
+def make_groups(spec):
+    out = []
+    for g, plist in enumerate(spec):
+        tf = B.TwoFluid(plist)
+        for b in range(len(plist)):
+            tf.init_fields(seed=100 * g + b, phi0=0.5, dphi=0.01, S0=0.01)
+        out.append(tf)
+    return out
+
+
+def alone(spec, steps):
+    ref = make_groups(spec)
+    for tf in ref:
+        tf.step(steps)
+        tf.sync()
+    return ref
+
+
+def assert_same(got, want):
+    for g, (a, b) in enumerate(zip(got, want)):
+        for inst in range(a.batch):
+            for f in FIELDS:
+                assert np.array_equal(a.read_field(inst, f), b.read_field(inst, f)), (g, inst, f)
+        assert a.step_count() == b.step_count()
+
+
+def test_ensemble_matches_groups_stepped_alone():
+    spec = groups_spec()
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.step(1)          # LBM-only first pass
+    ens.step(6)          # one persistent launch of six steps
+    ens.sync()
+    assert_same(grp, alone(spec, 7))
+    cfg = ens.config()
+    assert cfg["tile_y"] == 32 and cfg["ctas_per_sm"] == 2
+    # 40x36: 2 x (2 x 2) tiles, 64x48: 2 x 2, 33x17: 2 x 1
+    assert cfg["tiles_per_step"] == 8 + 4 + 2
+    assert ens.launches() == 2
+
+
+def test_ensemble_autotune_steps_are_real_steps():
+    """Six candidates (tile heights 32/24/16, one or two CTAs per SM) each run
+    real steps; the trajectory equals stepping alone."""
+    spec = groups_spec()
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.autotune(2)                       # first pass + 6 x 2 steps
+    ens.step(3)
+    ens.sync()
+    assert_same(grp, alone(spec, 1 + 12 + 3))
+    cfg = ens.config()
+    assert all(us > 0 for us in cfg["us_per_step"])
+    assert cfg["tile_y"] in (16, 24, 32) and cfg["ctas_per_sm"] in (1, 2)
+
+
+def test_ensemble_member_reads_between_calls():
+    """A member read completes that member's pending sub-steps; the next
+    ensemble call realigns all members and the trajectory is unchanged."""
+    spec = groups_spec()
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.step(3)
+    grp[1].read_field(0, B.FIELD_PHI)
+    ens.step(2)
+    grp[0].conserved(1)
+    ens.step(4)
+    ens.sync()
+    assert_same(grp, alone(spec, 9))
+
+
+@pytest.mark.parametrize("storage", [B.STORE_F16, B.STORE_BF16], ids=["f16", "bf16"])
+def test_ensemble_16bit_storage(storage):
+    spec = groups_spec(storage)
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.step(5)
+    ens.sync()
+    assert_same(grp, alone(spec, 5))
+
+
+def test_ensemble_repeated_calls_replay():
+    """Equal calls reuse their launch shape; results stay identical."""
+    spec = groups_spec()
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    for _ in range(4):
+        ens.step(3)
+    ens.sync()
+    assert_same(grp, alone(spec, 12))
+    assert ens.launches() == 1 + 4    # one first pass, then one launch per call
+
+
+def test_ensemble_rejects_bad_members():
+    base = B.SolverParams(nx=16, ny=16)
+    a = B.TwoFluid(base)
+    with pytest.raises(B.TwoFluidError):
+        B.Ensemble([a, B.TwoFluid(base.with_(n_sub=3))])          # per-stage path only
+    with pytest.raises(B.TwoFluidError):
+        B.Ensemble([a, B.TwoFluid(base.with_(storage=B.STORE_F16))])
+    with pytest.raises(B.TwoFluidError):
+        B.Ensemble([a, a])
