@@ -176,13 +176,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+# Sources the per-context fused kernel is compiled from.
+FUSED_SOURCES = ("tf_device.cuh", "tf_fused.cu", "tf_fused.cuh", "tf_internal.h", "tf_pair.cuh",
+                 "tf_ptx.cuh")
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2511_00445_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in FUSED_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

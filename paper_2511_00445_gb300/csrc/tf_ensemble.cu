@@ -176,6 +176,7 @@ struct tf_ensemble {
     std::vector<int> base_f, base_p, base_u;   // member buffer index at ensemble parity 0
     std::vector<EnsGroup> host_groups;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;         // private stream used only to record graphs
     int storage = TF_STORE_F32;
     EnsGroup* d_groups = nullptr;
     EnsCtl* d_ctl = nullptr;
@@ -222,17 +223,17 @@ int grid_for(tf_ensemble* e, int mode, int cfg) {
 }
 
 // Zero the control block, then one cooperative launch of `steps` steps on
-// `grid` CTAs (grid_for; computed outside any stream capture).
-cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid) {
+// `grid` CTAs (grid_for; computed outside any stream capture) into `st`.
+cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid, cudaStream_t st) {
     const int ti = mode == kPrologue ? 0 : cfg / 2;
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    cudaError_t err = cudaMemsetAsync(e->d_ctl, 0, sizeof(EnsCtl), e->stream);
+    cudaError_t err = cudaMemsetAsync(e->d_ctl, 0, sizeof(EnsCtl), st);
     if (err != cudaSuccess) return err;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(grid);
     lc.blockDim = dim3(NT);
     lc.dynamicSmemBytes = smem_for(mode, ti);
-    lc.stream = e->stream;
+    lc.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
@@ -246,6 +247,9 @@ cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid) {
 }
 
 // Issue one launch, from the graph cache when this shape was captured before.
+// Graphs are recorded on the ensemble's private capture stream (the caller's
+// stream may be the legacy default stream, which cannot be captured) and
+// launched into the caller's stream.
 int issue(tf_ensemble* e, int mode, int steps) {
     const auto key = std::make_tuple(mode, (int64_t)steps, e->fpar, e->ppar, e->upar,
                                      mode == kPrologue ? 0 : e->cfg);
@@ -257,11 +261,13 @@ int issue(tf_ensemble* e, int mode, int steps) {
         bool done = false;
         if (e->graphs) {
             cudaGraph_t graph = nullptr;
-            cudaError_t e0 = cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal);
+            cudaError_t e0 = e->cap_stream ? cudaStreamBeginCapture(e->cap_stream,
+                                                                    cudaStreamCaptureModeThreadLocal)
+                                           : cudaErrorNotSupported;
             cudaError_t e1 = cudaErrorUnknown, e2 = cudaErrorUnknown, e3 = cudaErrorUnknown;
             if (e0 == cudaSuccess) {
-                e1 = enqueue(e, mode, steps, e->cfg, grid);
-                e2 = cudaStreamEndCapture(e->stream, &graph);
+                e1 = enqueue(e, mode, steps, e->cfg, grid, e->cap_stream);
+                e2 = cudaStreamEndCapture(e->cap_stream, &graph);
                 cudaGraphExec_t exec = nullptr;
                 if (e1 == cudaSuccess && e2 == cudaSuccess && graph) {
                     e3 = cudaGraphInstantiate(&exec, graph, 0);
@@ -283,7 +289,7 @@ int issue(tf_ensemble* e, int mode, int steps) {
                 e->graphs = false;
             }
         }
-        if (!done) TF_ECK(e, enqueue(e, mode, steps, e->cfg, grid));
+        if (!done) TF_ECK(e, enqueue(e, mode, steps, e->cfg, grid, e->stream));
     }
     e->launches += 1;
     if (mode == kPrologue) {
@@ -421,12 +427,18 @@ int tf_ensemble_create(tf_ctx* const* groups, int n_groups, void* d_workspace,
     if (err == cudaSuccess) err = configure_storage<PopF32>();
     if (err == cudaSuccess) err = configure_storage<PopF16>();
     if (err == cudaSuccess) err = configure_storage<PopBF16>();
+    if (err == cudaSuccess && cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        e->cap_stream = nullptr;   // graphs unavailable; launches go directly into the stream
+        cudaGetLastError();
+    }
     if (err != cudaSuccess || !coop) {
+        if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
         delete e;
         return TF_ERR_CUDA;
     }
     const int rc = normalise(e);
     if (rc != TF_OK) {
+        if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
         delete e;
         return rc;
     }
@@ -438,6 +450,7 @@ int tf_ensemble_destroy(tf_ensemble* e) {
     if (!e) return TF_ERR_ARG;
     cudaStreamSynchronize(e->stream);
     for (auto& kv : e->cache) cudaGraphExecDestroy(kv.second);
+    if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
     delete e;
     return TF_OK;
 }
