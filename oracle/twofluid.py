@@ -538,3 +538,129 @@ def phase_difference(state: State, p: Params):
 def std_phi(phi):
     """Standard deviation Delta of the concentration field (Sec. IV, Fig. 3)."""
     return float(np.sqrt(np.mean((phi - phi.mean()) ** 2)))
+
+
+# --------------------------------------------------------------------------
+# Correlations, defects, energy densities, Reynolds number (Sec. IV).
+# --------------------------------------------------------------------------
+def displacement_shells(nx: int, ny: int):
+    """Shell of every displacement r = (r_x, r_y) of the periodic grid, taken
+    as its minimum image (signed r_x in numpy fftfreq order) in lattice
+    units: floor(|r| + 1/2), shells 0 .. min(nx, ny)/2 (longer displacements
+    are dropped).  Returns (shell, n_shell); shell has shape (ny, nx) indexed
+    by the displacement's array position (dy, dx)."""
+    sx = np.rint(np.fft.fftfreq(nx) * nx)
+    sy = np.rint(np.fft.fftfreq(ny) * ny)
+    r = np.sqrt(sx[None, :] * sx[None, :] + sy[:, None] * sy[:, None])
+    return np.floor(r + 0.5).astype(np.int64), min(nx, ny) // 2 + 1
+
+
+def autocorrelation(a):
+    """R(r) = < sum_c a_c(x) a_c(x + r) >_x for every displacement r, by the
+    definition (one shifted copy per displacement; small grids only).
+    a: components (c, ny, nx).  Returns (ny, nx) indexed by (dy, dx)."""
+    c, ny, nx = a.shape
+    R = np.empty((ny, nx))
+    for dy in range(ny):
+        ay = np.roll(a, -dy, axis=1)
+        for dx in range(nx):
+            R[dy, dx] = (a * np.roll(ay, -dx, axis=2)).sum(axis=0).mean()
+    return R
+
+
+def spatial_correlation(a, centred: bool):
+    """C(r) = <a(0) . a(r)> / <|a|^2> averaged over the displacements of each
+    shell (Sec. IV, spatial correlation functions of u_c, omega_c and Q).
+    centred: use delta a = a - <a> (the paper's delta u_c, delta omega_c)."""
+    a = np.asarray(a, dtype=np.float64)
+    if centred:
+        a = a - a.mean(axis=(1, 2), keepdims=True)
+    ny, nx = a.shape[1:]
+    R = autocorrelation(a)
+    shell, n_shell = displacement_shells(nx, ny)
+    keep = shell < n_shell
+    sums = np.zeros(n_shell)
+    counts = np.zeros(n_shell)
+    np.add.at(sums, shell[keep], R[keep])
+    np.add.at(counts, shell[keep], 1.0)
+    return sums / counts / R[0, 0]
+
+
+def correlation_fields(state: State, p: Params):
+    """The three correlated quantities of the current state: u_c (2, ny, nx),
+    omega_c (1, ny, nx) and (Q_xx, Q_xy) (2, ny, nx), whose dot product is
+    Q:Q / 2 for a traceless symmetric Q (the factor cancels in the ratios)."""
+    mc = macro(state, p)
+    uc = mixture_velocity(state.phi, mc["u1"], mc["u2"])
+    return uc, vorticity(uc)[None], np.stack([state.Qxx, state.Qxy])
+
+
+def spatial_correlations(state: State, p: Params):
+    """[C_uu(r), C_ww(r), C_QQ(r)] shell-averaged (Sec. IV)."""
+    uc, wc, q = correlation_fields(state, p)
+    return [spatial_correlation(uc, True), spatial_correlation(wc, True),
+            spatial_correlation(q, False)]
+
+
+def time_correlations(then: State, now: State, p: Params):
+    """[C_uu(t), C_ww(t), C_QQ(t)] between two states (Sec. IV, temporal
+    correlation functions): <a(tau) . a(tau + t)> / <|a(tau)|^2>."""
+    out = []
+    for a, b in zip(correlation_fields(then, p), correlation_fields(now, p)):
+        out.append(float((a * b).sum(axis=0).mean() / (a * a).sum(axis=0).mean()))
+    return out
+
+
+def defect_charges(Qxx, Qxy):
+    """Winding-number charge of the director around every plaquette (Sec. IV,
+    +-1/2 defects): the plaquette with lower-left site (x, y) is walked
+    (x, y) -> (x+1, y) -> (x+1, y+1) -> (x, y+1) -> (x, y); the director angle
+    theta = atan2(Q_xy, Q_xx) / 2 changes along each edge by the difference
+    wrapped into [-pi/2, pi/2) (a director is a headless line); the summed
+    change over 2 pi is the charge.  Returns charges (ny, nx) in halves."""
+    th = 0.5 * np.arctan2(Qxy, Qxx)
+    loop = [th, np.roll(th, -1, axis=1), np.roll(np.roll(th, -1, axis=1), -1, axis=0),
+            np.roll(th, -1, axis=0)]
+    total = np.zeros_like(th)
+    for k in range(4):
+        d = loop[(k + 1) % 4] - loop[k]
+        total += (d + 0.5 * np.pi) % np.pi - 0.5 * np.pi
+    return np.rint(2.0 * total / (2.0 * np.pi)) / 2.0
+
+
+def defect_counts(Qxx, Qxy):
+    """[number of +1/2, number of -1/2, number of other nonzero charges];
+    the defect density of Sec. IV is (n_+ + n_-) / (nx ny)."""
+    q = defect_charges(Qxx, Qxy)
+    return np.array([np.count_nonzero(q == 0.5), np.count_nonzero(q == -0.5),
+                     np.count_nonzero((q != 0) & (np.abs(q) != 0.5))], dtype=np.int64)
+
+
+def elastic_energy_density(Qxx, Qxy, K):
+    """E_elastic = K/2 |grad Q|^2 = K/2 sum_{k,i,j} (d_k Q_ij)^2 with all four
+    tensor entries (Q_yy = -Q_xx, Q_yx = Q_xy) and central differences
+    (Sec. IV, Fig. 6)."""
+    Q = q_tensor(Qxx, Qxy)
+    g = 0.0
+    for i in range(2):
+        for j in range(2):
+            g = g + ddx(Q[i, j]) ** 2 + ddy(Q[i, j]) ** 2
+    return 0.5 * K * g
+
+
+def kinetic_energy_density(state: State, p: Params):
+    """E_kin = 1/2 rho_c |u_c|^2 with the local total density rho_c = rho1 + rho2
+    (Sec. IV, Fig. 6)."""
+    mc = macro(state, p)
+    uc = mixture_velocity(state.phi, mc["u1"], mc["u2"])
+    return 0.5 * (mc["rho1"] + mc["rho2"]) * (uc * uc).sum(axis=0)
+
+
+def reynolds(state: State, p: Params):
+    """Re = rho_c u_c,rms L_a / eta_c, L_a = sqrt(K / |zeta|) (Sec. IV), with
+    rho_c = rho1 + rho2 the rest densities, eta_c = eta1 + eta2 and
+    eta_k = rho_k (tau_k - 1/2) / 3 in lattice units.  Returns (Re, L_a)."""
+    uc_rms = phase_difference(state, p)[3]
+    La = np.sqrt(p.K / abs(p.zeta)) if p.zeta != 0 else np.inf
+    eta = p.rho1 * (p.tau1 - 0.5) / 3.0 + p.rho2 * (p.tau2 - 0.5) / 3.0
+    return (p.rho1 + p.rho2) * uc_rms * La / eta, La
