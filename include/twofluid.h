@@ -63,6 +63,12 @@ extern "C" {
 #define TF_FIELD_RHO1  7   /* density of fluid 1 (read only, derived)            */
 #define TF_FIELD_RHO2  8   /* density of fluid 2 (read only, derived)            */
 #define TF_FIELD_MU    9   /* chemical potential mu (read only, derived)         */
+/* Energy and flow maps of Sec. IV (Fig. 6), read only, derived; u_c = phi u1 +
+ * (1 - phi) u2, central differences, FP64 from the stored FP32 state: */
+#define TF_FIELD_E_ELASTIC 10 /* K/2 |grad Q|^2 over all four entries of Q          */
+#define TF_FIELD_E_KIN     11 /* 1/2 (rho1 + rho2) |u_c|^2, local densities         */
+#define TF_FIELD_UC_MAG    12 /* |u_c|                                              */
+#define TF_FIELD_OMEGA_C   13 /* omega_c = d_x u_c,y - d_y u_c,x                    */
 #define TF_FIELD_F1   16   /* + i (i = 0..8): pre-collision population f_i of fluid 1 (r/w) */
 #define TF_FIELD_F2   32   /* + i (i = 0..8): pre-collision population f_i of fluid 2 (r/w) */
 /* D2Q9 direction order: c0 = (0,0); c1..c4 = (1,0), (0,1), (-1,0), (0,-1);
@@ -188,6 +194,44 @@ int tf_phase_difference(tf_ctx* ctx, int inst, double out[6]);
 
 /* Standard deviation Delta of phi (Sec. IV, Fig. 3) and its mean. */
 int tf_phi_stats(tf_ctx* ctx, int inst, double* mean, double* stddev);
+
+/* Spatial correlation functions (Sec. IV) of
+ *   TF_CORR_U: delta u_c = u_c - <u_c>,  TF_CORR_OMEGA: delta omega_c,
+ *   TF_CORR_Q: Q, with a(0) . a(r) = Q(0):Q(r) (uncentred).
+ * C[m] = mean over the displacements r of shell m of R(r) / R(0), with
+ * R(r) = <a(x) . a(x + r)>_x; r is the minimum image in lattice units and
+ * shell m collects floor(|r| + 1/2) = m, m = 0 .. tf_n_shell()-1 (longer
+ * displacements are dropped).  FP64 through the FFT (Wiener-Khinchin).
+ * Synchronous; n_shell must equal tf_n_shell(). */
+#define TF_CORR_U     0
+#define TF_CORR_OMEGA 1
+#define TF_CORR_Q     2
+int tf_correlation(tf_ctx* ctx, int inst, int which, double* C, int n_shell);
+
+/* Temporal correlation functions (Sec. IV).  tf_snapshot keeps u_c, omega_c
+ * and Q of one instance (FP32, in the workspace) as the reference time tau;
+ * tf_time_correlation returns out = [C_uu(t), C_ww(t), C_QQ(t)] =
+ * <a(tau) . a(tau + t)> / <|a(tau)|^2> (uncentred) against the current
+ * state; TF_ERR_ARG when the instance has no snapshot.  Synchronous. */
+int tf_snapshot(tf_ctx* ctx, int inst);
+int tf_time_correlation(tf_ctx* ctx, int inst, double out[3]);
+
+/* Topological defects of the director field (Sec. IV, winding number
+ * method): around every plaquette (x, y) -> (x+1, y) -> (x+1, y+1) ->
+ * (x, y+1) the director turns along each edge by its smallest rotation (a
+ * headless line: angles within (-pi/2, pi/2)); the total over 2 pi is the
+ * charge.  out = [number of +1/2, number of -1/2, number of other nonzero
+ * charges (only exact ties)]; the defect density is (out[0] + out[1]) /
+ * (nx ny).  Decided exactly: only signs of FP64 products of the stored FP32
+ * Q values enter.  Synchronous. */
+int tf_defects(tf_ctx* ctx, int inst, int64_t out[3]);
+
+/* Reynolds number of Sec. IV: Re = rho_c u_c,rms L_a / eta_c with
+ * rho_c = rho1 + rho2 (rest densities), eta_c = eta1 + eta2, eta_k =
+ * rho_k (tau_k - 1/2) / 3 (lattice units) and L_a = sqrt(K / |zeta|);
+ * zeta = 0 gives Re = L_a = +inf.  The coarsening-arrest scale L_c is the
+ * caller's time average of tf_length_scale.  Synchronous. */
+int tf_reynolds(tf_ctx* ctx, int inst, double* Re, double* L_a);
 
 /* Raw state (populations, phi, Q of every instance) as one byte blob in
  * the device storage layout.  tf_state_bytes() gives its size. */

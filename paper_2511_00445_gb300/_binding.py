@@ -29,6 +29,8 @@ NOALLOC_MAX_ELEMS = 4096 * 1024
 FIELD_PHI, FIELD_QXX, FIELD_QXY = 0, 1, 2
 FIELD_U1X, FIELD_U1Y, FIELD_U2X, FIELD_U2Y = 3, 4, 5, 6
 FIELD_RHO1, FIELD_RHO2, FIELD_MU = 7, 8, 9
+FIELD_E_ELASTIC, FIELD_E_KIN, FIELD_UC_MAG, FIELD_OMEGA_C = 10, 11, 12, 13
+CORR_U, CORR_OMEGA, CORR_Q = 0, 1, 2
 FIELD_F1, FIELD_F2 = 16, 32
 STORE_F32 = 0
 STORE_F16 = 1
@@ -42,6 +44,7 @@ EXPORTS = [
     "tf_write_field", "tf_set_equilibrium", "tf_read_field", "tf_step", "tf_sync",
     "tf_step_count", "tf_kernel_launches", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
     "tf_length_scale", "tf_energy_spectrum", "tf_phase_difference", "tf_phi_stats",
+    "tf_correlation", "tf_snapshot", "tf_time_correlation", "tf_defects", "tf_reynolds",
     "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load",
     "tf_ensemble_workspace_bytes", "tf_ensemble_create", "tf_ensemble_destroy",
     "tf_ensemble_last_error", "tf_ensemble_step", "tf_ensemble_sync", "tf_ensemble_autotune",
@@ -140,6 +143,11 @@ def load_library() -> ctypes.CDLL:
         "tf_energy_spectrum": (i, [vp, i, dp, i, dp]),
         "tf_phase_difference": (i, [vp, i, dp]),
         "tf_phi_stats": (i, [vp, i, dp, dp]),
+        "tf_correlation": (i, [vp, i, i, dp, i]),
+        "tf_snapshot": (i, [vp, i]),
+        "tf_time_correlation": (i, [vp, i, dp]),
+        "tf_defects": (i, [vp, i, ctypes.POINTER(ctypes.c_int64)]),
+        "tf_reynolds": (i, [vp, i, dp, dp]),
         "tf_state_bytes": (sz, [vp]),
         "tf_advance_host": (i, [vp, vp, i64, vp]),
         "tf_save": (i, [vp, ctypes.c_char_p]),
@@ -294,6 +302,30 @@ class TwoFluid:
         m, s = ctypes.c_double(), ctypes.c_double()
         self._check(self.lib.tf_phi_stats(self.ctx, inst, ctypes.byref(m), ctypes.byref(s)))
         return m.value, s.value
+
+    def correlation(self, inst: int, which: int) -> np.ndarray:
+        out = np.empty(self.n_shell())
+        self._check(self.lib.tf_correlation(self.ctx, inst, which, _dptr(out), out.size))
+        return out
+
+    def snapshot(self, inst: int):
+        self._check(self.lib.tf_snapshot(self.ctx, inst))
+
+    def time_correlation(self, inst: int) -> np.ndarray:
+        out = np.empty(3)
+        self._check(self.lib.tf_time_correlation(self.ctx, inst, _dptr(out)))
+        return out
+
+    def defects(self, inst: int) -> np.ndarray:
+        out = np.zeros(3, dtype=np.int64)
+        self._check(self.lib.tf_defects(self.ctx, inst,
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return out
+
+    def reynolds(self, inst: int):
+        re, la = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.tf_reynolds(self.ctx, inst, ctypes.byref(re), ctypes.byref(la)))
+        return re.value, la.value
 
     # -- raw state, end-to-end, checkpoints
     def state_bytes(self) -> int:

@@ -124,9 +124,10 @@ size_t tf_layout(const tf_params& p0, int batch, DevBuffers* d, char* base) {
     t.red_out = (double*)take(16 * sizeof(double));
     for (int k = 0; k < 2; ++k) t.cbuf[k] = (double2*)take(N * sizeof(double2));
     t.shell_part =
-        (double*)take((size_t)shell_blocks_for((long long)N) * (n_shell + 1) * sizeof(double));
+        (double*)take((size_t)shell_blocks_for((long long)N) * 2 * (n_shell + 1) * sizeof(double));
     t.shell_out = (double*)take((size_t)(n_shell + 1) * sizeof(double));
     t.stage = (double*)take(N * sizeof(double));
+    t.snap = (float*)take(5 * B * N * sizeof(float));
     t.flags = (int*)take(64 * sizeof(int));
     if (d) *d = t;
     return off;
@@ -165,6 +166,7 @@ int tf_create(const tf_params* params, int batch, void* d_workspace, size_t work
     ctx->storage = params[0].storage;
     ctx->N = (long long)ctx->nx * ctx->ny;
     ctx->params.assign(params, params + batch);
+    ctx->has_snap.assign(batch, 0);
     for (int b = 0; b < batch; ++b) ctx->dparams.push_back(tf_make_devparams(params[b]));
     ctx->stream = (cudaStream_t)stream;
     ctx->ws = (char*)d_workspace;
@@ -251,7 +253,7 @@ int tf_set_equilibrium(tf_ctx* ctx, int inst, const double* u1, const double* u2
 int tf_read_field(tf_ctx* ctx, int inst, int field, double* host) {
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !host) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
-    if (!((field >= TF_FIELD_PHI && field <= TF_FIELD_MU) || is_pop_field(field)))
+    if (!((field >= TF_FIELD_PHI && field <= TF_FIELD_OMEGA_C) || is_pop_field(field)))
         return fail(ctx, TF_ERR_ARG, "unknown field id");
     TF_CK(ctx, tf_launch_flush(ctx));
     TF_CK(ctx, tf_launch_read_field(ctx, inst, field, ctx->d.stage));
@@ -387,6 +389,72 @@ int tf_phi_stats(tf_ctx* ctx, int inst, double* mean, double* stddev) {
     const double var = s[1] / (double)ctx->N - md * md;
     if (mean) *mean = (double)(float)ctx->params[inst].phi_ref + md;
     if (stddev) *stddev = std::sqrt(var > 0 ? var : 0.0);
+    return TF_OK;
+}
+
+int tf_correlation(tf_ctx* ctx, int inst, int which, double* C, int n_shell) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || !C) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    if (which < TF_CORR_U || which > TF_CORR_Q) return fail(ctx, TF_ERR_ARG, "unknown correlation");
+    if (n_shell != ctx->n_shell) return fail(ctx, TF_ERR_ARG, "n_shell must equal tf_n_shell()");
+    if (ctx->nx > kMaxFFT || ctx->ny > kMaxFFT)
+        return fail(ctx, TF_ERR_ARG, "correlations need nx, ny <= 8192");
+    TF_CK(ctx, tf_launch_flush(ctx));
+    TF_CK(ctx, tf_launch_correlation(ctx, inst, which, ctx->d.shell_out));
+    TF_CK(ctx, cudaMemcpyAsync(C, ctx->d.shell_out, n_shell * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
+int tf_snapshot(tf_ctx* ctx, int inst) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst)) return fail(ctx, TF_ERR_ARG, "bad instance index");
+    TF_CK(ctx, tf_launch_flush(ctx));
+    TF_CK(ctx, tf_launch_snapshot(ctx, inst));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->has_snap[inst] = 1;
+    return TF_OK;
+}
+
+int tf_time_correlation(tf_ctx* ctx, int inst, double out[3]) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    if (!ctx->has_snap[inst]) return fail(ctx, TF_ERR_ARG, "no snapshot for this instance");
+    TF_CK(ctx, tf_launch_flush(ctx));
+    TF_CK(ctx, tf_launch_time_correlation(ctx, inst, ctx->d.red_out));
+    double s[6];
+    TF_CK(ctx, cudaMemcpyAsync(s, ctx->d.red_out, 6 * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 3; ++k) out[k] = s[2 * k + 1] != 0.0 ? s[2 * k] / s[2 * k + 1] : 0.0;
+    return TF_OK;
+}
+
+int tf_defects(tf_ctx* ctx, int inst, int64_t out[3]) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
+    TF_CK(ctx, tf_launch_flush(ctx));
+    TF_CK(ctx, tf_launch_defects(ctx, inst, ctx->d.red_out));
+    double s[3];
+    TF_CK(ctx, cudaMemcpyAsync(s, ctx->d.red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 3; ++k) out[k] = (int64_t)s[k];   // exact: counts far below 2^53
+    return TF_OK;
+}
+
+int tf_reynolds(tf_ctx* ctx, int inst, double* Re, double* L_a) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!valid_inst(ctx, inst) || (!Re && !L_a)) return fail(ctx, TF_ERR_ARG, "bad instance or null pointers");
+    double ph[6];
+    const int rc = tf_phase_difference(ctx, inst, ph);
+    if (rc != TF_OK) return rc;
+    const tf_params& p = ctx->params[inst];
+    const double La = p.zeta != 0.0 ? std::sqrt(p.K / std::fabs(p.zeta)) : HUGE_VAL;
+    const double eta = p.rho1 * (p.tau1 - 0.5) / 3.0 + p.rho2 * (p.tau2 - 0.5) / 3.0;
+    if (L_a) *L_a = La;
+    if (Re) *Re = p.zeta != 0.0 ? (p.rho1 + p.rho2) * ph[3] * La / eta : HUGE_VAL;
     return TF_OK;
 }
 

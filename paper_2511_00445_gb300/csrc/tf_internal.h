@@ -110,9 +110,10 @@ struct DevBuffers {
     double* red_part;  // reduction partials [B][red_blocks][8]
     double* red_out;   // reduction results [B][8]
     double2* cbuf[2];  // complex FFT buffers, N each
-    double* shell_part;// shell histogram partials [shell_blocks][n_shell]
+    double* shell_part;// shell histogram partials [shell_blocks][2 (n_shell + 1)]
     double* shell_out; // [n_shell]
     double* stage;     // FP64 staging plane [N] (and small results)
+    float* snap;       // reference fields of the temporal correlations [B][5][N]
     int* flags;        // device status words
 };
 
@@ -132,6 +133,7 @@ struct tf_ctx {
     int64_t steps = 0;
     int64_t launches = 0;            // kernels launched by this context
     int n_shell = 0;
+    std::vector<char> has_snap;      // per instance: tf_snapshot taken
     int red_blocks = 0;
     int shell_blocks = 0;
     std::string last_error;
@@ -177,5 +179,13 @@ cudaError_t tf_launch_phi_stats(tf_ctx* ctx, int inst, double* dout2);
 // total to d.shell_out[n_shell].
 cudaError_t tf_launch_spectrum(tf_ctx* ctx, int inst, int which);
 cudaError_t tf_launch_shell_counts(tf_ctx* ctx);
+// Shell-averaged spatial correlation (which = TF_CORR_*) into dout[n_shell].
+cudaError_t tf_launch_correlation(tf_ctx* ctx, int inst, int which, double* dout);
+// Reference fields for the temporal correlations; then the six sums
+// (uu', uu, ww', ww, QQ', QQ) against the current state.
+cudaError_t tf_launch_snapshot(tf_ctx* ctx, int inst);
+cudaError_t tf_launch_time_correlation(tf_ctx* ctx, int inst, double* dout6);
+// Plaquette charge counts (+1/2, -1/2, other) as doubles.
+cudaError_t tf_launch_defects(tf_ctx* ctx, int inst, double* dout3);
 // One-time kernel attributes (large dynamic shared memory).
 cudaError_t tf_configure_observe_kernels();

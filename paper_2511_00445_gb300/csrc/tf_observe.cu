@@ -133,6 +133,65 @@ k_set_eq(void* __restrict__ f, const double* __restrict__ u1, const double* __re
     }
 }
 
+// ------------------------------------------------- derived flow quantities
+// u_c = phi u1 + (1 - phi) u2 (component comp) at site p of instance b, FP64.
+__device__ __forceinline__ double mixture_u(const float* __restrict__ phi,
+                                            const float* __restrict__ mac, long long N, int b,
+                                            double c, int comp, long long p) {
+    const float* m = mac + 8 * b * N;
+    const double pv = c + (double)phi[b * N + p];
+    return pv * (double)m[comp * N + p] + (1.0 - pv) * (double)m[(comp + 2) * N + p];
+}
+
+// Periodic neighbours of site i: east, west, north, south.
+struct Nbrs {
+    long long e, w, n, s;
+};
+__device__ __forceinline__ Nbrs nbrs_of(long long i, int nx, int ny) {
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    Nbrs r;
+    r.e = (long long)y * nx + (x + 1 < nx ? x + 1 : 0);
+    r.w = (long long)y * nx + (x > 0 ? x - 1 : nx - 1);
+    r.n = (long long)(y + 1 < ny ? y + 1 : 0) * nx + x;
+    r.s = (long long)(y > 0 ? y - 1 : ny - 1) * nx + x;
+    return r;
+}
+
+// omega_c = d_x u_c,y - d_y u_c,x, central differences.
+__device__ __forceinline__ double mixture_vorticity(const float* __restrict__ phi,
+                                                    const float* __restrict__ mac, int nx,
+                                                    int ny, int b, double c, long long i) {
+    const long long N = (long long)nx * ny;
+    const Nbrs g = nbrs_of(i, nx, ny);
+    return 0.5 * (mixture_u(phi, mac, N, b, c, 1, g.e) - mixture_u(phi, mac, N, b, c, 1, g.w)) -
+           0.5 * (mixture_u(phi, mac, N, b, c, 0, g.n) - mixture_u(phi, mac, N, b, c, 0, g.s));
+}
+
+// Energy and flow maps of Sec. IV (Fig. 6) at site i.
+__device__ double energy_map(const float* __restrict__ phi, const float* __restrict__ Q,
+                             const float* __restrict__ mac, int nx, int ny, int b, long long i,
+                             int field, const DevParams* __restrict__ prm) {
+    const long long N = (long long)nx * ny;
+    const double c = prm[b].phi_ref;
+    if (field == TF_FIELD_E_ELASTIC) {
+        // K/2 sum_{k,i,j} (d_k Q_ij)^2 = K sum_k [(d_k Q_xx)^2 + (d_k Q_xy)^2]
+        const float* qa = Q + 2 * b * N;
+        const float* qb = qa + N;
+        const Nbrs g = nbrs_of(i, nx, ny);
+        const double ax = 0.5 * ((double)qa[g.e] - (double)qa[g.w]);
+        const double ay = 0.5 * ((double)qa[g.n] - (double)qa[g.s]);
+        const double bx = 0.5 * ((double)qb[g.e] - (double)qb[g.w]);
+        const double by = 0.5 * ((double)qb[g.n] - (double)qb[g.s]);
+        return (double)prm[b].K * (ax * ax + ay * ay + bx * bx + by * by);
+    }
+    if (field == TF_FIELD_OMEGA_C) return mixture_vorticity(phi, mac, nx, ny, b, c, i);
+    const double ux = mixture_u(phi, mac, N, b, c, 0, i), uy = mixture_u(phi, mac, N, b, c, 1, i);
+    const double uu = ux * ux + uy * uy;
+    if (field == TF_FIELD_UC_MAG) return sqrt(uu);
+    const float* m = mac + 8 * b * N;
+    return 0.5 * ((double)m[4 * N + i] + (double)m[5 * N + i]) * uu;   // E_kin
+}
+
 // ---------------------------------------------------------- field reads
 __global__ void __launch_bounds__(RB)
 k_read(const void* __restrict__ f, const float* __restrict__ phi, const float* __restrict__ Q,
@@ -150,6 +209,8 @@ k_read(const void* __restrict__ f, const float* __restrict__ phi, const float* _
         v = (double)mac[(8 * b + (field - TF_FIELD_U1X)) * N + i];
     } else if (field == TF_FIELD_MU) {
         v = (double)mu[b * N + i];
+    } else if (field >= TF_FIELD_E_ELASTIC && field <= TF_FIELD_OMEGA_C) {
+        v = energy_map(phi, Q, mac, nx, ny, b, i, field, prm);
     } else {
         const int fl = field >= TF_FIELD_F2 ? 1 : 0;
         const int k = field - (fl ? TF_FIELD_F2 : TF_FIELD_F1);
@@ -398,6 +459,177 @@ k_shell_finish(const double* __restrict__ part, int nparts, int n_shell, double*
     }
 }
 
+// ---------------------------------------------------------- correlations
+// Correlated quantity of instance b as complex doubles (ny rows of nx):
+// TF_CORR_U (u_c,x, u_c,y), TF_CORR_OMEGA (omega_c, 0), TF_CORR_Q (Q_xx, Q_xy).
+__global__ void __launch_bounds__(RB)
+k_corr_load(const float* __restrict__ phi, const float* __restrict__ Q,
+            const float* __restrict__ mac, int nx, int ny, int b, int which,
+            const DevParams* __restrict__ prm, double2* __restrict__ out) {
+    const long long N = (long long)nx * ny;
+    const long long i = (long long)blockIdx.x * RB + threadIdx.x;
+    if (i >= N) return;
+    const double c = prm[b].phi_ref;
+    if (which == TF_CORR_U)
+        out[i] = make_double2(mixture_u(phi, mac, N, b, c, 0, i), mixture_u(phi, mac, N, b, c, 1, i));
+    else if (which == TF_CORR_OMEGA)
+        out[i] = make_double2(mixture_vorticity(phi, mac, nx, ny, b, c, i), 0.0);
+    else
+        out[i] = make_double2((double)Q[2 * b * N + i], (double)Q[(2 * b + 1) * N + i]);
+}
+
+// Power of the (one or two) real components packed in z = a + i b:
+// |a_hat(k)|^2 + |b_hat(k)|^2 = (|Z(k)|^2 + |Z(-k)|^2) / 2, written as (P, 0)
+// in the same [jx][jy] layout (nx rows of ny).  centred: drop k = 0.
+__global__ void __launch_bounds__(RB)
+k_corr_power(const double2* __restrict__ T, int nx, int ny, int centred,
+             double2* __restrict__ out) {
+    const long long N = (long long)nx * ny;
+    const long long i = (long long)blockIdx.x * RB + threadIdx.x;
+    if (i >= N) return;
+    const int jx = (int)(i / ny), jy = (int)(i % ny);
+    const int mx = jx == 0 ? 0 : nx - jx, my = jy == 0 ? 0 : ny - jy;
+    const double2 z = T[i], w = T[(long long)mx * ny + my];
+    double p = 0.5 * ((z.x * z.x + z.y * z.y) + (w.x * w.x + w.y * w.y));
+    if (centred && jx == 0 && jy == 0) p = 0.0;
+    out[i] = make_double2(p, 0.0);
+}
+
+// Shell of displacement (rx, ry) (array positions): floor(|r| + 1/2) with the
+// minimum image r, separately rounded IEEE operations.
+__device__ __forceinline__ int rshell_of(int rx, int ry, int nx, int ny) {
+    const double tx = (double)signed_mode(rx, nx), ty = (double)signed_mode(ry, ny);
+    const double r = __dsqrt_rn(__dadd_rn(__dmul_rn(tx, tx), __dmul_rn(ty, ty)));
+    return (int)floor(__dadd_rn(r, 0.5));
+}
+
+// Shell sums of Re R(r) and displacement counts over R[ry][rx] (ny rows of nx):
+// per-block partials [2 * n_shell] (sums, then counts).
+__global__ void __launch_bounds__(RB)
+k_rshell_bin(const double2* __restrict__ R, int nx, int ny, int n_shell,
+             double* __restrict__ part) {
+    extern __shared__ double hist[];
+    for (int k = threadIdx.x; k < 2 * n_shell; k += RB) hist[k] = 0.0;
+    __syncthreads();
+    const long long N = (long long)nx * ny;
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < N;
+         i += (long long)gridDim.x * RB) {
+        const int ry = (int)(i / nx), rx = (int)(i % nx);
+        const int sh = rshell_of(rx, ry, nx, ny);
+        if (sh < n_shell) {
+            atomicAdd(&hist[sh], R[i].x);
+            atomicAdd(&hist[n_shell + sh], 1.0);
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * n_shell; k += RB)
+        part[(long long)blockIdx.x * 2 * n_shell + k] = hist[k];
+}
+
+// out[m] = (shell-m sum / shell-m count) / R(0), partials summed in block order.
+__global__ void __launch_bounds__(RB)
+k_rshell_finish(const double* __restrict__ part, int nparts, int n_shell,
+                const double2* __restrict__ R, double* __restrict__ out) {
+    const double r0 = R[0].x;
+    for (int k = blockIdx.x * RB + threadIdx.x; k < n_shell; k += gridDim.x * RB) {
+        double s = 0.0, n = 0.0;
+        for (int j = 0; j < nparts; ++j) {
+            s += part[(long long)j * 2 * n_shell + k];
+            n += part[(long long)j * 2 * n_shell + n_shell + k];
+        }
+        out[k] = n > 0.0 && r0 != 0.0 ? s / n / r0 : 0.0;
+    }
+}
+
+// Snapshot of instance b: u_c,x, u_c,y, omega_c, Q_xx, Q_xy (FP32 planes).
+__global__ void __launch_bounds__(RB)
+k_snapshot(const float* __restrict__ phi, const float* __restrict__ Q,
+           const float* __restrict__ mac, int nx, int ny, int b,
+           const DevParams* __restrict__ prm, float* __restrict__ snap) {
+    const long long N = (long long)nx * ny;
+    const long long i = (long long)blockIdx.x * RB + threadIdx.x;
+    if (i >= N) return;
+    const double c = prm[b].phi_ref;
+    float* o = snap + 5 * b * N;
+    o[i] = (float)mixture_u(phi, mac, N, b, c, 0, i);
+    o[N + i] = (float)mixture_u(phi, mac, N, b, c, 1, i);
+    o[2 * N + i] = (float)mixture_vorticity(phi, mac, nx, ny, b, c, i);
+    o[3 * N + i] = Q[2 * b * N + i];
+    o[4 * N + i] = Q[(2 * b + 1) * N + i];
+}
+
+// Sums of a(snapshot) . a(now) and |a(snapshot)|^2 for u_c, omega_c, Q:
+// partials [6] = (uu', uu, ww', ww, QQ', QQ).
+__global__ void __launch_bounds__(RB)
+k_timecorr(const float* __restrict__ phi, const float* __restrict__ Q,
+           const float* __restrict__ mac, const float* __restrict__ snap, int nx, int ny, int b,
+           const DevParams* __restrict__ prm, double* __restrict__ part) {
+    const long long N = (long long)nx * ny;
+    const double c = prm[b].phi_ref;
+    const float* o = snap + 5 * b * N;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < N;
+         i += (long long)gridDim.x * RB) {
+        const double ax = o[i], ay = o[N + i], aw = o[2 * N + i], aq = o[3 * N + i],
+                     bq = o[4 * N + i];
+        const double ux = mixture_u(phi, mac, N, b, c, 0, i), uy = mixture_u(phi, mac, N, b, c, 1, i);
+        const double w = mixture_vorticity(phi, mac, nx, ny, b, c, i);
+        const double qa = Q[2 * b * N + i], qb = Q[(2 * b + 1) * N + i];
+        v[0] += ax * ux + ay * uy;
+        v[1] += ax * ax + ay * ay;
+        v[2] += aw * w;
+        v[3] += aw * aw;
+        v[4] += aq * qa + bq * qb;
+        v[5] += aq * aq + bq * bq;
+    }
+    block_sum<6>(v);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) part[blockIdx.x * 6 + k] = v[k];
+}
+
+// ---------------------------------------------------------------- defects
+// Winding of the doubled director angle, i.e. of the vector (Q_xx, Q_xy),
+// along one edge a -> b turned by its smallest rotation: +1 when that
+// rotation crosses the positive x half-axis counter-clockwise, -1 clockwise.
+// a.y*b.x and a.x*b.y are exact in FP64 for FP32 inputs and the sign of
+// their difference is exact, so the decision is exact.  An antiparallel pair
+// (cross product 0) contributes nothing.
+__device__ __forceinline__ int edge_crossing(double ax, double ay, double bx, double by) {
+    const double cr = ax * by - ay * bx;
+    if (ay < 0.0 && by >= 0.0 && cr > 0.0) return 1;
+    if (by < 0.0 && ay >= 0.0 && cr < 0.0) return -1;
+    return 0;
+}
+
+// Counts of plaquette charges +1/2, -1/2 and other nonzero (partials [3]).
+__global__ void __launch_bounds__(RB)
+k_defects(const float* __restrict__ Q, int nx, int ny, int b, double* __restrict__ part) {
+    const long long N = (long long)nx * ny;
+    const float* qa = Q + 2 * b * N;
+    const float* qb = qa + N;
+    double v[3] = {0, 0, 0};
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < N;
+         i += (long long)gridDim.x * RB) {
+        const int x = (int)(i % nx), y = (int)(i / nx);
+        const int xp = x + 1 < nx ? x + 1 : 0, yp = y + 1 < ny ? y + 1 : 0;
+        const long long c[4] = {(long long)y * nx + x, (long long)y * nx + xp,
+                                (long long)yp * nx + xp, (long long)yp * nx + x};
+        int w = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const long long p = c[k], q = c[(k + 1) & 3];
+            w += edge_crossing(qa[p], qb[p], qa[q], qb[q]);
+        }
+        // w winds the doubled angle: the charge is w / 2
+        if (w == 1) v[0] += 1.0;
+        else if (w == -1) v[1] += 1.0;
+        else if (w != 0) v[2] += 1.0;
+    }
+    block_sum<3>(v);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = v[k];
+}
+
 inline unsigned nblk(long long N) { return (unsigned)((N + RB - 1) / RB); }
 
 }  // namespace
@@ -442,7 +674,8 @@ cudaError_t tf_launch_set_equilibrium(tf_ctx* ctx, int inst, const double* du1,
 
 cudaError_t tf_launch_read_field(tf_ctx* ctx, int inst, int field, double* ddst) {
     const DevBuffers& d = ctx->d;
-    if ((field >= TF_FIELD_U1X && field <= TF_FIELD_RHO2) || field == TF_FIELD_MU) {
+    if ((field >= TF_FIELD_U1X && field <= TF_FIELD_RHO2) || field == TF_FIELD_MU ||
+        (field >= TF_FIELD_E_KIN && field <= TF_FIELD_OMEGA_C)) {
         cudaError_t e = tf_launch_macro(ctx, d.macro);
         if (e != cudaSuccess) return e;
     }
@@ -524,11 +757,78 @@ cudaError_t tf_launch_shell_counts(tf_ctx* ctx) {
     return cudaGetLastError();
 }
 
+// 2-D forward DFT: `in` holds `rows` rows of `cols`; the result lands in
+// `out` as cols rows of `rows` (transposed).
+static cudaError_t fft2d(cudaStream_t st, double2* in, double2* out, int rows, int cols) {
+    k_fft_rows<<<rows, RB, cols * sizeof(double2), st>>>(in, cols);
+    dim3 tb(32, 8), tg((cols + 31) / 32, (rows + 31) / 32);
+    k_transpose<<<tg, tb, 0, st>>>(in, out, rows, cols);
+    k_fft_rows<<<cols, RB, rows * sizeof(double2), st>>>(out, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t tf_launch_correlation(tf_ctx* ctx, int inst, int which, double* dout) {
+    const DevBuffers& d = ctx->d;
+    const int nx = ctx->nx, ny = ctx->ny;
+    if (which != TF_CORR_Q) {
+        cudaError_t e = tf_launch_macro(ctx, d.macro);
+        if (e != cudaSuccess) return e;
+    }
+    k_corr_load<<<nblk(ctx->N), RB, 0, ctx->stream>>>(d.phi[ctx->pcur], d.Q[ctx->pcur], d.macro,
+                                                      nx, ny, inst, which, d.prm, d.cbuf[0]);
+    // cbuf[0] (ny x nx) -> cbuf[1] = spectrum [jx][jy]
+    cudaError_t e = fft2d(ctx->stream, d.cbuf[0], d.cbuf[1], ny, nx);
+    if (e != cudaSuccess) return e;
+    k_corr_power<<<nblk(ctx->N), RB, 0, ctx->stream>>>(d.cbuf[1], nx, ny, which != TF_CORR_Q,
+                                                       d.cbuf[0]);
+    // The power is even in k, so its forward transform is N^2 R(r):
+    // cbuf[0] (nx x ny) -> cbuf[1] = [ry][rx]
+    e = fft2d(ctx->stream, d.cbuf[0], d.cbuf[1], nx, ny);
+    if (e != cudaSuccess) return e;
+    const size_t shm = (size_t)(2 * ctx->n_shell) * sizeof(double);
+    k_rshell_bin<<<ctx->shell_blocks, RB, shm, ctx->stream>>>(d.cbuf[1], nx, ny, ctx->n_shell,
+                                                              d.shell_part);
+    k_rshell_finish<<<(ctx->n_shell + RB - 1) / RB, RB, 0, ctx->stream>>>(
+        d.shell_part, ctx->shell_blocks, ctx->n_shell, d.cbuf[1], dout);
+    return cudaGetLastError();
+}
+
+cudaError_t tf_launch_snapshot(tf_ctx* ctx, int inst) {
+    const DevBuffers& d = ctx->d;
+    cudaError_t e = tf_launch_macro(ctx, d.macro);
+    if (e != cudaSuccess) return e;
+    k_snapshot<<<nblk(ctx->N), RB, 0, ctx->stream>>>(d.phi[ctx->pcur], d.Q[ctx->pcur], d.macro,
+                                                     ctx->nx, ctx->ny, inst, d.prm, d.snap);
+    return cudaGetLastError();
+}
+
+cudaError_t tf_launch_time_correlation(tf_ctx* ctx, int inst, double* dout6) {
+    const DevBuffers& d = ctx->d;
+    cudaError_t e = tf_launch_macro(ctx, d.macro);
+    if (e != cudaSuccess) return e;
+    k_timecorr<<<ctx->red_blocks, RB, 0, ctx->stream>>>(d.phi[ctx->pcur], d.Q[ctx->pcur], d.macro,
+                                                       d.snap, ctx->nx, ctx->ny, inst, d.prm,
+                                                       d.red_part);
+    k_finish<6><<<1, RB, 0, ctx->stream>>>(d.red_part, ctx->red_blocks, dout6);
+    return cudaGetLastError();
+}
+
+cudaError_t tf_launch_defects(tf_ctx* ctx, int inst, double* dout3) {
+    const DevBuffers& d = ctx->d;
+    k_defects<<<ctx->red_blocks, RB, 0, ctx->stream>>>(d.Q[ctx->pcur], ctx->nx, ctx->ny, inst,
+                                                      d.red_part);
+    k_finish<3><<<1, RB, 0, ctx->stream>>>(d.red_part, ctx->red_blocks, dout3);
+    return cudaGetLastError();
+}
+
 cudaError_t tf_configure_observe_kernels() {
     // The row FFT and the shell histogram may need more than 48 KB of
     // dynamic shared memory (rows up to 8192 points, up to 8192 shells).
     cudaError_t e = cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          8192 * (int)sizeof(double2));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_rshell_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * 8193 * (int)sizeof(double));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_shell_bin, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 8193 * (int)sizeof(double));
