@@ -313,6 +313,85 @@ int tf_ensemble_config(const tf_ensemble* ens, int* tile_y, int* ctas_per_sm, in
  * one kernel). */
 int64_t tf_ensemble_launches(const tf_ensemble* ens);
 
+/* ---- learned surrogate: a U-Net that advances a state by many steps ---- */
+/* The paper has no learned component; this layer is a convolutional
+ * surrogate of the coupled step: from (phi, Q_xx, Q_xy, u1, u2) at time t of
+ * one instance (plus its activity zeta as a constant input plane) it predicts
+ * the fields at t + horizon, trained on pairs the solver itself produces,
+ * with the plain method as the judge of its error (observables above).
+ *
+ * Network (NHWC activations in BF16, FP32 master weights and accumulation):
+ * `levels` U-Net levels with C_l = base_channels * 2^l channels; per level two
+ * 3x3 convolutions with circular padding (the lattice is periodic) + ReLU;
+ * 2x2 average pooling down, nearest-neighbour upsampling up, skip
+ * concatenation [upsampled, skip], and a 1x1 head to 7 outputs.  Inputs:
+ * 8 channels, the 7 fields normalised per channel by the dataset's mean and
+ * standard deviation and zeta / max|zeta|; outputs: the 7 increments
+ * x(t + horizon) - x(t), normalised the same way.  The 3x3 convolutions,
+ * their input gradients and their weight gradients run as tcgen05 tensor-
+ * core GEMMs; Adam updates the FP32 weights.  Loss: mean squared error of the
+ * normalised increments.
+ *
+ * Flat parameter vector (tf_sur_set_weights / tf_sur_get_weights /
+ * tf_sur_gradients): for every 3x3 convolution in order (encoder level 0 ..
+ * levels-1, two each; then decoder level levels-2 .. 0, two each) its weights
+ * W[out][ky][kx][in] (tap (ky, kx) reads the input at (y + ky - 1,
+ * x + kx - 1)) and biases b[out]; then the head W[7][C_0] and b[7]. */
+typedef struct tf_surrogate tf_surrogate;
+typedef struct tf_sur_config {
+    int levels;         /* 1..5                                                  */
+    int base_channels;  /* C_0: 16, 32 or 64                                     */
+    int nx, ny;         /* lattice size: multiples of 8 * 2^(levels-1)           */
+    int max_batch;      /* minibatch capacity, >= 1                              */
+    int max_pairs;      /* training-pair capacity, >= 1                          */
+    int horizon;        /* lattice steps one prediction spans, >= 1              */
+} tf_sur_config;
+#define TF_SUR_IN   8   /* phi - phi_ref, Q_xx, Q_xy, u1x, u1y, u2x, u2y, zeta */
+#define TF_SUR_OUT  7
+
+size_t tf_sur_workspace_bytes(const tf_sur_config* cfg);   /* 0 if cfg is invalid */
+int tf_sur_create(const tf_sur_config* cfg, void* d_workspace, size_t workspace_bytes,
+                  void* stream, tf_surrogate** out);
+int tf_sur_destroy(tf_surrogate* s);
+const char* tf_sur_last_error(const tf_surrogate* s);
+int64_t tf_sur_num_params(const tf_surrogate* s);
+
+/* Weights: He-normal initialisation from a seeded SplitMix64 stream, or a
+ * copy of `n` FP32 values in the flat order above (host arrays). */
+int tf_sur_init_weights(tf_surrogate* s, uint64_t seed);
+int tf_sur_set_weights(tf_surrogate* s, const float* host, int64_t n);
+int tf_sur_get_weights(tf_surrogate* s, float* host, int64_t n);
+
+/* Direct access for checks: `x` holds batch x ny x nx x 8 normalised inputs
+ * (host, FP32, rounded to BF16 on upload), `target` batch x ny x nx x 7.
+ * tf_sur_forward writes the batch x ny x nx x 7 outputs; tf_sur_gradients the
+ * loss and the flat gradient of the loss with respect to the weights.
+ * Synchronous. */
+int tf_sur_forward(tf_surrogate* s, const float* x, int batch, float* out);
+int tf_sur_gradients(tf_surrogate* s, const float* x, const float* target, int batch,
+                     double* loss, float* grad, int64_t n);
+
+/* Training data from a solver context with the same nx, ny (it must share
+ * the surrogate's stream): which = 0 stores instance `inst`'s current fields
+ * as the input of pair `slot`, which = 1 as its target; the caller advances
+ * the context by `horizon` steps in between.  tf_sur_fit_normalisation
+ * derives the per-channel statistics from pairs 0 .. n_pairs-1. */
+int tf_sur_add_pair(tf_surrogate* s, int slot, tf_ctx* ctx, int inst, int which);
+int tf_sur_fit_normalisation(tf_surrogate* s, int n_pairs);
+
+/* `steps` Adam steps (learning rate lr, betas 0.9 / 0.999) on minibatches of
+ * `batch` pairs drawn from 0 .. n_pairs-1 by a seeded SplitMix64 stream;
+ * losses[i] (may be NULL) receives the loss of step i.  Synchronous. */
+int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, uint64_t seed,
+                 double* losses);
+
+/* Advance instance `inst` of `ctx` by `horizon` steps with the network: its
+ * phi and Q are replaced by the prediction and its populations by the
+ * equilibrium of its rest densities and the predicted u1, u2.  The
+ * context's step count (one counter for all its instances) is unchanged.
+ * Asynchronous on the shared stream. */
+int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst);
+
 /* ---- fixed-footprint entry point ------------------------------------- */
 /* The paper has no counterpart to this call; it exists for integration.
  *

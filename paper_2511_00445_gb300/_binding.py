@@ -48,8 +48,20 @@ EXPORTS = [
     "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load",
     "tf_ensemble_workspace_bytes", "tf_ensemble_create", "tf_ensemble_destroy",
     "tf_ensemble_last_error", "tf_ensemble_step", "tf_ensemble_sync", "tf_ensemble_autotune",
-    "tf_ensemble_config", "tf_ensemble_launches", "tf_phi_stats_noalloc",
+    "tf_ensemble_config", "tf_ensemble_launches",
+    "tf_sur_workspace_bytes", "tf_sur_create", "tf_sur_destroy", "tf_sur_last_error",
+    "tf_sur_num_params", "tf_sur_init_weights", "tf_sur_set_weights", "tf_sur_get_weights",
+    "tf_sur_forward", "tf_sur_gradients", "tf_sur_add_pair", "tf_sur_fit_normalisation",
+    "tf_sur_train", "tf_sur_predict", "tf_phi_stats_noalloc",
 ]
+SUR_IN, SUR_OUT = 8, 7
+
+
+class TFSurConfig(ctypes.Structure):
+    """Mirror of struct tf_sur_config."""
+    _fields_ = [("levels", ctypes.c_int), ("base_channels", ctypes.c_int), ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_pairs", ctypes.c_int),
+                ("horizon", ctypes.c_int)]
 ENS_CANDIDATES = 6
 
 
@@ -122,6 +134,7 @@ def load_library() -> ctypes.CDLL:
     vp, i, i64, d, dp, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
                              ctypes.POINTER(ctypes.c_double), ctypes.c_size_t)
     P = ctypes.POINTER(TFParams)
+    fp = ctypes.POINTER(ctypes.c_float)
     sig = {
         "tf_workspace_bytes": (sz, [P, i]),
         "tf_create": (i, [P, i, vp, sz, vp, ctypes.POINTER(vp)]),
@@ -162,6 +175,20 @@ def load_library() -> ctypes.CDLL:
         "tf_ensemble_config": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i64), dp, ctypes.POINTER(i)]),
         "tf_ensemble_launches": (i64, [vp]),
+        "tf_sur_workspace_bytes": (sz, [ctypes.POINTER(TFSurConfig)]),
+        "tf_sur_create": (i, [ctypes.POINTER(TFSurConfig), vp, sz, vp, ctypes.POINTER(vp)]),
+        "tf_sur_destroy": (i, [vp]),
+        "tf_sur_last_error": (ctypes.c_char_p, [vp]),
+        "tf_sur_num_params": (i64, [vp]),
+        "tf_sur_init_weights": (i, [vp, ctypes.c_uint64]),
+        "tf_sur_set_weights": (i, [vp, fp, i64]),
+        "tf_sur_get_weights": (i, [vp, fp, i64]),
+        "tf_sur_forward": (i, [vp, fp, i, fp]),
+        "tf_sur_gradients": (i, [vp, fp, fp, i, dp, fp, i64]),
+        "tf_sur_add_pair": (i, [vp, i, vp, i, i]),
+        "tf_sur_fit_normalisation": (i, [vp, i]),
+        "tf_sur_train": (i, [vp, i, i, i, d, ctypes.c_uint64, dp]),
+        "tf_sur_predict": (i, [vp, vp, i]),
         "tf_phi_stats_noalloc": (i, [vp, ctypes.c_longlong, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -403,3 +430,88 @@ class Ensemble:
 
     def launches(self) -> int:
         return int(self.lib.tf_ensemble_launches(self.ens))
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Surrogate:
+    """The U-Net surrogate behind the tf_sur_* entry points (see twofluid.h).
+    Arrays are NHWC float32 numpy arrays; the workspace lives in torch memory."""
+
+    def __init__(self, levels=4, base_channels=32, nx=256, ny=256, max_batch=8, max_pairs=64,
+                 horizon=50, device="cuda", stream=None):
+        import torch
+        self.lib = load_library()
+        self.cfg = TFSurConfig(levels, base_channels, nx, ny, max_batch, max_pairs, horizon)
+        nbytes = self.lib.tf_sur_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise TwoFluidError(TF_ERR_ARG, "invalid surrogate configuration")
+        self.device = torch.device(device)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        rc = self.lib.tf_sur_create(ctypes.byref(self.cfg), ctypes.c_void_p(aligned), nbytes,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != TF_OK:
+            raise TwoFluidError(rc, "tf_sur_create failed")
+        self.h = h
+        self.n_params = int(self.lib.tf_sur_num_params(h))
+
+    def _check(self, rc: int):
+        if rc != TF_OK:
+            raise TwoFluidError(rc, self.lib.tf_sur_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tf_sur_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_weights(self, seed: int):
+        self._check(self.lib.tf_sur_init_weights(self.h, seed))
+
+    def set_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(self.lib.tf_sur_set_weights(self.h, _fptr(w), w.size))
+
+    def get_weights(self) -> np.ndarray:
+        w = np.empty(self.n_params, dtype=np.float32)
+        self._check(self.lib.tf_sur_get_weights(self.h, _fptr(w), w.size))
+        return w
+
+    def forward(self, x: np.ndarray) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty(x.shape[:3] + (SUR_OUT,), dtype=np.float32)
+        self._check(self.lib.tf_sur_forward(self.h, _fptr(x), x.shape[0], _fptr(out)))
+        return out
+
+    def gradients(self, x: np.ndarray, target: np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self.lib.tf_sur_gradients(self.h, _fptr(x), _fptr(t), x.shape[0],
+                                              ctypes.byref(loss), _fptr(g), g.size))
+        return loss.value, g
+
+    def add_pair(self, slot: int, solver: TwoFluid, inst: int, which: int):
+        self._check(self.lib.tf_sur_add_pair(self.h, slot, solver.ctx, inst, which))
+
+    def fit_normalisation(self, n_pairs: int):
+        self._check(self.lib.tf_sur_fit_normalisation(self.h, n_pairs))
+
+    def train(self, n_pairs: int, steps: int, batch: int, lr: float, seed: int = 0) -> np.ndarray:
+        losses = np.zeros(steps)
+        self._check(self.lib.tf_sur_train(self.h, n_pairs, steps, batch, lr, seed, _dptr(losses)))
+        return losses
+
+    def predict(self, solver: TwoFluid, inst: int):
+        self._check(self.lib.tf_sur_predict(self.h, solver.ctx, inst))

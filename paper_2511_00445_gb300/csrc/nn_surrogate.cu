@@ -1,0 +1,1033 @@
+// Convolutional surrogate of the coupled step (declared in include/twofluid.h):
+// U-Net forward / backward with tcgen05 GEMMs (nn_tc.cuh), Adam, training
+// pairs captured from solver contexts, and prediction back into a context.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nn_tc.cuh"
+#include "tf_internal.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+constexpr int EB = 256;             // threads of the element-wise kernels
+constexpr int CIN = TF_SUR_IN, COUT = TF_SUR_OUT;
+
+__device__ __forceinline__ int wrap_i(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// ------------------------------------------------------------ GEMM operations
+// Forward 3x3 convolution with circular padding, bias and optional ReLU:
+// out[p][o] = b[o] + sum_{tap, c} W[o][tap][c] in[p + d(tap)][c].
+struct ConvFwd {
+    int M, N, K;
+    int* err;
+    const bf16* in;
+    const bf16* w;       // [cout][9 cin]
+    const float* bias;
+    bf16* out;
+    int H, W, cin, cout, relu;
+    __device__ uint4 a_chunk(int m, int k8) const {
+        const int k = k8 * 8;
+        if (m >= M || k >= K) return make_uint4(0, 0, 0, 0);
+        const int tap = k / cin, c0 = k - tap * cin;
+        const int x = m % W, t = m / W, y = t % H, b = t / H;
+        const int yy = wrap_i(y + tap / 3 - 1, H), xx = wrap_i(x + tap % 3 - 1, W);
+        return *reinterpret_cast<const uint4*>(in + ((size_t)(b * H + yy) * W + xx) * cin + c0);
+    }
+    __device__ uint4 b_chunk(int n, int k8) const {
+        const int k = k8 * 8;
+        if (n >= N || k >= K) return make_uint4(0, 0, 0, 0);
+        return *reinterpret_cast<const uint4*>(w + (size_t)n * K + k);
+    }
+    __device__ void epilogue(int m, int n0, const float (&v)[16]) const {
+        __align__(16) bf16 o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float z = v[j] + (n0 + j < N ? bias[n0 + j] : 0.f);
+            if (relu) z = fmaxf(z, 0.f);
+            o[j] = __float2bfloat16_rn(z);
+        }
+        bf16* dst = out + (size_t)m * cout + n0;
+        if (n0 + 16 <= N) {
+            reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(o)[0];
+            reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(o)[1];
+        } else {
+            for (int j = 0; j < 16 && n0 + j < N; ++j) dst[j] = o[j];
+        }
+    }
+};
+
+// Input gradient: dx[p][c] += sum_{tap, o} W[o][tap][c] dz[p - d(tap)][o],
+// with the transposed weights wt[c][tap][o].
+struct ConvBwdData {
+    int M, N, K;
+    int* err;
+    const bf16* dz;
+    const bf16* wt;      // [cin][9 cout]
+    float* dx;
+    int H, W, cin, cout;
+    __device__ uint4 a_chunk(int m, int k8) const {
+        const int k = k8 * 8;
+        if (m >= M || k >= K) return make_uint4(0, 0, 0, 0);
+        const int tap = k / cout, c0 = k - tap * cout;
+        const int x = m % W, t = m / W, y = t % H, b = t / H;
+        const int yy = wrap_i(y - (tap / 3 - 1), H), xx = wrap_i(x - (tap % 3 - 1), W);
+        return *reinterpret_cast<const uint4*>(dz + ((size_t)(b * H + yy) * W + xx) * cout + c0);
+    }
+    __device__ uint4 b_chunk(int n, int k8) const {
+        const int k = k8 * 8;
+        if (n >= N || k >= K) return make_uint4(0, 0, 0, 0);
+        return *reinterpret_cast<const uint4*>(wt + (size_t)n * K + k);
+    }
+    __device__ void epilogue(int m, int n0, const float (&v)[16]) const {
+        float* dst = dx + (size_t)m * cin + n0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (n0 + j < N) dst[j] += v[j];
+    }
+};
+
+// Weight gradient: dW[o][tap][c] += sum_p dz[p][o] in[p + d(tap)][c] over a
+// split of the pixels, from channel-major copies dzT[o][p] and inT[c][p].
+struct ConvBwdW {
+    int M, N, K;         // M = cout, N = 9 cin, K = pixels
+    int* err;
+    const bf16* dzT;
+    const bf16* inT;
+    float* dw;
+    int H, W, cin;
+    __device__ uint4 a_chunk(int m, int k8) const {
+        const int k = k8 * 8;
+        if (m >= M || k >= K) return make_uint4(0, 0, 0, 0);
+        return *reinterpret_cast<const uint4*>(dzT + (size_t)m * K + k);
+    }
+    __device__ uint4 b_chunk(int n, int k8) const {
+        const int k = k8 * 8;
+        if (n >= N || k >= K) return make_uint4(0, 0, 0, 0);
+        const int tap = n / cin, c = n - tap * cin;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const int x = k % W, t = k / W, y = t % H, b = t / H;    // 8 pixels of one row (W % 8 == 0)
+        const bf16* row = inT + (size_t)c * K + (size_t)(b * H + wrap_i(y + dy, H)) * W;
+        if (dx == 0) return *reinterpret_cast<const uint4*>(row + x);
+        __align__(16) bf16 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = row[wrap_i(x + j + dx, W)];
+        return *reinterpret_cast<const uint4*>(v);
+    }
+    __device__ void epilogue(int m, int n0, const float (&v)[16]) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (n0 + j < N) atomicAdd(dw + (size_t)m * N + n0 + j, v[j]);
+    }
+};
+
+template <int BN, class Op>
+cudaError_t run_gemm(const Op& op, int splits, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(tcg::k_gemm<BN, Op>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tcg::smem_bytes<BN>());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int chunks = (op.K + tcg::BK - 1) / tcg::BK;
+    if (splits > chunks) splits = chunks;
+    if (splits < 1) splits = 1;
+    const int per = (chunks + splits - 1) / splits;
+    splits = (chunks + per - 1) / per;
+    const dim3 grid((op.M + tcg::BM - 1) / tcg::BM, (op.N + BN - 1) / BN, splits);
+    tcg::k_gemm<BN, Op><<<grid, tcg::NTHREADS, tcg::smem_bytes<BN>(), st>>>(op, per);
+    return cudaGetLastError();
+}
+
+template <class Op>
+cudaError_t gemm(const Op& op, int splits, cudaStream_t st) {
+    if (op.N >= 128) return run_gemm<128>(op, splits, st);
+    if (op.N >= 64) return run_gemm<64>(op, splits, st);
+    if (op.N >= 32) return run_gemm<32>(op, splits, st);
+    return run_gemm<16>(op, splits, st);
+}
+
+// ------------------------------------------------------ element-wise kernels
+inline unsigned blocks(long long n) { return (unsigned)((n + EB - 1) / EB); }
+
+__global__ void k_pool(const bf16* __restrict__ in, bf16* __restrict__ out, int B, int H, int W,
+                       int C) {   // in: H x W, out: H/2 x W/2
+    const long long n = (long long)B * (H / 2) * (W / 2) * C;
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    long long t = i / C;
+    const int x = (int)(t % (W / 2));
+    t /= (W / 2);
+    const int y = (int)(t % (H / 2)), b = (int)(t / (H / 2));
+    auto at = [&](int yy, int xx) {
+        return __bfloat162float(in[((size_t)(b * H + yy) * W + xx) * C + c]);
+    };
+    const float s = at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1);
+    out[i] = __float2bfloat16_rn(0.25f * s);
+}
+
+__global__ void k_pool_bwd(const float* __restrict__ d, float* __restrict__ dx, int B, int H,
+                           int W, int C) {   // d: H/2 x W/2, dx: H x W (accumulate)
+    const long long n = (long long)B * H * W * C;
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % C);
+    long long t = i / C;
+    const int x = (int)(t % W);
+    t /= W;
+    const int y = (int)(t % H), b = (int)(t / H);
+    dx[i] += 0.25f * d[((size_t)(b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+}
+
+// Nearest upsampling of src (H/2 x W/2, Cs channels) into channels [0, Cs) of
+// the concatenation dst (H x W, Cd channels); k_copy_ch puts the skip into
+// channels [Cs, Cd).
+__global__ void k_up_into(const bf16* __restrict__ src, bf16* __restrict__ dst, int B, int H,
+                          int W, int Cs, int Cd) {
+    const long long n = (long long)B * H * W * Cs;
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % Cs);
+    const long long p = i / Cs;
+    const int x = (int)(p % W);
+    const long long t = p / W;
+    const int y = (int)(t % H), b = (int)(t / H);
+    dst[p * Cd + c] = src[((size_t)(b * (H / 2) + y / 2) * (W / 2) + x / 2) * Cs + c];
+}
+
+__global__ void k_copy_ch(const bf16* __restrict__ src, bf16* __restrict__ dst, long long P,
+                          int Cs, int Cd, int off) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= P * Cs) return;
+    const long long p = i / Cs;
+    dst[p * Cd + off + (i % Cs)] = src[i];
+}
+
+// Gradient of [upsampled, skip]: the skip part accumulates into dskip, the
+// upsampled part sums over each 2x2 block into dsrc.
+__global__ void k_cat_bwd_skip(const float* __restrict__ dcat, float* __restrict__ dskip,
+                               long long P, int Cs, int Cd) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= P * (Cd - Cs)) return;
+    const int Ck = Cd - Cs;
+    const long long p = i / Ck;
+    dskip[i] += dcat[p * Cd + Cs + (i % Ck)];
+}
+
+__global__ void k_cat_bwd_up(const float* __restrict__ dcat, float* __restrict__ dsrc, int B,
+                             int H, int W, int Cs, int Cd) {   // dsrc: H/2 x W/2 x Cs
+    const long long n = (long long)B * (H / 2) * (W / 2) * Cs;
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % Cs);
+    long long t = i / Cs;
+    const int x = (int)(t % (W / 2));
+    t /= (W / 2);
+    const int y = (int)(t % (H / 2)), b = (int)(t / (H / 2));
+    float s = 0.f;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+            s += dcat[((size_t)(b * H + 2 * y + dy) * W + 2 * x + dx) * Cd + c];
+    dsrc[i] += s;
+}
+
+// dz = bf16(dout * (out > 0)) and its channel-major copy dzT[c][p].
+__global__ void k_relu_mask(const float* __restrict__ dout, const bf16* __restrict__ out,
+                            bf16* __restrict__ dz, bf16* __restrict__ dzT, long long P, int C) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= P * C) return;
+    const float g = __bfloat162float(out[i]) > 0.f ? dout[i] : 0.f;
+    const bf16 v = __float2bfloat16_rn(g);
+    dz[i] = v;
+    dzT[(i % C) * P + i / C] = v;
+}
+
+__global__ void k_to_cm(const bf16* __restrict__ in, bf16* __restrict__ inT, long long P, int C) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= P * C) return;
+    inT[(i % C) * P + i / C] = in[i];
+}
+
+// Bias gradient: db[o] += sum_p dzT[o][p] (one block per output channel).
+__global__ void k_bias_grad(const bf16* __restrict__ dzT, long long P, float* __restrict__ db) {
+    __shared__ float red[EB];
+    float s = 0.f;
+    for (long long p = threadIdx.x; p < P; p += EB) s += __bfloat162float(dzT[blockIdx.x * P + p]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = EB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(db + blockIdx.x, red[0]);
+}
+
+// Head: pred[p][o] = bh[o] + sum_c Wh[o][c] h[p][c] (FP32 weights).
+__global__ void k_head(const bf16* __restrict__ h, const float* __restrict__ Wh,
+                       const float* __restrict__ bh, float* __restrict__ pred, long long P, int C) {
+    const long long p = (long long)blockIdx.x * EB + threadIdx.x;
+    if (p >= P) return;
+    float acc[COUT];
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) acc[o] = bh[o];
+    for (int c = 0; c < C; ++c) {
+        const float v = __bfloat162float(h[p * C + c]);
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) acc[o] += Wh[o * C + c] * v;
+    }
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) pred[p * COUT + o] = acc[o];
+}
+
+// Loss terms and dpred = 2 (pred - target) / n; per-block partial loss sums.
+__global__ void k_loss(const float* __restrict__ pred, const float* __restrict__ tgt,
+                       float* __restrict__ dpred, long long n, double* __restrict__ part) {
+    __shared__ double red[EB];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * EB + threadIdx.x; i < n; i += (long long)gridDim.x * EB) {
+        const float d = pred[i] - tgt[i];
+        dpred[i] = 2.f * d / (float)n;
+        s += (double)d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = EB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Head backward: dh[p][c] += sum_o Wh[o][c] dpred[p][o]; dWh, dbh by block sums.
+__global__ void k_head_bwd(const bf16* __restrict__ h, const float* __restrict__ dpred,
+                           const float* __restrict__ Wh, float* __restrict__ dh,
+                           float* __restrict__ dWh, float* __restrict__ dbh, long long P, int C) {
+    extern __shared__ float acc[];   // COUT * C + COUT
+    for (int k = threadIdx.x; k < COUT * C + COUT; k += EB) acc[k] = 0.f;
+    __syncthreads();
+    for (long long p = (long long)blockIdx.x * EB + threadIdx.x; p < P; p += (long long)gridDim.x * EB) {
+        float g[COUT];
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) {
+            g[o] = dpred[p * COUT + o];
+            atomicAdd(&acc[COUT * C + o], g[o]);
+        }
+        for (int c = 0; c < C; ++c) {
+            const float v = __bfloat162float(h[p * C + c]);
+            float s = 0.f;
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) {
+                s += Wh[o * C + c] * g[o];
+                atomicAdd(&acc[o * C + c], g[o] * v);
+            }
+            dh[p * C + c] += s;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < COUT * C; k += EB) atomicAdd(dWh + k, acc[k]);
+    for (int k = threadIdx.x; k < COUT; k += EB) atomicAdd(dbh + k, acc[COUT * C + k]);
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr, float b1, float b2, float c1,
+                       float c2, float eps) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of one convolution's weights: w[o][tap][c] and wt[c][tap][o].
+__global__ void k_weights_bf16(const float* __restrict__ w, bf16* __restrict__ wb,
+                               bf16* __restrict__ wt, int cout, int cin) {
+    const long long n = (long long)cout * 9 * cin;
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    const int c = (int)(i % cin);
+    const int tap = (int)((i / cin) % 9), o = (int)(i / (9LL * cin));
+    const bf16 v = __float2bfloat16_rn(w[i]);
+    wb[i] = v;
+    wt[((size_t)c * 9 + tap) * cout + o] = v;
+}
+
+// Raw fields of a solver instance: phi - phi_ref, Q_xx, Q_xy, u1x, u1y, u2x, u2y.
+__global__ void k_capture(const float* __restrict__ phi, const float* __restrict__ Q,
+                          const float* __restrict__ mac, long long N, int b, float* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= N) return;
+    dst[i] = phi[b * N + i];
+    dst[N + i] = Q[2 * b * N + i];
+    dst[2 * N + i] = Q[(2 * b + 1) * N + i];
+    for (int k = 0; k < 4; ++k) dst[(3 + k) * N + i] = mac[(8 * b + k) * N + i];
+}
+
+// Per-channel sums over the pairs: [0..6] input, [7..13] input^2,
+// [14..20] increment, [21..27] increment^2 (partials per block).
+__global__ void k_stats(const float* __restrict__ data, long long N, int n_pairs,
+                        double* __restrict__ part) {
+    __shared__ double red[28][32];
+    double s[28];
+    for (int k = 0; k < 28; ++k) s[k] = 0.0;
+    const long long total = (long long)n_pairs * N;
+    for (long long j = (long long)blockIdx.x * EB + threadIdx.x; j < total; j += (long long)gridDim.x * EB) {
+        const long long pr = j / N, i = j % N;
+        const float* in = data + pr * 14 * N;
+        const float* tg = in + 7 * N;
+        for (int c = 0; c < 7; ++c) {
+            const double a = in[c * N + i], d = (double)tg[c * N + i] - a;
+            s[c] += a;
+            s[7 + c] += a * a;
+            s[14 + c] += d;
+            s[21 + c] += d * d;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 28; ++k) {
+        double v = s[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 28) {
+        double v = 0.0;
+        for (int w = 0; w < EB / 32; ++w) v += red[threadIdx.x][w];
+        part[blockIdx.x * 28 + threadIdx.x] = v;
+    }
+}
+
+// Normalisation constants: mean[7], inv_std[7], dmean[7], dstd[7].
+struct Norm {
+    float mean[7], inv_std[7], dmean[7], dstd[7];
+};
+
+// Minibatch from pairs idx[0..B): x (BF16, 8 channels) and target (FP32, 7).
+__global__ void k_assemble(const float* __restrict__ data, const int* __restrict__ idx,
+                           const float* __restrict__ zeta, Norm nm, float zscale, long long N,
+                           int B, bf16* __restrict__ x, float* __restrict__ tgt) {
+    const long long j = (long long)blockIdx.x * EB + threadIdx.x;
+    if (j >= (long long)B * N) return;
+    const int bi = (int)(j / N);
+    const long long i = j % N;
+    const float* in = data + (long long)idx[bi] * 14 * N;
+    const float* tg = in + 7 * N;
+    __align__(16) bf16 xv[8];
+    for (int c = 0; c < 7; ++c) {
+        const float a = in[c * N + i];
+        xv[c] = __float2bfloat16_rn((a - nm.mean[c]) * nm.inv_std[c]);
+        if (tgt) tgt[j * 7 + c] = (tg[c * N + i] - a - nm.dmean[c]) / nm.dstd[c];
+    }
+    xv[7] = __float2bfloat16_rn(zeta[idx[bi]] * zscale);
+    *reinterpret_cast<uint4*>(x + j * 8) = *reinterpret_cast<const uint4*>(xv);
+}
+
+// Prediction back to FP64 planes: phi (absolute), Q_xx, Q_xy, and u1, u2 as
+// [2][N] each (the layouts tf_launch_write_field / set_equilibrium take).
+__global__ void k_predict_out(const float* __restrict__ raw, const float* __restrict__ pred, Norm nm,
+                              double phi_ref, long long N, double* __restrict__ phi,
+                              double* __restrict__ qxx, double* __restrict__ qxy,
+                              double* __restrict__ u1, double* __restrict__ u2) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= N) return;
+    double v[7];
+    for (int c = 0; c < 7; ++c)
+        v[c] = (double)raw[c * N + i] + (double)nm.dmean[c] + (double)nm.dstd[c] * pred[i * 7 + c];
+    phi[i] = phi_ref + v[0];
+    qxx[i] = v[1];
+    qxy[i] = v[2];
+    u1[i] = v[3];
+    u1[N + i] = v[4];
+    u2[i] = v[5];
+    u2[N + i] = v[6];
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) for weight initialisation and
+// minibatch draws.
+uint64_t splitmix(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double uniform(uint64_t& s) { return (double)(splitmix(s) >> 11) * 0x1.0p-53; }
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Conv {
+    int cin, cout, level;
+    long long w_off, b_off;      // offsets into the flat FP32 parameter vector
+    size_t wb, wt;               // byte offsets of the BF16 copies
+    int in_t, out_t;             // activation tensors
+};
+struct Tensor {
+    int C, level;
+    size_t act, grad;            // byte offsets (BF16 activations, FP32 gradients)
+};
+enum OpKind { OP_CONV, OP_POOL, OP_CAT };
+struct Op {
+    int kind, a, b, c;           // conv: a = conv index; pool: a -> b; cat: up a, skip b -> c
+};
+
+}  // namespace
+
+struct tf_surrogate {
+    tf_sur_config cfg{};
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    std::vector<Conv> convs;
+    std::vector<Tensor> tensors;
+    std::vector<Op> ops;
+    long long n_params = 0, head_w = 0, head_b = 0;
+    int x_t = 0, dec0_t = 0;     // input and last decoder tensors
+    // workspace regions (byte offsets)
+    size_t p_off = 0, g_off = 0, m_off = 0, v_off = 0, wbf_off = 0, act_off = 0, grad_off = 0;
+    size_t dz_off = 0, dzT_off = 0, inT_off = 0, pred_off = 0, tgt_off = 0, dpred_off = 0;
+    size_t data_off = 0, zeta_off = 0, idx_off = 0, part_off = 0, err_off = 0, out64_off = 0;
+    size_t raw_off = 0, total = 0;
+    long long max_cp = 0;        // largest pixels x channels of any tensor at max_batch
+    std::vector<float> zeta;     // per pair
+    Norm norm{};
+    float zscale = 1.f;
+    bool norm_ready = false;
+    int adam_t = 0;
+    std::string last_error;
+    template <class T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+    long long pixels(int level, int B) const {
+        return (long long)B * (cfg.ny >> level) * (cfg.nx >> level);
+    }
+};
+
+namespace {
+
+int sfail(tf_surrogate* s, int code, const std::string& msg) {
+    if (s) s->last_error = msg;
+    return code;
+}
+#define SCK(s, call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return sfail(s, TF_ERR_CUDA, std::string(#call) + ": " +     \
+                                                                cudaGetErrorString(e_));   \
+    } while (0)
+
+bool valid_cfg(const tf_sur_config& c) {
+    if (c.levels < 1 || c.levels > 5) return false;
+    if (c.base_channels != 16 && c.base_channels != 32 && c.base_channels != 64) return false;
+    const int q = 8 << (c.levels - 1);
+    if (c.nx < q || c.ny < q || c.nx % q || c.ny % q) return false;
+    if (c.nx > 4096 || c.ny > 4096) return false;
+    return c.max_batch >= 1 && c.max_pairs >= 1 && c.horizon >= 1;
+}
+
+// Builds the layer graph and the workspace layout; returns the byte total.
+size_t plan(tf_surrogate* s) {
+    const tf_sur_config& c = s->cfg;
+    const int L = c.levels, B = c.max_batch;
+    s->convs.clear();
+    s->tensors.clear();
+    s->ops.clear();
+    auto tensor = [&](int C, int level) {
+        s->tensors.push_back(Tensor{C, level, 0, 0});
+        return (int)s->tensors.size() - 1;
+    };
+    long long np = 0;
+    auto conv = [&](int in_t, int cout) {
+        const Tensor t = s->tensors[in_t];
+        Conv cv{t.C, cout, t.level, np, np + (long long)cout * 9 * t.C, 0, 0, in_t, 0};
+        np += (long long)cout * 9 * t.C + cout;
+        cv.out_t = tensor(cout, t.level);
+        s->convs.push_back(cv);
+        s->ops.push_back(Op{OP_CONV, (int)s->convs.size() - 1, 0, 0});
+        return cv.out_t;
+    };
+    s->x_t = tensor(CIN, 0);
+    std::vector<int> skip(L);
+    int h = s->x_t;
+    for (int l = 0; l < L; ++l) {
+        if (l > 0) {
+            const int p = tensor(s->tensors[h].C, l);
+            s->ops.push_back(Op{OP_POOL, h, p, 0});
+            h = p;
+        }
+        h = conv(h, c.base_channels << l);
+        h = conv(h, c.base_channels << l);
+        skip[l] = h;
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const int cat = tensor(s->tensors[h].C + s->tensors[skip[l]].C, l);
+        s->ops.push_back(Op{OP_CAT, h, skip[l], cat});
+        h = conv(cat, c.base_channels << l);
+        h = conv(h, c.base_channels << l);
+    }
+    s->dec0_t = h;
+    s->head_w = np;
+    np += (long long)COUT * c.base_channels;
+    s->head_b = np;
+    np += COUT;
+    s->n_params = np;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = al256(off + bytes);
+        return o;
+    };
+    s->p_off = take(np * 4);
+    s->g_off = take(np * 4);
+    s->m_off = take(np * 4);
+    s->v_off = take(np * 4);
+    for (Conv& cv : s->convs) {
+        cv.wb = take((size_t)cv.cout * 9 * cv.cin * 2);
+        cv.wt = take((size_t)cv.cout * 9 * cv.cin * 2);
+    }
+    long long max_cp = 0;
+    for (Tensor& t : s->tensors) {
+        const long long cp = s->pixels(t.level, B) * t.C;
+        if (cp > max_cp) max_cp = cp;
+        t.act = take((size_t)cp * 2);
+        t.grad = take((size_t)cp * 4);
+    }
+    s->max_cp = max_cp;
+    s->dz_off = take((size_t)max_cp * 2);
+    s->dzT_off = take((size_t)max_cp * 2);
+    s->inT_off = take((size_t)max_cp * 2);
+    const long long P0 = s->pixels(0, B), N = (long long)c.nx * c.ny;
+    s->pred_off = take((size_t)P0 * COUT * 4);
+    s->tgt_off = take((size_t)P0 * COUT * 4);
+    s->dpred_off = take((size_t)P0 * COUT * 4);
+    s->data_off = take((size_t)c.max_pairs * 14 * N * 4);
+    s->raw_off = take((size_t)14 * N * 4);                 // prediction input slot
+    s->zeta_off = take((size_t)(c.max_pairs + 1) * 4);
+    s->idx_off = take((size_t)B * 4);
+    s->part_off = take(1024 * 28 * 8);
+    s->out64_off = take((size_t)7 * N * 8);
+    s->err_off = take(64);
+    s->total = off;
+    return off;
+}
+
+// ---------------------------------------------------------------- passes
+cudaError_t forward_pass(tf_surrogate* s, int B) {
+    cudaStream_t st = s->stream;
+    int* err = s->at<int>(s->err_off);
+    const float* P = s->at<float>(s->p_off);
+    for (const Op& op : s->ops) {
+        if (op.kind == OP_CONV) {
+            const Conv& cv = s->convs[op.a];
+            const Tensor& ti = s->tensors[cv.in_t];
+            const int H = s->cfg.ny >> ti.level, W = s->cfg.nx >> ti.level;
+            ConvFwd g;
+            g.M = B * H * W;
+            g.N = cv.cout;
+            g.K = 9 * cv.cin;
+            g.err = err;
+            g.in = s->at<bf16>(ti.act);
+            g.w = s->at<bf16>(cv.wb);
+            g.bias = P + cv.b_off;
+            g.out = s->at<bf16>(s->tensors[cv.out_t].act);
+            g.H = H;
+            g.W = W;
+            g.cin = cv.cin;
+            g.cout = cv.cout;
+            g.relu = 1;
+            cudaError_t e = gemm(g, 1, st);
+            if (e != cudaSuccess) return e;
+        } else if (op.kind == OP_POOL) {
+            const Tensor& a = s->tensors[op.a];
+            const int H = s->cfg.ny >> a.level, W = s->cfg.nx >> a.level;
+            k_pool<<<blocks((long long)B * H * W * a.C / 4), EB, 0, st>>>(
+                s->at<bf16>(a.act), s->at<bf16>(s->tensors[op.b].act), B, H, W, a.C);
+        } else {
+            const Tensor& up = s->tensors[op.a];
+            const Tensor& sk = s->tensors[op.b];
+            const Tensor& cat = s->tensors[op.c];
+            const int H = s->cfg.ny >> cat.level, W = s->cfg.nx >> cat.level;
+            const long long Pp = (long long)B * H * W;
+            k_up_into<<<blocks(Pp * up.C), EB, 0, st>>>(s->at<bf16>(up.act), s->at<bf16>(cat.act),
+                                                       B, H, W, up.C, cat.C);
+            k_copy_ch<<<blocks(Pp * sk.C), EB, 0, st>>>(s->at<bf16>(sk.act), s->at<bf16>(cat.act),
+                                                       Pp, sk.C, cat.C, up.C);
+        }
+    }
+    const Tensor& d0 = s->tensors[s->dec0_t];
+    const long long P0 = s->pixels(0, B);
+    k_head<<<blocks(P0), EB, 0, st>>>(s->at<bf16>(d0.act), P + s->head_w, P + s->head_b,
+                                      s->at<float>(s->pred_off), P0, d0.C);
+    return cudaGetLastError();
+}
+
+// Loss of the current prediction against s->tgt and the gradients in s->g.
+cudaError_t backward_pass(tf_surrogate* s, int B, double* loss) {
+    cudaStream_t st = s->stream;
+    int* err = s->at<int>(s->err_off);
+    const float* P = s->at<float>(s->p_off);
+    float* G = s->at<float>(s->g_off);
+    cudaError_t e = cudaMemsetAsync(G, 0, s->n_params * 4, st);
+    for (const Tensor& t : s->tensors)
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->ws + t.grad, 0, (size_t)s->pixels(t.level, B) * t.C * 4, st);
+    if (e != cudaSuccess) return e;
+    const long long P0 = s->pixels(0, B);
+    const long long n = P0 * COUT;
+    const int lb = 256;
+    k_loss<<<lb, EB, 0, st>>>(s->at<float>(s->pred_off), s->at<float>(s->tgt_off),
+                              s->at<float>(s->dpred_off), n, s->at<double>(s->part_off));
+    const Tensor& d0 = s->tensors[s->dec0_t];
+    k_head_bwd<<<152, EB, (COUT * d0.C + COUT) * sizeof(float), st>>>(
+        s->at<bf16>(d0.act), s->at<float>(s->dpred_off), P + s->head_w, s->at<float>(d0.grad),
+        G + s->head_w, G + s->head_b, P0, d0.C);
+    for (int k = (int)s->ops.size() - 1; k >= 0; --k) {
+        const Op& op = s->ops[k];
+        if (op.kind == OP_CONV) {
+            const Conv& cv = s->convs[op.a];
+            const Tensor& ti = s->tensors[cv.in_t];
+            const Tensor& to = s->tensors[cv.out_t];
+            const int H = s->cfg.ny >> ti.level, W = s->cfg.nx >> ti.level;
+            const long long Pp = (long long)B * H * W;
+            bf16* dz = s->at<bf16>(s->dz_off);
+            bf16* dzT = s->at<bf16>(s->dzT_off);
+            bf16* inT = s->at<bf16>(s->inT_off);
+            k_relu_mask<<<blocks(Pp * cv.cout), EB, 0, st>>>(s->at<float>(to.grad), s->at<bf16>(to.act),
+                                                             dz, dzT, Pp, cv.cout);
+            k_to_cm<<<blocks(Pp * cv.cin), EB, 0, st>>>(s->at<bf16>(ti.act), inT, Pp, cv.cin);
+            ConvBwdW gw;
+            gw.M = cv.cout;
+            gw.N = 9 * cv.cin;
+            gw.K = (int)Pp;
+            gw.err = err;
+            gw.dzT = dzT;
+            gw.inT = inT;
+            gw.dw = G + cv.w_off;
+            gw.H = H;
+            gw.W = W;
+            gw.cin = cv.cin;
+            const int tiles = ((gw.M + 127) / 128) * ((gw.N + 63) / 64);
+            e = gemm(gw, (304 + tiles - 1) / tiles, st);
+            if (e != cudaSuccess) return e;
+            k_bias_grad<<<cv.cout, EB, 0, st>>>(dzT, Pp, G + cv.b_off);
+            if (cv.in_t != s->x_t) {
+                ConvBwdData gd;
+                gd.M = (int)Pp;
+                gd.N = cv.cin;
+                gd.K = 9 * cv.cout;
+                gd.err = err;
+                gd.dz = dz;
+                gd.wt = s->at<bf16>(cv.wt);
+                gd.dx = s->at<float>(ti.grad);
+                gd.H = H;
+                gd.W = W;
+                gd.cin = cv.cin;
+                gd.cout = cv.cout;
+                e = gemm(gd, 1, st);
+                if (e != cudaSuccess) return e;
+            }
+        } else if (op.kind == OP_POOL) {
+            const Tensor& a = s->tensors[op.a];
+            const int H = s->cfg.ny >> a.level, W = s->cfg.nx >> a.level;
+            k_pool_bwd<<<blocks((long long)B * H * W * a.C), EB, 0, st>>>(
+                s->at<float>(s->tensors[op.b].grad), s->at<float>(a.grad), B, H, W, a.C);
+        } else {
+            const Tensor& up = s->tensors[op.a];
+            const Tensor& sk = s->tensors[op.b];
+            const Tensor& cat = s->tensors[op.c];
+            const int H = s->cfg.ny >> cat.level, W = s->cfg.nx >> cat.level;
+            const long long Pp = (long long)B * H * W;
+            k_cat_bwd_skip<<<blocks(Pp * sk.C), EB, 0, st>>>(s->at<float>(cat.grad),
+                                                             s->at<float>(sk.grad), Pp, up.C, cat.C);
+            k_cat_bwd_up<<<blocks(Pp * up.C / 4), EB, 0, st>>>(s->at<float>(cat.grad),
+                                                              s->at<float>(up.grad), B, H, W, up.C,
+                                                              cat.C);
+        }
+    }
+    if (loss) {
+        std::vector<double> part(lb);
+        e = cudaMemcpyAsync(part.data(), s->at<double>(s->part_off), lb * sizeof(double),
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        double t = 0.0;
+        for (double v : part) t += v;
+        *loss = t / (double)n;
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+cudaError_t refresh_bf16(tf_surrogate* s) {
+    const float* P = s->at<float>(s->p_off);
+    for (const Conv& cv : s->convs)
+        k_weights_bf16<<<blocks((long long)cv.cout * 9 * cv.cin), EB, 0, s->stream>>>(
+            P + cv.w_off, s->at<bf16>(cv.wb), s->at<bf16>(cv.wt), cv.cout, cv.cin);
+    return cudaGetLastError();
+}
+
+int check_status(tf_surrogate* s) {
+    int flag = 0;
+    SCK(s, cudaMemcpyAsync(&flag, s->at<int>(s->err_off), sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    if (flag) {
+        SCK(s, cudaMemsetAsync(s->at<int>(s->err_off), 0, sizeof(int), s->stream));
+        return sfail(s, flag, "a tensor-core GEMM wait timed out");
+    }
+    return TF_OK;
+}
+
+int upload_x(tf_surrogate* s, const float* x, int batch) {
+    const long long n = s->pixels(0, batch) * CIN;
+    std::vector<uint16_t> h(n);
+    for (long long i = 0; i < n; ++i) {
+        const bf16 v = __float2bfloat16_rn(x[i]);
+        std::memcpy(&h[i], &v, 2);
+    }
+    SCK(s, cudaMemcpyAsync(s->ws + s->tensors[s->x_t].act, h.data(), n * 2, cudaMemcpyHostToDevice,
+                           s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    return TF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tf_sur_workspace_bytes(const tf_sur_config* cfg) {
+    if (!cfg || !valid_cfg(*cfg)) return 0;
+    tf_surrogate tmp;
+    tmp.cfg = *cfg;
+    return plan(&tmp);
+}
+
+int tf_sur_create(const tf_sur_config* cfg, void* d_workspace, size_t workspace_bytes, void* stream,
+                  tf_surrogate** out) {
+    if (!out) return TF_ERR_ARG;
+    *out = nullptr;
+    if (!cfg || !valid_cfg(*cfg)) return TF_ERR_ARG;
+    tf_surrogate* s = new (std::nothrow) tf_surrogate();
+    if (!s) return TF_ERR_ARG;
+    s->cfg = *cfg;
+    const size_t need = plan(s);
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255) || workspace_bytes < need) {
+        delete s;
+        return TF_ERR_WORKSPACE;
+    }
+    s->ws = static_cast<char*>(d_workspace);
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->zeta.assign(cfg->max_pairs, 0.f);
+    cudaError_t e = cudaMemsetAsync(s->ws, 0, s->total, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        delete s;
+        return TF_ERR_CUDA;
+    }
+    *out = s;
+    return TF_OK;
+}
+
+int tf_sur_destroy(tf_surrogate* s) {
+    if (!s) return TF_ERR_ARG;
+    cudaStreamSynchronize(s->stream);
+    delete s;
+    return TF_OK;
+}
+
+const char* tf_sur_last_error(const tf_surrogate* s) { return s ? s->last_error.c_str() : "null surrogate"; }
+
+int64_t tf_sur_num_params(const tf_surrogate* s) { return s ? s->n_params : -1; }
+
+int tf_sur_set_weights(tf_surrogate* s, const float* host, int64_t n) {
+    if (!s) return TF_ERR_ARG;
+    if (!host || n != s->n_params) return sfail(s, TF_ERR_ARG, "weight count mismatch");
+    SCK(s, cudaMemcpyAsync(s->at<float>(s->p_off), host, n * 4, cudaMemcpyHostToDevice, s->stream));
+    SCK(s, cudaMemsetAsync(s->at<float>(s->m_off), 0, n * 4, s->stream));
+    SCK(s, cudaMemsetAsync(s->at<float>(s->v_off), 0, n * 4, s->stream));
+    s->adam_t = 0;
+    SCK(s, refresh_bf16(s));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    return TF_OK;
+}
+
+int tf_sur_get_weights(tf_surrogate* s, float* host, int64_t n) {
+    if (!s) return TF_ERR_ARG;
+    if (!host || n != s->n_params) return sfail(s, TF_ERR_ARG, "weight count mismatch");
+    SCK(s, cudaMemcpyAsync(host, s->at<float>(s->p_off), n * 4, cudaMemcpyDeviceToHost, s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    return TF_OK;
+}
+
+int tf_sur_init_weights(tf_surrogate* s, uint64_t seed) {
+    if (!s) return TF_ERR_ARG;
+    std::vector<float> w(s->n_params, 0.f);
+    uint64_t st = seed;
+    auto normal = [&]() {   // Box-Muller on two SplitMix64 uniforms
+        const double u1 = 1.0 - uniform(st), u2 = uniform(st);
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+    };
+    for (const Conv& cv : s->convs) {
+        const double sd = std::sqrt(2.0 / (9.0 * cv.cin));
+        for (long long i = 0; i < (long long)cv.cout * 9 * cv.cin; ++i) w[cv.w_off + i] = (float)(sd * normal());
+    }
+    const int C0 = s->cfg.base_channels;
+    for (long long i = 0; i < (long long)COUT * C0; ++i) w[s->head_w + i] = (float)(normal() / std::sqrt((double)C0));
+    return tf_sur_set_weights(s, w.data(), s->n_params);
+}
+
+int tf_sur_forward(tf_surrogate* s, const float* x, int batch, float* out) {
+    if (!s) return TF_ERR_ARG;
+    if (!x || !out || batch < 1 || batch > s->cfg.max_batch) return sfail(s, TF_ERR_ARG, "bad batch or null array");
+    int rc = upload_x(s, x, batch);
+    if (rc != TF_OK) return rc;
+    SCK(s, forward_pass(s, batch));
+    if ((rc = check_status(s)) != TF_OK) return rc;
+    SCK(s, cudaMemcpyAsync(out, s->at<float>(s->pred_off), s->pixels(0, batch) * COUT * 4,
+                           cudaMemcpyDeviceToHost, s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    return TF_OK;
+}
+
+int tf_sur_gradients(tf_surrogate* s, const float* x, const float* target, int batch, double* loss,
+                     float* grad, int64_t n) {
+    if (!s) return TF_ERR_ARG;
+    if (!x || !target || batch < 1 || batch > s->cfg.max_batch)
+        return sfail(s, TF_ERR_ARG, "bad batch or null array");
+    if (grad && n != s->n_params) return sfail(s, TF_ERR_ARG, "gradient count mismatch");
+    int rc = upload_x(s, x, batch);
+    if (rc != TF_OK) return rc;
+    SCK(s, cudaMemcpyAsync(s->at<float>(s->tgt_off), target, s->pixels(0, batch) * COUT * 4,
+                           cudaMemcpyHostToDevice, s->stream));
+    SCK(s, forward_pass(s, batch));
+    double l = 0.0;
+    SCK(s, backward_pass(s, batch, &l));
+    if ((rc = check_status(s)) != TF_OK) return rc;
+    if (loss) *loss = l;
+    if (grad) {
+        SCK(s, cudaMemcpyAsync(grad, s->at<float>(s->g_off), n * 4, cudaMemcpyDeviceToHost, s->stream));
+        SCK(s, cudaStreamSynchronize(s->stream));
+    }
+    return TF_OK;
+}
+
+int tf_sur_add_pair(tf_surrogate* s, int slot, tf_ctx* ctx, int inst, int which) {
+    if (!s || !ctx) return TF_ERR_ARG;
+    if (slot < 0 || slot >= s->cfg.max_pairs || (which != 0 && which != 1) || inst < 0 ||
+        inst >= ctx->batch)
+        return sfail(s, TF_ERR_ARG, "bad slot, instance or role");
+    if (ctx->nx != s->cfg.nx || ctx->ny != s->cfg.ny || ctx->stream != s->stream)
+        return sfail(s, TF_ERR_ARG, "solver grid or stream differs from the surrogate's");
+    SCK(s, tf_launch_flush(ctx));
+    SCK(s, tf_launch_macro(ctx, ctx->d.macro));
+    const long long N = ctx->N;
+    k_capture<<<blocks(N), EB, 0, s->stream>>>(ctx->d.phi[ctx->pcur], ctx->d.Q[ctx->pcur], ctx->d.macro,
+                                               N, inst,
+                                               s->at<float>(s->data_off) + ((long long)slot * 2 + which) * 7 * N);
+    SCK(s, cudaGetLastError());
+    s->zeta[slot] = (float)ctx->params[inst].zeta;
+    return TF_OK;
+}
+
+int tf_sur_fit_normalisation(tf_surrogate* s, int n_pairs) {
+    if (!s) return TF_ERR_ARG;
+    if (n_pairs < 1 || n_pairs > s->cfg.max_pairs) return sfail(s, TF_ERR_ARG, "bad pair count");
+    const long long N = (long long)s->cfg.nx * s->cfg.ny;
+    const int nb = 512;
+    k_stats<<<nb, EB, 0, s->stream>>>(s->at<float>(s->data_off), N, n_pairs, s->at<double>(s->part_off));
+    SCK(s, cudaGetLastError());
+    std::vector<double> part((size_t)nb * 28);
+    SCK(s, cudaMemcpyAsync(part.data(), s->at<double>(s->part_off), part.size() * 8, cudaMemcpyDeviceToHost,
+                           s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    double t[28] = {};
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 28; ++k) t[k] += part[(size_t)b * 28 + k];
+    const double cnt = (double)n_pairs * N;
+    for (int c = 0; c < 7; ++c) {
+        const double m = t[c] / cnt, var = t[7 + c] / cnt - m * m;
+        const double dm = t[14 + c] / cnt, dvar = t[21 + c] / cnt - dm * dm;
+        s->norm.mean[c] = (float)m;
+        s->norm.inv_std[c] = (float)(1.0 / std::sqrt(var > 1e-30 ? var : 1e-30));
+        s->norm.dmean[c] = (float)dm;
+        s->norm.dstd[c] = (float)std::sqrt(dvar > 1e-30 ? dvar : 1e-30);
+    }
+    float zmax = 0.f;
+    for (int p = 0; p < n_pairs; ++p) zmax = std::fmax(zmax, std::fabs(s->zeta[p]));
+    s->zscale = zmax > 0.f ? 1.f / zmax : 1.f;
+    SCK(s, cudaMemcpyAsync(s->at<float>(s->zeta_off), s->zeta.data(), n_pairs * 4, cudaMemcpyHostToDevice,
+                           s->stream));
+    SCK(s, cudaStreamSynchronize(s->stream));
+    s->norm_ready = true;
+    return TF_OK;
+}
+
+int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, uint64_t seed,
+                 double* losses) {
+    if (!s) return TF_ERR_ARG;
+    if (!s->norm_ready) return sfail(s, TF_ERR_ARG, "call tf_sur_fit_normalisation first");
+    if (n_pairs < 1 || n_pairs > s->cfg.max_pairs || steps < 0 || batch < 1 || batch > s->cfg.max_batch ||
+        !(lr > 0))
+        return sfail(s, TF_ERR_ARG, "bad training arguments");
+    const long long N = (long long)s->cfg.nx * s->cfg.ny;
+    uint64_t st = seed;
+    std::vector<int> idx(batch);
+    for (int it = 0; it < steps; ++it) {
+        for (int b = 0; b < batch; ++b) idx[b] = (int)(splitmix(st) % (uint64_t)n_pairs);
+        SCK(s, cudaMemcpyAsync(s->at<int>(s->idx_off), idx.data(), batch * 4, cudaMemcpyHostToDevice,
+                               s->stream));
+        k_assemble<<<blocks((long long)batch * N), EB, 0, s->stream>>>(
+            s->at<float>(s->data_off), s->at<int>(s->idx_off), s->at<float>(s->zeta_off), s->norm,
+            s->zscale, N, batch, s->at<bf16>(s->tensors[s->x_t].act), s->at<float>(s->tgt_off));
+        SCK(s, forward_pass(s, batch));
+        double l = 0.0;
+        SCK(s, backward_pass(s, batch, losses ? &l : nullptr));
+        if (losses) losses[it] = l;
+        s->adam_t += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, (float)s->adam_t), c2 = 1.f - std::pow(b2, (float)s->adam_t);
+        k_adam<<<blocks(s->n_params), EB, 0, s->stream>>>(s->at<float>(s->p_off), s->at<float>(s->g_off),
+                                                         s->at<float>(s->m_off), s->at<float>(s->v_off),
+                                                         s->n_params, (float)lr, b1, b2, c1, c2, 1e-8f);
+        SCK(s, refresh_bf16(s));
+    }
+    return check_status(s);
+}
+
+int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst) {
+    if (!s || !ctx) return TF_ERR_ARG;
+    if (!s->norm_ready) return sfail(s, TF_ERR_ARG, "call tf_sur_fit_normalisation first");
+    if (inst < 0 || inst >= ctx->batch) return sfail(s, TF_ERR_ARG, "bad instance");
+    if (ctx->nx != s->cfg.nx || ctx->ny != s->cfg.ny || ctx->stream != s->stream)
+        return sfail(s, TF_ERR_ARG, "solver grid or stream differs from the surrogate's");
+    const long long N = ctx->N;
+    SCK(s, tf_launch_flush(ctx));
+    ctx->fd_pending = false;
+    SCK(s, tf_launch_macro(ctx, ctx->d.macro));
+    float* raw = s->at<float>(s->raw_off);
+    k_capture<<<blocks(N), EB, 0, s->stream>>>(ctx->d.phi[ctx->pcur], ctx->d.Q[ctx->pcur], ctx->d.macro, N,
+                                               inst, raw);
+    // The prediction input is "pair 0" of the raw slot, its zeta one entry
+    // past the dataset's.
+    const float z = (float)ctx->params[inst].zeta;
+    float* zslot = s->at<float>(s->zeta_off) + s->cfg.max_pairs;
+    const int zero = 0;
+    SCK(s, cudaMemcpyAsync(zslot, &z, 4, cudaMemcpyHostToDevice, s->stream));
+    SCK(s, cudaMemcpyAsync(s->at<int>(s->idx_off), &zero, 4, cudaMemcpyHostToDevice, s->stream));
+    k_assemble<<<blocks(N), EB, 0, s->stream>>>(raw, s->at<int>(s->idx_off), zslot, s->norm, s->zscale,
+                                                N, 1, s->at<bf16>(s->tensors[s->x_t].act), nullptr);
+    SCK(s, forward_pass(s, 1));
+    double* o = s->at<double>(s->out64_off);
+    k_predict_out<<<blocks(N), EB, 0, s->stream>>>(raw, s->at<float>(s->pred_off), s->norm,
+                                                   (double)ctx->params[inst].phi_ref, N, o, o + N, o + 2 * N,
+                                                   o + 3 * N, o + 5 * N);
+    SCK(s, cudaGetLastError());
+    SCK(s, tf_launch_write_field(ctx, inst, TF_FIELD_PHI, o));
+    SCK(s, tf_launch_write_field(ctx, inst, TF_FIELD_QXX, o + N));
+    SCK(s, tf_launch_write_field(ctx, inst, TF_FIELD_QXY, o + 2 * N));
+    SCK(s, tf_launch_set_equilibrium(ctx, inst, o + 3 * N, o + 5 * N));
+    return TF_OK;
+}
+
+}  // extern "C"

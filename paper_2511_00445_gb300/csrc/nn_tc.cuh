@@ -1,0 +1,184 @@
+// Tensor-core GEMM core for the surrogate network (sm_103a, tcgen05).
+//
+// D[m][n] = sum_k A[m][k] B[n][k] with BF16 operands and FP32 accumulation in
+// tensor memory.  One CTA (4 warps) owns a 128 x BN tile of D and walks K in
+// chunks of 64: every thread gathers 16-byte pieces (8 consecutive k) of A
+// and B through the operation's loaders and stores them in shared memory in
+// the canonical no-swizzle K-major layout (8-row x 16-byte core matrices);
+// one thread issues four tcgen05.mma (K = 16 each) per chunk and commits them
+// to the stage's mbarrier.  Two stages: the gather of chunk j+1 overlaps the
+// MMAs of chunk j.  Epilogue: each thread owns one row of the tile, reads its
+// accumulators 16 columns at a time (tcgen05.ld) and hands them to the
+// operation.  Every mbarrier wait is bounded; a wait that runs out writes
+// TF_ERR_TIMEOUT to the status word and the CTA finishes without trapping.
+//
+// An operation Op provides
+//   int M, N, K;                                   GEMM sizes (K a multiple of 8)
+//   uint4 a_chunk(int m, int k8) const;            A[m][8 k8 .. 8 k8 + 7] (zero outside)
+//   uint4 b_chunk(int n, int k8) const;            B[n][8 k8 .. 8 k8 + 7] (zero outside)
+//   void epilogue(int m, int n0, const float (&v)[16]) const;  D[m][n0 .. n0 + 15]
+//   int* err;                                      device status word
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "twofluid.h"
+
+namespace tcg {
+
+constexpr int BM = 128, BK = 64, NTHREADS = 128;
+constexpr uint32_t kPolls = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Byte offset of element (r, k) of an R-row K-major tile (BK columns) in the
+// canonical no-swizzle layout: core matrix (r/8, k/8) holds 8 rows of 16 bytes.
+// Core matrices adjacent in K are R*16 bytes apart (leading byte offset), row
+// groups 128 bytes apart (stride byte offset).
+__device__ __forceinline__ uint32_t tile_off(int r, int k, int R) {
+    return (uint32_t)(((k >> 3) * (R >> 3) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kPolls; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int BN>
+constexpr int smem_bytes() {
+    return 2 * (BM * BK * 2 + BN * BK * 2);
+}
+
+// grid: (ceil(M / 128), ceil(N / BN), splits); split z covers K chunks
+// [z * chunks_per_split, (z + 1) * chunks_per_split).
+template <int BN, class Op>
+__global__ void __launch_bounds__(NTHREADS) k_gemm(const Op op, int chunks_per_split) {
+    static_assert(BN == 16 || BN == 32 || BN == 64 || BN == 128, "tile width");
+    constexpr int TCOLS = BN < 32 ? 32 : BN;                  // tensor-memory columns
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nchunks_all = (op.K + BK - 1) / BK;
+    const int c_begin = blockIdx.z * chunks_per_split;
+    const int c_end = min(nchunks_all, c_begin + chunks_per_split);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tmem_base;
+    uint32_t phase[2] = {0, 0};
+    bool ok = true;
+    int used = 0;
+    for (int c = c_begin; c < c_end; ++c, ++used) {
+        const int s = used & 1;
+        unsigned char* As = tc_smem + s * (A_BYTES + B_BYTES);
+        unsigned char* Bs = As + A_BYTES;
+        if (used >= 2) {   // the MMAs of chunk used-2 read this stage
+            ok = ok && mbar_wait(&bars[s], phase[s]);
+            phase[s] ^= 1;
+        }
+        const int k8_0 = c * (BK / 8);
+        for (int q = tid; q < BM * (BK / 8); q += NTHREADS) {
+            const int r = q >> 3, kc = q & 7;
+            *reinterpret_cast<uint4*>(As + tile_off(r, kc * 8, BM)) = op.a_chunk(m0 + r, k8_0 + kc);
+        }
+        for (int q = tid; q < BN * (BK / 8); q += NTHREADS) {
+            const int r = q >> 3, kc = q & 7;
+            *reinterpret_cast<uint4*>(Bs + tile_off(r, kc * 8, BN)) = op.b_chunk(n0 + r, k8_0 + kc);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+                const uint64_t ad = smem_desc(smem_u32(As) + k * 2 * (BM / 8) * 128, BM * 16, 128);
+                const uint64_t bd = smem_desc(smem_u32(Bs) + k * 2 * (BN / 8) * 128, BN * 16, 128);
+                const uint32_t acc = (used > 0 || k > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tbase),
+                    "l"(ad), "l"(bd), "r"(instr_desc(BM, BN)), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&bars[s])));
+        }
+    }
+    // The last commit covers every MMA issued before it.
+    if (used > 0) {
+        const int s = (used - 1) & 1;
+        ok = ok && mbar_wait(&bars[s], phase[s]);
+    }
+    if (!ok && tid == 0) atomicExch(op.err, TF_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (used > 0 && ok) {
+        const int m = m0 + warp * 32 + (tid & 31);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+            if (m < op.M && n0 + c0 < op.N) op.epilogue(m, n0 + c0, v);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                     "r"(TCOLS));
+}
+
+}  // namespace tcg

@@ -1,0 +1,135 @@
+"""The convolutional surrogate on the GPU (tensor-core GEMMs) against the FP64
+oracle (oracle/surrogate.py), and trained on the solver's own trajectories.
+
+Tolerances: activations are stored in BF16 between layers and the 3x3
+weights are rounded to BF16 (unit roundoff 2^-9, about 2e-3 per rounding);
+over a handful of layers with random signs the normwise relative error of
+the output and of each gradient group stays at the 1e-2 level, so the bar
+is 3e-2 (output) and 5e-2 (gradients)."""
+import numpy as np
+import pytest
+
+from oracle import surrogate as OS
+from paper_2511_00445_gb300 import _binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2511_00445_gb300 import build
+    build.build()
+
+
+def flat(net: OS.Net) -> np.ndarray:
+    parts = []
+    for W, b in zip(net.W, net.b):
+        parts += [W.ravel(), b.ravel()]
+    parts += [net.Wh.ravel(), net.bh.ravel()]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def bf16_round(a):
+    """Round FP32 values to the nearest BF16 (ties to even), returned as FP32."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16).astype(np.uint32).view(np.float32)
+
+
+def as_fp32_net(net: OS.Net) -> OS.Net:
+    """The oracle net with the FP32 weights the GPU receives."""
+    out = OS.Net(net.levels, net.c0, net.c_in, net.c_out)
+    out.W = [w.astype(np.float32).astype(np.float64) for w in net.W]
+    out.b = [b.astype(np.float32).astype(np.float64) for b in net.b]
+    out.Wh = net.Wh.astype(np.float32).astype(np.float64)
+    out.bh = net.bh.astype(np.float32).astype(np.float64)
+    return out
+
+
+def relerr(got, want):
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+@pytest.mark.parametrize("levels,c0,n", [(1, 16, 16), (2, 16, 16), (3, 32, 32)])
+def test_forward_and_gradients_match_oracle(levels, c0, n):
+    rng = np.random.default_rng(levels)
+    net = as_fp32_net(OS.init_net(levels, c0, B.SUR_IN, B.SUR_OUT, rng))
+    x = bf16_round(rng.standard_normal((2, n, n, B.SUR_IN)))
+    t = rng.standard_normal((2, n, n, B.SUR_OUT)).astype(np.float32)
+    sur = B.Surrogate(levels=levels, base_channels=c0, nx=n, ny=n, max_batch=2, max_pairs=1,
+                      horizon=1)
+    sur.set_weights(flat(net))
+    pred_want, _ = OS.forward(net, x.astype(np.float64))
+    assert relerr(sur.forward(x), pred_want) <= 3e-2
+    loss_want, dW, db, dWh, dbh = OS.backward(net, x.astype(np.float64), t.astype(np.float64))
+    loss, g = sur.gradients(x, t)
+    assert loss == pytest.approx(loss_want, rel=3e-2)
+    off = 0
+    for k in range(len(dW)):
+        for want in (dW[k], db[k]):
+            got = g[off:off + want.size].reshape(want.shape)
+            assert relerr(got, want) <= 5e-2, (k, relerr(got, want))
+            off += want.size
+    for want in (dWh, dbh):
+        got = g[off:off + want.size].reshape(want.shape)
+        assert relerr(got, want) <= 5e-2
+        off += want.size
+    assert off == sur.n_params
+
+
+def _pairs(sur, zetas, seeds, n_per, horizon, burn, nx):
+    """Capture (state, state + horizon) pairs of every instance and seed."""
+    slot = 0
+    for sd in seeds:
+        tf = B.TwoFluid([B.SolverParams(nx=nx, ny=nx, zeta=z) for z in zetas])
+        tf.init_fields(sd, phi0=0.5, dphi=0.01, S0=0.3)
+        tf.step(burn)
+        for _ in range(n_per):
+            for b in range(len(zetas)):
+                sur.add_pair(slot + b, tf, b, 0)
+            tf.step(horizon)
+            for b in range(len(zetas)):
+                sur.add_pair(slot + b, tf, b, 1)
+            slot += len(zetas)
+    return slot
+
+
+def test_training_and_prediction_beat_persistence():
+    """Trained on trajectories of four seeds, the network predicts a held-out
+    seed's state `horizon` steps ahead better than persistence (the current
+    state taken as the prediction): RMS errors of phi, Q_xx, u1x, u2x and the
+    summed error of the energy spectrum, averaged over the four instances."""
+    nx, horizon = 64, 50
+    zetas = [0.002, 0.005, 0.01, 0.02]
+    sur = B.Surrogate(levels=3, base_channels=32, nx=nx, ny=nx, max_batch=8, max_pairs=256,
+                      horizon=horizon)
+    sur.init_weights(7)
+    n_pairs = _pairs(sur, zetas, seeds=[1, 2, 3, 4], n_per=16, horizon=horizon, burn=300, nx=nx)
+    sur.fit_normalisation(n_pairs)
+    losses = sur.train(n_pairs, steps=3000, batch=8, lr=1e-3, seed=3)
+    assert np.mean(losses[-50:]) < 0.2 * np.mean(losses[:5])
+
+    def state(seed):
+        tf = B.TwoFluid([B.SolverParams(nx=nx, ny=nx, zeta=z) for z in zetas])
+        tf.init_fields(seed, phi0=0.5, dphi=0.01, S0=0.3)
+        tf.step(600)
+        return tf
+    truth, pred = state(11), state(11)
+    fields = (B.FIELD_PHI, B.FIELD_QXX, B.FIELD_U1X, B.FIELD_U2X)
+    start = {(b, f): truth.read_field(b, f) for b in range(len(zetas)) for f in fields}
+    start_E = {b: truth.energy_spectrum(b)[0] for b in range(len(zetas))}
+    truth.step(horizon)
+    for b in range(len(zetas)):
+        sur.predict(pred, b)
+    ratios = np.zeros((len(zetas), len(fields) + 1))
+    for b in range(len(zetas)):
+        for j, f in enumerate(fields):
+            want = truth.read_field(b, f)
+            ratios[b, j] = (np.sqrt(np.mean((pred.read_field(b, f) - want) ** 2)) /
+                            np.sqrt(np.mean((start[(b, f)] - want) ** 2)))
+        E_want = truth.energy_spectrum(b)[0]
+        ratios[b, -1] = (np.abs(pred.energy_spectrum(b)[0] - E_want).sum() /
+                         np.abs(start_E[b] - E_want).sum())
+    mean = ratios.mean(axis=0)
+    assert np.all(mean[:-1] < 0.9), mean
+    assert mean[-1] < 0.95, mean
+    assert pred.step_count() == 600             # predictions do not step the solver
