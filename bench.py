@@ -63,6 +63,10 @@ WORKLOADS = {
                        name="ensemble of 48: 16 x 128^2 + 16 x 256^2 + 16 x 512^2, FP32, "
                             "zeta {0.001,0.005,0.01} x lambda {0.3,0.7,1.1} x K {0.02,0.04,0.08}"),
 }
+WORKLOADS["surrogate256"] = dict(
+    nx=256, ny=256, zetas=[0.0, 0.002, 0.005, 0.01], surrogate=True,
+    name="U-Net surrogate, 4 levels x 32 base channels, BF16, 256x256, horizon 50 steps, "
+         "trained on the zeta sweep {0,0.002,0.005,0.01}")
 ENS_ZETA, ENS_LAMBDA, ENS_K = (0.001, 0.005, 0.01), (0.3, 0.7, 1.1), (0.02, 0.04, 0.08)
 
 
@@ -556,6 +560,148 @@ def run_ensemble(args, wl):
         torch.distributed.destroy_process_group()
 
 
+def unet_flops(levels: int, c0: int, n: int) -> float:
+    """Multiply-adds x 2 of one forward pass on an n x n lattice."""
+    ch = [c0 << l for l in range(levels)]
+    f, prev = 0.0, 8
+    for l in range(levels):
+        px = (n >> l) ** 2
+        f += 2 * px * 9 * (prev * ch[l] + ch[l] * ch[l])
+        prev = ch[l]
+    for l in range(levels - 2, -1, -1):
+        px = (n >> l) ** 2
+        f += 2 * px * 9 * ((ch[l + 1] + ch[l]) * ch[l] + ch[l] * ch[l])
+    return f + 2 * n * n * c0 * 7
+
+
+def run_surrogate(args, wl):
+    """Train the surrogate on the sweep's trajectories, then time one
+    prediction (horizon steps of one instance) against the plain step doing
+    the same horizon, and state the prediction's error on a held-out seed."""
+    import numpy as np
+    import torch
+
+    from paper_2511_00445_gb300 import build as bld
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    bld.build()
+    from paper_2511_00445_gb300 import _binding as B
+    dev = torch.device("cuda", local)
+    nx, horizon, levels, c0 = wl["nx"], 50, 4, 32
+    zetas = wl["zetas"]
+    sur = B.Surrogate(levels=levels, base_channels=c0, nx=nx, ny=nx, max_batch=4, max_pairs=64,
+                      horizon=horizon, device=dev)
+    sur.init_weights(7)
+    slot = 0
+    for sd in (1, 2):
+        tf = B.TwoFluid([B.SolverParams(nx=nx, ny=nx, zeta=z) for z in zetas], device=dev)
+        tf.init_fields(rank_seed(sd, rank), phi0=0.5, dphi=0.01, S0=0.3)
+        tf.step(400)
+        for _ in range(8):
+            for b in range(len(zetas)):
+                sur.add_pair(slot + b, tf, b, 0)
+            tf.step(horizon)
+            for b in range(len(zetas)):
+                sur.add_pair(slot + b, tf, b, 1)
+            slot += len(zetas)
+        tf.close()
+    sur.fit_normalisation(slot)
+    train_steps = 800
+    t0 = time.perf_counter()
+    losses = sur.train(slot, steps=train_steps, batch=4, lr=1e-3, seed=3)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+
+    # held-out seed: prediction vs the solver, and persistence
+    def state(seed):
+        tf = B.TwoFluid([B.SolverParams(nx=nx, ny=nx, zeta=z) for z in zetas], device=dev)
+        tf.init_fields(seed, phi0=0.5, dphi=0.01, S0=0.3)
+        tf.step(600)
+        return tf
+    truth, pred = state(rank_seed(11, rank)), state(rank_seed(11, rank))
+    L0 = [truth.length_scale(b) for b in range(len(zetas))]
+    E0 = [truth.energy_spectrum(b) for b in range(len(zetas))]
+    truth.step(horizon)
+    for b in range(len(zetas)):
+        sur.predict(pred, b)
+    err = {"L_rel": [], "L_rel_persist": [], "E_total_rel": [], "E_total_rel_persist": [],
+           "E_shell_l1": [], "E_shell_l1_persist": []}
+    for b in range(len(zetas)):
+        Lt, Lp = truth.length_scale(b), pred.length_scale(b)
+        (Et, Ett), (Ep, Ept) = truth.energy_spectrum(b), pred.energy_spectrum(b)
+        err["L_rel"].append(abs(Lp - Lt) / Lt)
+        err["L_rel_persist"].append(abs(L0[b] - Lt) / Lt)
+        err["E_total_rel"].append(abs(Ept - Ett) / Ett)
+        err["E_total_rel_persist"].append(abs(E0[b][1] - Ett) / Ett)
+        err["E_shell_l1"].append(float(np.abs(Ep - Et).sum() / Et.sum()))
+        err["E_shell_l1_persist"].append(float(np.abs(E0[b][0] - Et).sum() / Et.sum()))
+    err = {k: float(np.mean(v)) for k, v in err.items()}
+
+    # timing: one prediction (one instance, horizon steps) vs the plain step
+    one = B.TwoFluid(B.SolverParams(nx=nx, ny=nx, zeta=0.005), device=dev)
+    one.init_fields(5, phi0=0.5, dphi=0.01, S0=0.3)
+    one.step(100)
+    stream = one.stream
+    for _ in range(args.warmup):
+        sur.predict(one, 0)
+    torch.cuda.synchronize(dev)
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(args.steps):
+            sur.predict(one, 0)
+        b_.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    t_pred = a.elapsed_time(b_) / 1e3 / args.steps
+    one.step(args.warmup * horizon)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        one.step(args.steps * horizon)
+        b_.record(stream)
+    torch.cuda.synchronize(dev)
+    t_plain = a.elapsed_time(b_) / 1e3 / args.steps
+    sites = nx * nx
+    value = horizon * sites / t_pred / 1e6
+    plain = horizon * sites / t_plain / 1e6
+    flops = unet_flops(levels, c0, nx)
+    peak = 1919.9
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = float(json.load(fh)["bf16_tflops"])
+        peak_kind = "measured burst"
+    except (OSError, KeyError, ValueError):
+        peak_kind = "fallback"
+    achieved = flops / t_pred / 1e12
+    train_flops = 3 * flops * 4 * train_steps / t_train / 1e12
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_pred * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic (solver trajectories from the seeded initial condition of Sec. III)",
+            "config": {"workload": wl["name"], "sites_per_step": sites,
+                       "step": "one prediction = 50 lattice steps of one 256^2 instance",
+                       "value": "equivalent MLUPS = 50 x sites / prediction time",
+                       "l2": "not flushed (activations of one prediction ~60 MB)",
+                       "timing": "CUDA events around K predictions on the solver stream"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "whole prediction (tcgen05 convolutions + element-wise)",
+                         "flops_per_prediction": flops},
+            "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": None,
+            "surrogate": {"plain_value": plain, "speedup_vs_plain": value / plain,
+                          "error_vs_solver_heldout": err, "train_steps": train_steps,
+                          "train_pairs": slot, "train_seconds": t_train,
+                          "train_tflops": train_flops,
+                          "loss_first_last": [float(np.mean(losses[:5])), float(np.mean(losses[-20:]))]},
+        }
+        print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,6 +724,8 @@ def main(argv=None):
         run_reference(args, wl)
     elif wl.get("ensemble"):
         run_ensemble(args, wl)
+    elif wl.get("surrogate"):
+        run_surrogate(args, wl)
     else:
         run_ours(args, wl)
 
