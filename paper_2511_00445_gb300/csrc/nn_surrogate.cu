@@ -19,77 +19,6 @@ constexpr int CIN = TF_SUR_IN, COUT = TF_SUR_OUT;
 __device__ __forceinline__ int wrap_i(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // ------------------------------------------------------------ GEMM operations
-// Forward 3x3 convolution with circular padding, bias and optional ReLU:
-// out[p][o] = b[o] + sum_{tap, c} W[o][tap][c] in[p + d(tap)][c].
-struct ConvFwd {
-    int M, N, K;
-    int* err;
-    const bf16* in;
-    const bf16* w;       // [cout][9 cin]
-    const float* bias;
-    bf16* out;
-    int H, W, cin, cout, relu;
-    __device__ uint4 a_chunk(int m, int k8) const {
-        const int k = k8 * 8;
-        if (m >= M || k >= K) return make_uint4(0, 0, 0, 0);
-        const int tap = k / cin, c0 = k - tap * cin;
-        const int x = m % W, t = m / W, y = t % H, b = t / H;
-        const int yy = wrap_i(y + tap / 3 - 1, H), xx = wrap_i(x + tap % 3 - 1, W);
-        return *reinterpret_cast<const uint4*>(in + ((size_t)(b * H + yy) * W + xx) * cin + c0);
-    }
-    __device__ uint4 b_chunk(int n, int k8) const {
-        const int k = k8 * 8;
-        if (n >= N || k >= K) return make_uint4(0, 0, 0, 0);
-        return *reinterpret_cast<const uint4*>(w + (size_t)n * K + k);
-    }
-    __device__ void epilogue(int m, int n0, const float (&v)[16]) const {
-        __align__(16) bf16 o[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            float z = v[j] + (n0 + j < N ? bias[n0 + j] : 0.f);
-            if (relu) z = fmaxf(z, 0.f);
-            o[j] = __float2bfloat16_rn(z);
-        }
-        bf16* dst = out + (size_t)m * cout + n0;
-        if (n0 + 16 <= N) {
-            reinterpret_cast<uint4*>(dst)[0] = reinterpret_cast<const uint4*>(o)[0];
-            reinterpret_cast<uint4*>(dst)[1] = reinterpret_cast<const uint4*>(o)[1];
-        } else {
-            for (int j = 0; j < 16 && n0 + j < N; ++j) dst[j] = o[j];
-        }
-    }
-};
-
-// Input gradient: dx[p][c] += sum_{tap, o} W[o][tap][c] dz[p - d(tap)][o],
-// with the transposed weights wt[c][tap][o].
-struct ConvBwdData {
-    int M, N, K;
-    int* err;
-    const bf16* dz;
-    const bf16* wt;      // [cin][9 cout]
-    float* dx;
-    int H, W, cin, cout;
-    __device__ uint4 a_chunk(int m, int k8) const {
-        const int k = k8 * 8;
-        if (m >= M || k >= K) return make_uint4(0, 0, 0, 0);
-        const int tap = k / cout, c0 = k - tap * cout;
-        const int x = m % W, t = m / W, y = t % H, b = t / H;
-        const int yy = wrap_i(y - (tap / 3 - 1), H), xx = wrap_i(x - (tap % 3 - 1), W);
-        return *reinterpret_cast<const uint4*>(dz + ((size_t)(b * H + yy) * W + xx) * cout + c0);
-    }
-    __device__ uint4 b_chunk(int n, int k8) const {
-        const int k = k8 * 8;
-        if (n >= N || k >= K) return make_uint4(0, 0, 0, 0);
-        return *reinterpret_cast<const uint4*>(wt + (size_t)n * K + k);
-    }
-    __device__ void epilogue(int m, int n0, const float (&v)[16]) const {
-        float* dst = dx + (size_t)m * cin + n0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (n0 + j < N) dst[j] += v[j];
-    }
-};
-
 // Weight gradient: dW[o][tap][c] += sum_p dz[p][o] in[p + d(tap)][c] over a
 // split of the pixels, from channel-major copies dzT[o][p] and inT[c][p].
 struct ConvBwdW {
@@ -142,6 +71,28 @@ cudaError_t run_gemm(const Op& op, int splits, cudaStream_t st) {
     const dim3 grid((op.M + tcg::BM - 1) / tcg::BM, (op.N + BN - 1) / BN, splits);
     tcg::k_gemm<BN, Op><<<grid, tcg::NTHREADS, tcg::smem_bytes<BN>(), st>>>(op, per);
     return cudaGetLastError();
+}
+
+// Row-segment convolutions (forward and input gradient, tcg::k_conv_rows).
+template <int BN, bool GRAD>
+cudaError_t run_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(tcg::k_conv_rows<BN, GRAD>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tcg::row_smem_bytes<BN>());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int segs = (a.W + tcg::ROW_T - 1) / tcg::ROW_T;
+    const dim3 grid(segs * a.H * a.B, (a.Nout + BN - 1) / BN);
+    tcg::k_conv_rows<BN, GRAD><<<grid, tcg::ROW_NT, tcg::row_smem_bytes<BN>(), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool GRAD>
+cudaError_t conv_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
+    return a.Nout <= 32 ? run_rows<32, GRAD>(a, st) : run_rows<64, GRAD>(a, st);
 }
 
 template <class Op>
@@ -626,21 +577,10 @@ cudaError_t forward_pass(tf_surrogate* s, int B) {
             const Conv& cv = s->convs[op.a];
             const Tensor& ti = s->tensors[cv.in_t];
             const int H = s->cfg.ny >> ti.level, W = s->cfg.nx >> ti.level;
-            ConvFwd g;
-            g.M = B * H * W;
-            g.N = cv.cout;
-            g.K = 9 * cv.cin;
-            g.err = err;
-            g.in = s->at<bf16>(ti.act);
-            g.w = s->at<bf16>(cv.wb);
-            g.bias = P + cv.b_off;
-            g.out = s->at<bf16>(s->tensors[cv.out_t].act);
-            g.H = H;
-            g.W = W;
-            g.cin = cv.cin;
-            g.cout = cv.cout;
-            g.relu = 1;
-            cudaError_t e = gemm(g, 1, st);
+            tcg::ConvRowArgs g{s->at<bf16>(ti.act), s->at<bf16>(cv.wb), P + cv.b_off,
+                               s->at<bf16>(s->tensors[cv.out_t].act), nullptr,
+                               B, H, W, cv.cin, cv.cout, 1, err};
+            cudaError_t e = conv_rows<false>(g, st);
             if (e != cudaSuccess) return e;
         } else if (op.kind == OP_POOL) {
             const Tensor& a = s->tensors[op.a];
@@ -715,19 +655,9 @@ cudaError_t backward_pass(tf_surrogate* s, int B, double* loss) {
             if (e != cudaSuccess) return e;
             k_bias_grad<<<cv.cout, EB, 0, st>>>(dzT, Pp, G + cv.b_off);
             if (cv.in_t != s->x_t) {
-                ConvBwdData gd;
-                gd.M = (int)Pp;
-                gd.N = cv.cin;
-                gd.K = 9 * cv.cout;
-                gd.err = err;
-                gd.dz = dz;
-                gd.wt = s->at<bf16>(cv.wt);
-                gd.dx = s->at<float>(ti.grad);
-                gd.H = H;
-                gd.W = W;
-                gd.cin = cv.cin;
-                gd.cout = cv.cout;
-                e = gemm(gd, 1, st);
+                const tcg::ConvRowArgs gd{dz, s->at<bf16>(cv.wt), nullptr, nullptr,
+                                          s->at<float>(ti.grad), B, H, W, cv.cout, cv.cin, 0, err};
+                e = conv_rows<true>(gd, st);
                 if (e != cudaSuccess) return e;
             }
         } else if (op.kind == OP_POOL) {

@@ -151,9 +151,10 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm(const Op op, int chunks_per_s
         const int s = (used - 1) & 1;
         ok = ok && mbar_wait(&bars[s], phase[s]);
     }
+    // tcgen05.ld below is warp-collective: decide for the whole CTA
+    ok = __syncthreads_and(ok) != 0;
     if (!ok && tid == 0) atomicExch(op.err, TF_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
     if (used > 0 && ok) {
         const int m = m0 + warp * 32 + (tid & 31);
 #pragma unroll 1
@@ -172,6 +173,215 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm(const Op op, int chunks_per_s
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
             if (m < op.M && n0 + c0 < op.N) op.epilogue(m, n0 + c0, v);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                     "r"(TCOLS));
+}
+
+// ---------------------------------------------------------------------------
+// Row-segment 3x3 convolution on the tensor cores.
+//
+// One CTA computes output pixels (b, y, x0 .. x0 + T - 1), T = min(W - x0, 128),
+// for output channels n0 .. n0 + BN - 1.  For each chunk of up to 64 source
+// channels it stages the three source rows y - 1, y, y + 1 (columns x0 - 1 ..
+// x0 + T, periodic) in shared memory as 16-byte pixel rows (8 channels each,
+// one block per 8-channel group), and the weights of all nine taps for those
+// channels.  In that layout the A operand of tap (dy, dx) is the same tile
+// read from a start address shifted by whole pixel rows, so the nine taps
+// need no further loads: 9 x (channels / 16) MMAs per chunk.  Rows of A past
+// the T valid pixels read staged data of other rows; their results are
+// discarded by the epilogue.
+//   GRAD = false: out[p][n] = relu?(bias[n] + sum_{tap, c} w[n][tap][c] src[p + d(tap)][c])
+//   GRAD = true : dx[p][n] += sum_{tap, c} w[n][tap][c] src[p - d(tap)][c]
+// (the input gradient with w the transposed weights wt[cin][tap][cout]).
+// ---------------------------------------------------------------------------
+struct ConvRowArgs {
+    const __nv_bfloat16* src;   // NHWC, Cs channels
+    const __nv_bfloat16* w;     // [Nout][9][Cs]
+    const float* bias;          // forward only
+    __nv_bfloat16* out;         // forward: NHWC BF16, Nout channels
+    float* dx;                  // gradient: NHWC FP32, Nout channels (accumulated)
+    int B, H, W, Cs, Nout, relu;
+    int* err;
+};
+
+constexpr int ROW_T = 128;      // output pixels per CTA
+constexpr int ROW_CC = 64;      // source channels per chunk
+constexpr int ROW_NT = 256;     // threads: all stage operands; warps w and w + 4 share
+                                // tensor-memory lanes 32 (w % 4) .. in the epilogue
+constexpr int ROW_UNROLL = 8;   // 16-byte loads in flight per thread while staging
+
+__host__ __device__ constexpr int row_halo_rows(int T) {
+    return 3 * (T + 2) > 2 * (T + 2) + 2 + ROW_T ? 3 * (T + 2) : 2 * (T + 2) + 2 + ROW_T;
+}
+
+template <int BN>
+constexpr int row_smem_bytes() {
+    return 8 * row_halo_rows(ROW_T) * 16 + 36 * BN * 32;
+}
+
+template <int BN, bool GRAD>
+__global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
+    constexpr int TCOLS = BN < 32 ? 32 : BN;
+    constexpr int HR = row_halo_rows(ROW_T);          // staged rows per 8-channel block
+    constexpr int A_BYTES = 8 * HR * 16;
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    unsigned char* As = tc_smem;
+    unsigned char* Bs = tc_smem + A_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int segs = (a.W + ROW_T - 1) / ROW_T;
+    const int seg = blockIdx.x % segs, y = (blockIdx.x / segs) % a.H, b = blockIdx.x / (segs * a.H);
+    const int x0 = seg * ROW_T, T = min(ROW_T, a.W - x0), Tp = T + 2;
+    const int n0 = blockIdx.y * BN;
+    const int sgn = GRAD ? -1 : 1;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tmem_base;
+    uint32_t phase = 0;
+    bool ok = true;
+    const int nchunks = (a.Cs + ROW_CC - 1) / ROW_CC;
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const int c_base = ch * ROW_CC;
+        const int csteps = min(ROW_CC, (a.Cs - c_base + 15) & ~15) / 16;   // K = 16 steps
+        const int cgroups = 2 * csteps;                                    // 8-channel groups
+        // stage the source rows: pixel q of row r (q = 0 .. Tp-1) at block g, row r*Tp + q
+        const int na = 3 * Tp * cgroups;
+        for (int i0 = tid; i0 < na; i0 += ROW_NT * ROW_UNROLL) {
+            uint4 v[ROW_UNROLL];
+            uint32_t dst[ROW_UNROLL];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) {
+                const int i = i0 + u * ROW_NT;
+                v[u] = zero;
+                dst[u] = 0xFFFFFFFFu;
+                if (i < na) {
+                    const int g = i % cgroups, q = (i / cgroups) % Tp, r = i / (cgroups * Tp);
+                    const int c = c_base + 8 * g;
+                    dst[u] = (uint32_t)((g * HR + r * Tp + q) * 16);
+                    if (c < a.Cs) {
+                        int yy = y + sgn * (r - 1), xx = x0 - 1 + q;
+                        yy = yy < 0 ? yy + a.H : (yy >= a.H ? yy - a.H : yy);
+                        xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+                        v[u] = *reinterpret_cast<const uint4*>(
+                            a.src + ((size_t)(b * a.H + yy) * a.W + xx) * a.Cs + c);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u)
+                if (dst[u] != 0xFFFFFFFFu) *reinterpret_cast<uint4*>(As + dst[u]) = v[u];
+        }
+        // weights of the chunk: slice (tap, step) is a BN x 16 K-major tile
+        const int nb = 9 * BN * cgroups;
+        for (int i0 = tid; i0 < nb; i0 += ROW_NT * ROW_UNROLL) {
+            uint4 v[ROW_UNROLL];
+            uint32_t dst[ROW_UNROLL];
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u) {
+                const int i = i0 + u * ROW_NT;
+                v[u] = zero;
+                dst[u] = 0xFFFFFFFFu;
+                if (i < nb) {
+                    const int g = i % cgroups, n = (i / cgroups) % BN, tap = i / (cgroups * BN);
+                    const int c = c_base + 8 * g;
+                    const int slice = tap * (ROW_CC / 16) + (g >> 1);
+                    dst[u] = (uint32_t)(slice * BN * 32) + tile_off(n, 8 * (g & 1), BN);
+                    if (n0 + n < a.Nout && c < a.Cs)
+                        v[u] = *reinterpret_cast<const uint4*>(a.w + ((size_t)(n0 + n) * 9 + tap) * a.Cs + c);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < ROW_UNROLL; ++u)
+                if (dst[u] != 0xFFFFFFFFu) *reinterpret_cast<uint4*>(Bs + dst[u]) = v[u];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int tap = 0; tap < 9; ++tap) {
+                // source pixel of output pixel r for this tap: staged row (1 + dy), column r + 1 + dx
+                // (the staging already applied the sign of the row offset)
+                const int dx = sgn * (tap % 3 - 1);
+                const int row0 = (tap / 3) * Tp + 1 + dx;
+                for (int s = 0; s < csteps; ++s) {
+                    const uint64_t ad = smem_desc(smem_u32(As) + (2 * s * HR + row0) * 16, HR * 16, 128);
+                    const int slice = tap * (ROW_CC / 16) + s;
+                    const uint64_t bd = smem_desc(smem_u32(Bs) + slice * BN * 32, BN * 16, 128);
+                    const uint32_t acc = (ch > 0 || tap > 0 || s > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tbase),
+                        "l"(ad), "l"(bd), "r"(instr_desc(BM, BN)), "r"(acc));
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&bar)));
+        }
+        ok = ok && mbar_wait(&bar, phase);
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();   // the next chunk overwrites the staged tiles
+    }
+    ok = __syncthreads_and(ok) != 0;   // the loads below are warp-collective
+    if (!ok && tid == 0) atomicExch(a.err, TF_ERR_TIMEOUT);
+    if (ok) {
+        const int lane_row = (warp & 3) * 32 + (tid & 31);   // tensor-memory lane = output row
+        const size_t p = (size_t)(b * a.H + y) * a.W + x0 + lane_row;
+        const int half = warp >> 2;                          // columns [half * BN/2, (half+1) * BN/2)
+#pragma unroll 1
+        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2) && n0 + c0 < a.Nout; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (lane_row >= T) continue;   // rows past the segment hold discarded results
+            const int n = n0 + c0;
+            if (GRAD) {
+                float* d = a.dx + p * a.Nout + n;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (n + j < a.Nout) d[j] += __uint_as_float(r[j]);
+            } else {
+                __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float z = __uint_as_float(r[j]) + (n + j < a.Nout ? a.bias[n + j] : 0.f);
+                    if (a.relu) z = fmaxf(z, 0.f);
+                    o[j] = __float2bfloat16_rn(z);
+                }
+                __nv_bfloat16* d = a.out + p * a.Nout + n;
+                if (n + 16 <= a.Nout) {
+                    reinterpret_cast<uint4*>(d)[0] = reinterpret_cast<const uint4*>(o)[0];
+                    reinterpret_cast<uint4*>(d)[1] = reinterpret_cast<const uint4*>(o)[1];
+                } else {
+                    for (int j = 0; j < 16 && n + j < a.Nout; ++j) d[j] = o[j];
+                }
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
