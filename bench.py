@@ -664,6 +664,27 @@ def run_surrogate(args, wl):
         b_.record(stream)
     torch.cuda.synchronize(dev)
     t_plain = a.elapsed_time(b_) / 1e3 / args.steps
+    one.close()
+    # the whole sweep (four instances) predicted as one batch vs the batched plain step
+    sweep = state(rank_seed(21, rank))
+    for _ in range(args.warmup):
+        sur.predict(sweep, -1)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(args.steps):
+            sur.predict(sweep, -1)
+        b_.record(stream)
+    torch.cuda.synchronize(dev)
+    t_pred4 = a.elapsed_time(b_) / 1e3 / args.steps
+    sweep.step(args.warmup * horizon)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        sweep.step(args.steps * horizon)
+        b_.record(stream)
+    torch.cuda.synchronize(dev)
+    t_plain4 = a.elapsed_time(b_) / 1e3 / args.steps
     sites = nx * nx
     value = horizon * sites / t_pred / 1e6
     plain = horizon * sites / t_plain / 1e6
@@ -694,6 +715,12 @@ def run_surrogate(args, wl):
                          "flops_per_prediction": flops},
             "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": None,
             "surrogate": {"plain_value": plain, "speedup_vs_plain": value / plain,
+                          "sweep4": {"value": horizon * 4 * sites / t_pred4 / 1e6,
+                                     "plain_value": horizon * 4 * sites / t_plain4 / 1e6,
+                                     "speedup_vs_plain": t_plain4 / t_pred4,
+                                     "tflops": flops * 4 / t_pred4 / 1e12,
+                                     "how": "four sweep instances predicted as one batch vs "
+                                            "the plain step of the same batch"},
                           "error_vs_solver_heldout": err, "train_steps": train_steps,
                           "train_pairs": slot, "train_seconds": t_train,
                           "train_tflops": train_flops,

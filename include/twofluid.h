@@ -385,11 +385,12 @@ int tf_sur_fit_normalisation(tf_surrogate* s, int n_pairs);
 int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, uint64_t seed,
                  double* losses);
 
-/* Advance instance `inst` of `ctx` by `horizon` steps with the network: its
- * phi and Q are replaced by the prediction and its populations by the
- * equilibrium of its rest densities and the predicted u1, u2.  The
- * context's step count (one counter for all its instances) is unchanged.
- * Asynchronous on the shared stream. */
+/* Advance instance `inst` of `ctx` (inst = -1: every instance, predicted as
+ * one batch of at most max_batch) by `horizon` steps with the network: phi
+ * and Q are replaced by the prediction and the populations by the
+ * equilibrium of the rest densities and the predicted u1, u2.  The context's
+ * step count (one counter for all its instances) is unchanged.  Asynchronous
+ * on the shared stream. */
 int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst);
 
 /* ---- fixed-footprint entry point ------------------------------------- */

@@ -92,7 +92,13 @@ cudaError_t run_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
 
 template <bool GRAD>
 cudaError_t conv_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
-    return a.Nout <= 32 ? run_rows<32, GRAD>(a, st) : run_rows<64, GRAD>(a, st);
+    return run_rows<tcg::ROW_BN, GRAD>(a, st);
+}
+
+// Bytes of one layer's pre-tiled weights (tcg::row_wtile_index).
+size_t wtile_bytes(int nout, int cs) {
+    return (size_t)((nout + tcg::ROW_BN - 1) / tcg::ROW_BN) * ((cs + tcg::ROW_CC - 1) / tcg::ROW_CC) *
+           tcg::ROW_WTILE;
 }
 
 template <class Op>
@@ -106,21 +112,35 @@ cudaError_t gemm(const Op& op, int splits, cudaStream_t st) {
 // ------------------------------------------------------ element-wise kernels
 inline unsigned blocks(long long n) { return (unsigned)((n + EB - 1) / EB); }
 
+// 2x2 average pool, 8 channels (16 bytes) per thread.
 __global__ void k_pool(const bf16* __restrict__ in, bf16* __restrict__ out, int B, int H, int W,
                        int C) {   // in: H x W, out: H/2 x W/2
-    const long long n = (long long)B * (H / 2) * (W / 2) * C;
+    const int G = C / 8;
+    const long long n = (long long)B * (H / 2) * (W / 2) * G;
     const long long i = (long long)blockIdx.x * EB + threadIdx.x;
     if (i >= n) return;
-    const int c = (int)(i % C);
-    long long t = i / C;
+    const int g = (int)(i % G);
+    long long t = i / G;
     const int x = (int)(t % (W / 2));
     t /= (W / 2);
     const int y = (int)(t % (H / 2)), b = (int)(t / (H / 2));
     auto at = [&](int yy, int xx) {
-        return __bfloat162float(in[((size_t)(b * H + yy) * W + xx) * C + c]);
+        return *reinterpret_cast<const uint4*>(in + ((size_t)(b * H + yy) * W + xx) * C + 8 * g);
     };
-    const float s = at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1);
-    out[i] = __float2bfloat16_rn(0.25f * s);
+    const uint4 q0 = at(2 * y, 2 * x), q1 = at(2 * y, 2 * x + 1), q2 = at(2 * y + 1, 2 * x),
+                q3 = at(2 * y + 1, 2 * x + 1);
+    const bf16* v0 = reinterpret_cast<const bf16*>(&q0);
+    const bf16* v1 = reinterpret_cast<const bf16*>(&q1);
+    const bf16* v2 = reinterpret_cast<const bf16*>(&q2);
+    const bf16* v3 = reinterpret_cast<const bf16*>(&q3);
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float s4 = __bfloat162float(v0[k]) + __bfloat162float(v1[k]) + __bfloat162float(v2[k]) +
+                         __bfloat162float(v3[k]);
+        o[k] = __float2bfloat16_rn(0.25f * s4);
+    }
+    *reinterpret_cast<uint4*>(out + (size_t)(i / G) * C + 8 * g) = *reinterpret_cast<const uint4*>(o);
 }
 
 __global__ void k_pool_bwd(const float* __restrict__ d, float* __restrict__ dx, int B, int H,
@@ -138,26 +158,31 @@ __global__ void k_pool_bwd(const float* __restrict__ d, float* __restrict__ dx, 
 
 // Nearest upsampling of src (H/2 x W/2, Cs channels) into channels [0, Cs) of
 // the concatenation dst (H x W, Cd channels); k_copy_ch puts the skip into
-// channels [Cs, Cd).
+// channels [Cs, Cd).  8 channels (16 bytes) per thread.
 __global__ void k_up_into(const bf16* __restrict__ src, bf16* __restrict__ dst, int B, int H,
                           int W, int Cs, int Cd) {
-    const long long n = (long long)B * H * W * Cs;
+    const int G = Cs / 8;
+    const long long n = (long long)B * H * W * G;
     const long long i = (long long)blockIdx.x * EB + threadIdx.x;
     if (i >= n) return;
-    const int c = (int)(i % Cs);
-    const long long p = i / Cs;
+    const int g = (int)(i % G);
+    const long long p = i / G;
     const int x = (int)(p % W);
     const long long t = p / W;
     const int y = (int)(t % H), b = (int)(t / H);
-    dst[p * Cd + c] = src[((size_t)(b * (H / 2) + y / 2) * (W / 2) + x / 2) * Cs + c];
+    *reinterpret_cast<uint4*>(dst + p * Cd + 8 * g) = *reinterpret_cast<const uint4*>(
+        src + ((size_t)(b * (H / 2) + y / 2) * (W / 2) + x / 2) * Cs + 8 * g);
 }
 
 __global__ void k_copy_ch(const bf16* __restrict__ src, bf16* __restrict__ dst, long long P,
                           int Cs, int Cd, int off) {
+    const int G = Cs / 8;
     const long long i = (long long)blockIdx.x * EB + threadIdx.x;
-    if (i >= P * Cs) return;
-    const long long p = i / Cs;
-    dst[p * Cd + off + (i % Cs)] = src[i];
+    if (i >= P * G) return;
+    const long long p = i / G;
+    const int g = (int)(i % G);
+    *reinterpret_cast<uint4*>(dst + p * Cd + off + 8 * g) =
+        *reinterpret_cast<const uint4*>(src + p * Cs + 8 * g);
 }
 
 // Gradient of [upsampled, skip]: the skip part accumulates into dskip, the
@@ -298,17 +323,19 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// BF16 copies of one convolution's weights: w[o][tap][c] and wt[c][tap][o].
-__global__ void k_weights_bf16(const float* __restrict__ w, bf16* __restrict__ wb,
-                               bf16* __restrict__ wt, int cout, int cin) {
+// BF16 copies of one convolution's weights w[o][tap][c], pre-tiled for the
+// forward pass (rows o, source channels c) and for the input gradient (rows
+// c, source channels o).  Tile entries outside the layer stay zero.
+__global__ void k_weights_bf16(const float* __restrict__ w, unsigned char* __restrict__ wf,
+                               unsigned char* __restrict__ wg, int cout, int cin) {
     const long long n = (long long)cout * 9 * cin;
     const long long i = (long long)blockIdx.x * EB + threadIdx.x;
     if (i >= n) return;
     const int c = (int)(i % cin);
     const int tap = (int)((i / cin) % 9), o = (int)(i / (9LL * cin));
     const bf16 v = __float2bfloat16_rn(w[i]);
-    wb[i] = v;
-    wt[((size_t)c * 9 + tap) * cout + o] = v;
+    *reinterpret_cast<bf16*>(wf + tcg::row_wtile_index(o, tap, c, cin)) = v;
+    *reinterpret_cast<bf16*>(wg + tcg::row_wtile_index(c, tap, o, cout)) = v;
 }
 
 // Raw fields of a solver instance: phi - phi_ref, Q_xx, Q_xy, u1x, u1y, u2x, u2y.
@@ -381,24 +408,37 @@ __global__ void k_assemble(const float* __restrict__ data, const int* __restrict
     *reinterpret_cast<uint4*>(x + j * 8) = *reinterpret_cast<const uint4*>(xv);
 }
 
-// Prediction back to FP64 planes: phi (absolute), Q_xx, Q_xy, and u1, u2 as
-// [2][N] each (the layouts tf_launch_write_field / set_equilibrium take).
-__global__ void k_predict_out(const float* __restrict__ raw, const float* __restrict__ pred, Norm nm,
-                              double phi_ref, long long N, double* __restrict__ phi,
-                              double* __restrict__ qxx, double* __restrict__ qxy,
-                              double* __restrict__ u1, double* __restrict__ u2) {
+// Prediction written into instance b of a solver context: the stored phi
+// deviation and Q planes, and the populations at the equilibrium of the rest
+// densities and the predicted velocities (pull layout: f_i(x) is stored at
+// x - c_i), in the context's storage mode.  FP32 arithmetic.
+__global__ void k_writeback(const float* __restrict__ raw, const float* __restrict__ pred, Norm nm,
+                            int nx, int ny, int b, float* __restrict__ phi, float* __restrict__ Q,
+                            void* __restrict__ f, const DevParams* __restrict__ prm, int storage) {
+    const long long N = (long long)nx * ny;
     const long long i = (long long)blockIdx.x * EB + threadIdx.x;
     if (i >= N) return;
-    double v[7];
-    for (int c = 0; c < 7; ++c)
-        v[c] = (double)raw[c * N + i] + (double)nm.dmean[c] + (double)nm.dstd[c] * pred[i * 7 + c];
-    phi[i] = phi_ref + v[0];
-    qxx[i] = v[1];
-    qxy[i] = v[2];
-    u1[i] = v[3];
-    u1[N + i] = v[4];
-    u2[i] = v[5];
-    u2[N + i] = v[6];
+    float v[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) v[c] = raw[c * N + i] + nm.dmean[c] + nm.dstd[c] * pred[i * 7 + c];
+    phi[b * N + i] = v[0];
+    Q[2 * b * N + i] = v[1];
+    Q[(2 * b + 1) * N + i] = v[2];
+    const int x = (int)(i % nx), y = (int)(i / nx);
+#pragma unroll
+    for (int fl = 0; fl < 2; ++fl) {
+        const float ux = v[3 + 2 * fl], uy = v[4 + 2 * fl];
+        const float rho = fl ? prm[b].rho2 : prm[b].rho1;
+        const float uu = ux * ux + uy * uy;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float cu = d2q9_cx(k) * ux + d2q9_cy(k) * uy;
+            const float w = d2q9_w(k);
+            const float dev = w * (rho - 1.f) + w * rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+            const int sx = wrap_i(x - d2q9_cx(k), nx), sy = wrap_i(y - d2q9_cy(k), ny);
+            pop_store(f, (18LL * b + 9 * fl + k) * N + (long long)sy * nx + sx, dev, storage);
+        }
+    }
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014) for weight initialisation and
@@ -442,7 +482,7 @@ struct tf_surrogate {
     // workspace regions (byte offsets)
     size_t p_off = 0, g_off = 0, m_off = 0, v_off = 0, wbf_off = 0, act_off = 0, grad_off = 0;
     size_t dz_off = 0, dzT_off = 0, inT_off = 0, pred_off = 0, tgt_off = 0, dpred_off = 0;
-    size_t data_off = 0, zeta_off = 0, idx_off = 0, part_off = 0, err_off = 0, out64_off = 0;
+    size_t data_off = 0, zeta_off = 0, idx_off = 0, part_off = 0, err_off = 0;
     size_t raw_off = 0, total = 0;
     long long max_cp = 0;        // largest pixels x channels of any tensor at max_batch
     std::vector<float> zeta;     // per pair
@@ -538,8 +578,8 @@ size_t plan(tf_surrogate* s) {
     s->m_off = take(np * 4);
     s->v_off = take(np * 4);
     for (Conv& cv : s->convs) {
-        cv.wb = take((size_t)cv.cout * 9 * cv.cin * 2);
-        cv.wt = take((size_t)cv.cout * 9 * cv.cin * 2);
+        cv.wb = take(wtile_bytes(cv.cout, cv.cin));
+        cv.wt = take(wtile_bytes(cv.cin, cv.cout));
     }
     long long max_cp = 0;
     for (Tensor& t : s->tensors) {
@@ -557,11 +597,10 @@ size_t plan(tf_surrogate* s) {
     s->tgt_off = take((size_t)P0 * COUT * 4);
     s->dpred_off = take((size_t)P0 * COUT * 4);
     s->data_off = take((size_t)c.max_pairs * 14 * N * 4);
-    s->raw_off = take((size_t)14 * N * 4);                 // prediction input slot
-    s->zeta_off = take((size_t)(c.max_pairs + 1) * 4);
+    s->raw_off = take((size_t)B * 14 * N * 4);             // prediction inputs (one per instance)
+    s->zeta_off = take((size_t)(c.max_pairs + B) * 4);
     s->idx_off = take((size_t)B * 4);
     s->part_off = take(1024 * 28 * 8);
-    s->out64_off = take((size_t)7 * N * 8);
     s->err_off = take(64);
     s->total = off;
     return off;
@@ -585,7 +624,7 @@ cudaError_t forward_pass(tf_surrogate* s, int B) {
         } else if (op.kind == OP_POOL) {
             const Tensor& a = s->tensors[op.a];
             const int H = s->cfg.ny >> a.level, W = s->cfg.nx >> a.level;
-            k_pool<<<blocks((long long)B * H * W * a.C / 4), EB, 0, st>>>(
+            k_pool<<<blocks((long long)B * H * W * a.C / 32), EB, 0, st>>>(
                 s->at<bf16>(a.act), s->at<bf16>(s->tensors[op.b].act), B, H, W, a.C);
         } else {
             const Tensor& up = s->tensors[op.a];
@@ -593,10 +632,10 @@ cudaError_t forward_pass(tf_surrogate* s, int B) {
             const Tensor& cat = s->tensors[op.c];
             const int H = s->cfg.ny >> cat.level, W = s->cfg.nx >> cat.level;
             const long long Pp = (long long)B * H * W;
-            k_up_into<<<blocks(Pp * up.C), EB, 0, st>>>(s->at<bf16>(up.act), s->at<bf16>(cat.act),
-                                                       B, H, W, up.C, cat.C);
-            k_copy_ch<<<blocks(Pp * sk.C), EB, 0, st>>>(s->at<bf16>(sk.act), s->at<bf16>(cat.act),
-                                                       Pp, sk.C, cat.C, up.C);
+            k_up_into<<<blocks(Pp * up.C / 8), EB, 0, st>>>(s->at<bf16>(up.act), s->at<bf16>(cat.act),
+                                                           B, H, W, up.C, cat.C);
+            k_copy_ch<<<blocks(Pp * sk.C / 8), EB, 0, st>>>(s->at<bf16>(sk.act), s->at<bf16>(cat.act),
+                                                           Pp, sk.C, cat.C, up.C);
         }
     }
     const Tensor& d0 = s->tensors[s->dec0_t];
@@ -694,7 +733,7 @@ cudaError_t refresh_bf16(tf_surrogate* s) {
     const float* P = s->at<float>(s->p_off);
     for (const Conv& cv : s->convs)
         k_weights_bf16<<<blocks((long long)cv.cout * 9 * cv.cin), EB, 0, s->stream>>>(
-            P + cv.w_off, s->at<bf16>(cv.wb), s->at<bf16>(cv.wt), cv.cout, cv.cin);
+            P + cv.w_off, s->at<unsigned char>(cv.wb), s->at<unsigned char>(cv.wt), cv.cout, cv.cin);
     return cudaGetLastError();
 }
 
@@ -928,35 +967,39 @@ int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, 
 int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst) {
     if (!s || !ctx) return TF_ERR_ARG;
     if (!s->norm_ready) return sfail(s, TF_ERR_ARG, "call tf_sur_fit_normalisation first");
-    if (inst < 0 || inst >= ctx->batch) return sfail(s, TF_ERR_ARG, "bad instance");
+    const int i0 = inst < 0 ? 0 : inst, nb = inst < 0 ? ctx->batch : 1;
+    if (inst < -1 || inst >= ctx->batch) return sfail(s, TF_ERR_ARG, "bad instance");
+    if (nb > s->cfg.max_batch) return sfail(s, TF_ERR_ARG, "more instances than max_batch");
     if (ctx->nx != s->cfg.nx || ctx->ny != s->cfg.ny || ctx->stream != s->stream)
         return sfail(s, TF_ERR_ARG, "solver grid or stream differs from the surrogate's");
     const long long N = ctx->N;
     SCK(s, tf_launch_flush(ctx));
-    ctx->fd_pending = false;
     SCK(s, tf_launch_macro(ctx, ctx->d.macro));
+    // Prediction inputs: slot k holds instance i0 + k; their zetas follow the dataset's.
     float* raw = s->at<float>(s->raw_off);
-    k_capture<<<blocks(N), EB, 0, s->stream>>>(ctx->d.phi[ctx->pcur], ctx->d.Q[ctx->pcur], ctx->d.macro, N,
-                                               inst, raw);
-    // The prediction input is "pair 0" of the raw slot, its zeta one entry
-    // past the dataset's.
-    const float z = (float)ctx->params[inst].zeta;
+    std::vector<float> z(nb);
+    std::vector<int> idx(nb);
+    for (int k = 0; k < nb; ++k) {
+        k_capture<<<blocks(N), EB, 0, s->stream>>>(ctx->d.phi[ctx->pcur], ctx->d.Q[ctx->pcur],
+                                                   ctx->d.macro, N, i0 + k, raw + (long long)k * 14 * N);
+        z[k] = (float)ctx->params[i0 + k].zeta;
+        idx[k] = k;
+    }
     float* zslot = s->at<float>(s->zeta_off) + s->cfg.max_pairs;
-    const int zero = 0;
-    SCK(s, cudaMemcpyAsync(zslot, &z, 4, cudaMemcpyHostToDevice, s->stream));
-    SCK(s, cudaMemcpyAsync(s->at<int>(s->idx_off), &zero, 4, cudaMemcpyHostToDevice, s->stream));
-    k_assemble<<<blocks(N), EB, 0, s->stream>>>(raw, s->at<int>(s->idx_off), zslot, s->norm, s->zscale,
-                                                N, 1, s->at<bf16>(s->tensors[s->x_t].act), nullptr);
-    SCK(s, forward_pass(s, 1));
-    double* o = s->at<double>(s->out64_off);
-    k_predict_out<<<blocks(N), EB, 0, s->stream>>>(raw, s->at<float>(s->pred_off), s->norm,
-                                                   (double)ctx->params[inst].phi_ref, N, o, o + N, o + 2 * N,
-                                                   o + 3 * N, o + 5 * N);
+    SCK(s, cudaMemcpyAsync(zslot, z.data(), nb * 4, cudaMemcpyHostToDevice, s->stream));
+    SCK(s, cudaMemcpyAsync(s->at<int>(s->idx_off), idx.data(), nb * 4, cudaMemcpyHostToDevice, s->stream));
+    k_assemble<<<blocks((long long)nb * N), EB, 0, s->stream>>>(
+        raw, s->at<int>(s->idx_off), zslot, s->norm, s->zscale, N, nb,
+        s->at<bf16>(s->tensors[s->x_t].act), nullptr);
+    SCK(s, forward_pass(s, nb));
+    for (int k = 0; k < nb; ++k)
+        k_writeback<<<blocks(N), EB, 0, s->stream>>>(
+            raw + (long long)k * 14 * N, s->at<float>(s->pred_off) + (long long)k * N * COUT, s->norm,
+            ctx->nx, ctx->ny, i0 + k, ctx->d.phi[ctx->pcur], ctx->d.Q[ctx->pcur], ctx->d.f[ctx->fcur],
+            ctx->d.prm, ctx->storage);
     SCK(s, cudaGetLastError());
-    SCK(s, tf_launch_write_field(ctx, inst, TF_FIELD_PHI, o));
-    SCK(s, tf_launch_write_field(ctx, inst, TF_FIELD_QXX, o + N));
-    SCK(s, tf_launch_write_field(ctx, inst, TF_FIELD_QXY, o + 2 * N));
-    SCK(s, tf_launch_set_equilibrium(ctx, inst, o + 3 * N, o + 5 * N));
+    // (copies from pageable host memory return once the source is staged, so
+    // the host vectors may go out of scope without a synchronisation)
     return TF_OK;
 }
 

@@ -25,6 +25,7 @@
 
 #include <cstdint>
 
+#include "tf_ptx.cuh"
 #include "twofluid.h"
 
 namespace tcg {
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm(const Op op, int chunks_per_s
 // ---------------------------------------------------------------------------
 struct ConvRowArgs {
     const __nv_bfloat16* src;   // NHWC, Cs channels
-    const __nv_bfloat16* w;     // [Nout][9][Cs]
+    const __nv_bfloat16* w;     // pre-tiled weights, see row_wtile_index
     const float* bias;          // forward only
     __nv_bfloat16* out;         // forward: NHWC BF16, Nout channels
     float* dx;                  // gradient: NHWC FP32, Nout channels (accumulated)
@@ -213,7 +214,6 @@ constexpr int ROW_T = 128;      // output pixels per CTA
 constexpr int ROW_CC = 64;      // source channels per chunk
 constexpr int ROW_NT = 256;     // threads: all stage operands; warps w and w + 4 share
                                 // tensor-memory lanes 32 (w % 4) .. in the epilogue
-constexpr int ROW_UNROLL = 8;   // 16-byte loads in flight per thread while staging
 
 __host__ __device__ constexpr int row_halo_rows(int T) {
     return 3 * (T + 2) > 2 * (T + 2) + 2 + ROW_T ? 3 * (T + 2) : 2 * (T + 2) + 2 + ROW_T;
@@ -224,13 +224,30 @@ constexpr int row_smem_bytes() {
     return 8 * row_halo_rows(ROW_T) * 16 + 36 * BN * 32;
 }
 
+// Weights pre-tiled in the shared-memory image k_conv_rows stages: for output
+// tile t (channels 32 t ..) and source chunk ch (channels 64 ch ..), one block
+// of 36 slices (tap, 16-channel step) of 32 x 16 K-major core matrices,
+// ROW_WTILE bytes, blocks ordered (t, ch).  Byte offset of weight (n, tap, c)
+// for a layer with Cs source channels:
+constexpr int ROW_BN = 32;
+constexpr int ROW_WTILE = 36 * ROW_BN * 32;
+__host__ __device__ inline long long row_wtile_index(int n, int tap, int c, int Cs) {
+    const int nch = (Cs + ROW_CC - 1) / ROW_CC;
+    const int t = n / ROW_BN, nn = n % ROW_BN, ch = c / ROW_CC, cc = c % ROW_CC;
+    const int slice = tap * (ROW_CC / 16) + cc / 16, k = cc % 16;
+    const long long off_in = (long long)slice * ROW_BN * 32 +
+                             (((k >> 3) * (ROW_BN >> 3) + (nn >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2);
+    return ((long long)t * nch + ch) * ROW_WTILE + off_in;
+}
+
 template <int BN, bool GRAD>
 __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
+    static_assert(BN == ROW_BN, "weights are pre-tiled for ROW_BN output channels");
     constexpr int TCOLS = BN < 32 ? 32 : BN;
     constexpr int HR = row_halo_rows(ROW_T);          // staged rows per 8-channel block
     constexpr int A_BYTES = 8 * HR * 16;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar, wbar;
     __shared__ uint32_t tmem_base;
     unsigned char* As = tc_smem;
     unsigned char* Bs = tc_smem + A_BYTES;
@@ -248,6 +265,7 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -257,61 +275,37 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
     uint32_t phase = 0;
     bool ok = true;
     const int nchunks = (a.Cs + ROW_CC - 1) / ROW_CC;
+    const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(a.w) +
+                                (long long)blockIdx.y * nchunks * ROW_WTILE;
     const uint4 zero = make_uint4(0, 0, 0, 0);
     for (int ch = 0; ch < nchunks; ++ch) {
         const int c_base = ch * ROW_CC;
         const int csteps = min(ROW_CC, (a.Cs - c_base + 15) & ~15) / 16;   // K = 16 steps
         const int cgroups = 2 * csteps;                                    // 8-channel groups
-        // stage the source rows: pixel q of row r (q = 0 .. Tp-1) at block g, row r*Tp + q
+        // the chunk's weights: one bulk copy of the pre-tiled block (lands while
+        // the threads stage the source rows)
+        if (tid == 0) {
+            tfp::mbar_arrive_expect_tx(&wbar, (uint32_t)ROW_WTILE);
+            tfp::bulk_g2s(Bs, wsrc + (long long)ch * ROW_WTILE, (uint32_t)ROW_WTILE, &wbar);
+        }
+        // stage the source rows: pixel q of row r (q = 0 .. Tp-1) at block g, row
+        // r*Tp + q, by asynchronous 16-byte copies (zero-filled past Cs)
         const int na = 3 * Tp * cgroups;
-        for (int i0 = tid; i0 < na; i0 += ROW_NT * ROW_UNROLL) {
-            uint4 v[ROW_UNROLL];
-            uint32_t dst[ROW_UNROLL];
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) {
-                const int i = i0 + u * ROW_NT;
-                v[u] = zero;
-                dst[u] = 0xFFFFFFFFu;
-                if (i < na) {
-                    const int g = i % cgroups, q = (i / cgroups) % Tp, r = i / (cgroups * Tp);
-                    const int c = c_base + 8 * g;
-                    dst[u] = (uint32_t)((g * HR + r * Tp + q) * 16);
-                    if (c < a.Cs) {
-                        int yy = y + sgn * (r - 1), xx = x0 - 1 + q;
-                        yy = yy < 0 ? yy + a.H : (yy >= a.H ? yy - a.H : yy);
-                        xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
-                        v[u] = *reinterpret_cast<const uint4*>(
-                            a.src + ((size_t)(b * a.H + yy) * a.W + xx) * a.Cs + c);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u)
-                if (dst[u] != 0xFFFFFFFFu) *reinterpret_cast<uint4*>(As + dst[u]) = v[u];
+        for (int i = tid; i < na; i += ROW_NT) {
+            const int g = i % cgroups, q = (i / cgroups) % Tp, r = i / (cgroups * Tp);
+            const int c = c_base + 8 * g;
+            int yy = y + sgn * (r - 1), xx = x0 - 1 + q;
+            yy = yy < 0 ? yy + a.H : (yy >= a.H ? yy - a.H : yy);
+            xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+            const bool in = c < a.Cs;
+            const __nv_bfloat16* src = a.src + ((size_t)(b * a.H + yy) * a.W + xx) * a.Cs + (in ? c : 0);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             smem_u32(As + (g * HR + r * Tp + q) * 16)),
+                         "l"(src), "r"(in ? 16 : 0)
+                         : "memory");
         }
-        // weights of the chunk: slice (tap, step) is a BN x 16 K-major tile
-        const int nb = 9 * BN * cgroups;
-        for (int i0 = tid; i0 < nb; i0 += ROW_NT * ROW_UNROLL) {
-            uint4 v[ROW_UNROLL];
-            uint32_t dst[ROW_UNROLL];
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u) {
-                const int i = i0 + u * ROW_NT;
-                v[u] = zero;
-                dst[u] = 0xFFFFFFFFu;
-                if (i < nb) {
-                    const int g = i % cgroups, n = (i / cgroups) % BN, tap = i / (cgroups * BN);
-                    const int c = c_base + 8 * g;
-                    const int slice = tap * (ROW_CC / 16) + (g >> 1);
-                    dst[u] = (uint32_t)(slice * BN * 32) + tile_off(n, 8 * (g & 1), BN);
-                    if (n0 + n < a.Nout && c < a.Cs)
-                        v[u] = *reinterpret_cast<const uint4*>(a.w + ((size_t)(n0 + n) * 9 + tap) * a.Cs + c);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < ROW_UNROLL; ++u)
-                if (dst[u] != 0xFFFFFFFFu) *reinterpret_cast<uint4*>(Bs + dst[u]) = v[u];
-        }
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+        ok = ok && tfp::wait_bounded(&wbar, phase & 1u, kPolls);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {

@@ -118,8 +118,15 @@ def test_training_and_prediction_beat_persistence():
     start = {(b, f): truth.read_field(b, f) for b in range(len(zetas)) for f in fields}
     start_E = {b: truth.energy_spectrum(b)[0] for b in range(len(zetas))}
     truth.step(horizon)
-    for b in range(len(zetas)):
+    sur.predict(pred, 0)                        # one instance alone ...
+    for b in range(1, len(zetas)):              # ... the rest one by one
         sur.predict(pred, b)
+    # the same predictions as one batch of all instances
+    batch = state(11)
+    sur.predict(batch, -1)
+    for b in range(len(zetas)):
+        for f in (B.FIELD_PHI, B.FIELD_QXY, B.FIELD_U1Y):
+            assert np.array_equal(batch.read_field(b, f), pred.read_field(b, f)), (b, f)
     ratios = np.zeros((len(zetas), len(fields) + 1))
     for b in range(len(zetas)):
         for j, f in enumerate(fields):
