@@ -149,6 +149,18 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.at_end = False
+        if not self.lines:
+            # the timed region was shorter than the sampler's start-up: one query
+            # right at its end, while the clocks still reflect the load
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=10).stdout
+                self.lines = [ln.strip() for ln in out.splitlines() if ln.strip()]
+                self.at_end = True
+            except (OSError, subprocess.SubprocessError):
+                pass
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
@@ -166,6 +178,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "when": "at the end of the timed region" if self.at_end else "during the timed region",
                 "samples": len(sm)}
 
 

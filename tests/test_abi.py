@@ -108,3 +108,28 @@ def test_create_rejects_bad_workspace_before_any_device_call(lib):
     assert ctx.value is None
     assert lib.tf_destroy(None) == B.TF_ERR_ARG
     assert lib.tf_last_error(None) == b"null context"
+
+
+def test_surrogate_config_host_checks(lib):
+    """tf_sur_workspace_bytes validates the configuration on the host."""
+    def nbytes(**kw):
+        c = dict(levels=3, base_channels=16, nx=64, ny=64, max_batch=2, max_pairs=4, horizon=10)
+        c.update(kw)
+        cfg = B.TFSurConfig(*[c[k] for k in ("levels", "base_channels", "nx", "ny", "max_batch",
+                                              "max_pairs", "horizon")])
+        return lib.tf_sur_workspace_bytes(ctypes.byref(cfg))
+    base = nbytes()
+    assert base > 0 and base % 256 == 0
+    assert nbytes(max_pairs=8) > base                   # dataset grows with the pairs
+    assert nbytes(levels=0) == 0 and nbytes(levels=6) == 0
+    assert nbytes(base_channels=24) == 0                # 16, 32 or 64
+    assert nbytes(nx=48) == 0                           # multiple of 8 * 2^(levels-1) = 32
+    assert nbytes(max_batch=0) == 0 and nbytes(horizon=0) == 0
+    assert lib.tf_sur_workspace_bytes(None) == 0
+
+
+def test_ensemble_workspace_host_checks(lib):
+    assert lib.tf_ensemble_workspace_bytes(0) == 0
+    assert lib.tf_ensemble_workspace_bytes(65) == 0
+    n1, n64 = lib.tf_ensemble_workspace_bytes(1), lib.tf_ensemble_workspace_bytes(64)
+    assert 0 < n1 < n64 and n1 % 256 == 0
