@@ -318,7 +318,7 @@ int64_t tf_ensemble_launches(const tf_ensemble* ens);
  * surrogate of the coupled step: from (phi, Q_xx, Q_xy, u1, u2) at time t of
  * one instance (plus its activity zeta as a constant input plane) it predicts
  * the fields at t + horizon, trained on pairs the solver itself produces,
- * with the plain method as the judge of its error (observables above).
+ * with the plain method as the reference for its error (observables above).
  *
  * Network (NHWC activations in BF16, FP32 master weights and accumulation):
  * `levels` U-Net levels with C_l = base_channels * 2^l channels; per level two

@@ -21,7 +21,7 @@ binary fluid mixture", arXiv 2511.00445):
   boundaries, second-order central differences for phi and Q, five
   finite-difference sub-steps per lattice step.
 
-Readings where the paper is silent or ambiguous (each is listed in the design doc):
+Readings where the paper is silent or ambiguous:
 lattice units (dt = dx = 1, tau given directly); A_ch multiplies the double
 well and kappa = eps^2; the LdG coefficients A_Q, B_Q, C_Q are parameters (B_Q
 drops out in 2D) and default to a bulk order S = sqrt(-A_Q/C_Q) = 1/2, the
