@@ -393,6 +393,19 @@ int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, 
  * on the shared stream. */
 int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst);
 
+/* Prediction judged by the plain method: instance `inst` of `ctx` is copied
+ * into the same instance of `shadow` (a context of the same shape and
+ * storage on the same stream), `shadow` advances every instance by
+ * `horizon` plain steps, and `ctx`'s instance is predicted.  The relative
+ * errors of the prediction against the solver, err_L = |L_pred - L| / L (Eq. 27)
+ * and err_E = sum_m |E_pred(m) - E(m)| / sum_m E(m) (Eq. 22), decide: above
+ * max_err_L or max_err_E the instance falls back to the solver's state.
+ * out = [err_L, err_E, L_pred, L]; *fell_back = 1 after a fallback, else 0.
+ * The judge costs a plain run of `horizon` steps: call it for a sample of the
+ * predictions.  Synchronous. */
+int tf_sur_judged_predict(tf_surrogate* s, tf_ctx* ctx, tf_ctx* shadow, int inst,
+                          double max_err_L, double max_err_E, double out[4], int* fell_back);
+
 /* ---- fixed-footprint entry point ------------------------------------- */
 /* The paper has no counterpart to this call; it exists for integration.
  *

@@ -52,7 +52,7 @@ EXPORTS = [
     "tf_sur_workspace_bytes", "tf_sur_create", "tf_sur_destroy", "tf_sur_last_error",
     "tf_sur_num_params", "tf_sur_init_weights", "tf_sur_set_weights", "tf_sur_get_weights",
     "tf_sur_forward", "tf_sur_gradients", "tf_sur_add_pair", "tf_sur_fit_normalisation",
-    "tf_sur_train", "tf_sur_predict", "tf_phi_stats_noalloc",
+    "tf_sur_train", "tf_sur_predict", "tf_sur_judged_predict", "tf_phi_stats_noalloc",
 ]
 SUR_IN, SUR_OUT = 8, 7
 
@@ -189,6 +189,7 @@ def load_library() -> ctypes.CDLL:
         "tf_sur_fit_normalisation": (i, [vp, i]),
         "tf_sur_train": (i, [vp, i, i, i, d, ctypes.c_uint64, dp]),
         "tf_sur_predict": (i, [vp, vp, i]),
+        "tf_sur_judged_predict": (i, [vp, vp, vp, i, d, d, dp, ctypes.POINTER(i)]),
         "tf_phi_stats_noalloc": (i, [vp, ctypes.c_longlong, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -515,3 +516,11 @@ class Surrogate:
 
     def predict(self, solver: TwoFluid, inst: int):
         self._check(self.lib.tf_sur_predict(self.h, solver.ctx, inst))
+
+    def judged_predict(self, solver: TwoFluid, shadow: TwoFluid, inst: int, max_err_L: float,
+                       max_err_E: float):
+        out = np.zeros(4)
+        back = ctypes.c_int()
+        self._check(self.lib.tf_sur_judged_predict(self.h, solver.ctx, shadow.ctx, inst, max_err_L,
+                                                   max_err_E, _dptr(out), ctypes.byref(back)))
+        return out, bool(back.value)

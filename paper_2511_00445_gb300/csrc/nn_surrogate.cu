@@ -1003,4 +1003,62 @@ int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst) {
     return TF_OK;
 }
 
+// Instance `inst` of the raw state (populations, phi, Q) from src to dst.
+static int copy_instance(tf_surrogate* s, const tf_ctx* src, tf_ctx* dst, int inst) {
+    const long long N = src->N;
+    const size_t pb = tf_pop_bytes(src->storage);
+    SCK(s, cudaMemcpyAsync(static_cast<char*>(dst->d.f[dst->fcur]) + 18 * inst * N * pb,
+                           static_cast<const char*>(src->d.f[src->fcur]) + 18 * inst * N * pb,
+                           18 * N * pb, cudaMemcpyDeviceToDevice, s->stream));
+    SCK(s, cudaMemcpyAsync(dst->d.phi[dst->pcur] + inst * N, src->d.phi[src->pcur] + inst * N,
+                           N * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
+    SCK(s, cudaMemcpyAsync(dst->d.Q[dst->pcur] + 2 * inst * N, src->d.Q[src->pcur] + 2 * inst * N,
+                           2 * N * sizeof(float), cudaMemcpyDeviceToDevice, s->stream));
+    return TF_OK;
+}
+
+int tf_sur_judged_predict(tf_surrogate* s, tf_ctx* ctx, tf_ctx* shadow, int inst, double max_err_L,
+                          double max_err_E, double out[4], int* fell_back) {
+    if (!s || !ctx || !shadow) return TF_ERR_ARG;
+    if (shadow == ctx || shadow->nx != ctx->nx || shadow->ny != ctx->ny || shadow->batch != ctx->batch ||
+        shadow->storage != ctx->storage || shadow->stream != ctx->stream || inst < 0 || inst >= ctx->batch)
+        return sfail(s, TF_ERR_ARG, "shadow must match the context's shape, storage and stream");
+    SCK(s, tf_launch_flush(ctx));
+    SCK(s, tf_launch_flush(shadow));
+    int rc = copy_instance(s, ctx, shadow, inst);
+    if (rc != TF_OK) return rc;
+    if ((rc = tf_step(shadow, s->cfg.horizon)) != TF_OK) return sfail(s, rc, tf_last_error(shadow));
+    if ((rc = tf_sur_predict(s, ctx, inst)) != TF_OK) return rc;
+    const int ns = tf_n_shell(ctx);
+    std::vector<double> Ep(ns), Es(ns);
+    double Lp = 0.0, Ls = 0.0, tp = 0.0, ts = 0.0;
+    if ((rc = tf_length_scale(ctx, inst, &Lp)) != TF_OK ||
+        (rc = tf_energy_spectrum(ctx, inst, Ep.data(), ns, &tp)) != TF_OK)
+        return sfail(s, rc, tf_last_error(ctx));
+    if ((rc = tf_length_scale(shadow, inst, &Ls)) != TF_OK ||
+        (rc = tf_energy_spectrum(shadow, inst, Es.data(), ns, &ts)) != TF_OK)
+        return sfail(s, rc, tf_last_error(shadow));
+    double num = 0.0, den = 0.0;
+    for (int m = 0; m < ns; ++m) {
+        num += std::fabs(Ep[m] - Es[m]);
+        den += Es[m];
+    }
+    const double eL = Ls > 0.0 ? std::fabs(Lp - Ls) / Ls : 0.0;
+    const double eE = den > 0.0 ? num / den : 0.0;
+    const bool back = !(eL <= max_err_L && eE <= max_err_E);
+    if (back) {
+        SCK(s, tf_launch_flush(shadow));
+        if ((rc = copy_instance(s, shadow, ctx, inst)) != TF_OK) return rc;
+    }
+    SCK(s, cudaStreamSynchronize(s->stream));
+    if (out) {
+        out[0] = eL;
+        out[1] = eE;
+        out[2] = Lp;
+        out[3] = Ls;
+    }
+    if (fell_back) *fell_back = back ? 1 : 0;
+    return TF_OK;
+}
+
 }  // extern "C"

@@ -140,3 +140,16 @@ def test_training_and_prediction_beat_persistence():
     assert np.all(mean[:-1] < 0.9), mean
     assert mean[-1] < 0.95, mean
     assert pred.step_count() == 600             # predictions do not step the solver
+
+    # the plain method as judge: a generous threshold keeps the prediction; a
+    # zero threshold falls back to the solver's own result for that instance
+    shadow = state(99)
+    keep = state(11)
+    errs, back = sur.judged_predict(keep, shadow, 0, 1e9, 1e9)
+    assert not back and errs[0] >= 0 and errs[1] >= 0 and errs[3] > 0
+    assert np.array_equal(keep.read_field(0, B.FIELD_PHI), pred.read_field(0, B.FIELD_PHI))
+    fall = state(11)
+    errs, back = sur.judged_predict(fall, shadow, 2, 0.0, 0.0)
+    assert back
+    for f in (B.FIELD_PHI, B.FIELD_QXX, B.FIELD_U2Y, B.FIELD_F1 + 3):
+        assert np.array_equal(fall.read_field(2, f), truth.read_field(2, f)), f
