@@ -38,8 +38,10 @@ constexpr int NS_FUSED = 5;    // sub-steps handled by the fused kernel (Sec. II
 constexpr uint32_t kWaitPolls = 1u << 22;
 
 __device__ __forceinline__ int wrapc(int v, int n) {
-    // v may lie several periods outside [0, n) for tiny grids
-    v %= n;
+    if ((unsigned)v < (unsigned)n) return v;
+    if (v < 0 && v >= -n) return v + n;
+    if (v >= n && v < 2 * n) return v - n;
+    v %= n;     // several periods outside [0, n): tiny grids only
     return v < 0 ? v + n : v;
 }
 
@@ -69,8 +71,9 @@ enum { P_PHI = 0, P_MU, P_U1X, P_U1Y, P_U2X, P_U2Y, P_QA, P_QB };
 // paired FP32 arithmetic).  A warp walks its band top to bottom keeping rows
 // y-1, y, y+1 in registers (roles rotate by renaming), so y-neighbours come
 // from registers and x-neighbours from warp shuffles.  Rows are written back
-// in place after a warp sync; the rows just above and below a band belong to
-// other warps and are captured in registers before a barrier.
+// in place (a lane touches only its own columns in shared memory); the rows
+// just above and below a band belong to other warps and are captured in
+// registers before a barrier.
 template <int RH, int W, int A, int TY>
 __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
     using namespace tfq;
@@ -101,7 +104,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
                 nbr2(pcur, l, r);
                 const f2 lap = F2(m4, pcur, A2(A2(l, r), A2(pp, pn)));
                 const f2 poly = F2(pcur, F2(pcur, F2(pcur, mu3, mu2), mu1), mu0);
-                st_pair(mu + (o + y) * W + pc.c0, F2(kap, lap, poly), pc.in0, pc.in1);
+                st_pair(mu + (o + y) * W + pc.c0, F2(kap, lap, poly), pc.st);
                 pp = pcur;
                 pcur = pn;
             }
@@ -114,11 +117,26 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
     const PairCols pc(o, w, lane);
     const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
     const int oq = RH - rq, wq = TX + 2 * rq;     // Q neighbourhood (shared coordinates)
-    // (pc.in0 / in1 are false on surplus lanes; the Q neighbourhood lies inside)
-    const bool q0 = pc.in0 && pc.c0 >= oq && pc.c0 < oq + wq;
-    const bool q1 = pc.in1 && pc.c0 + 1 >= oq && pc.c0 + 1 < oq + wq;
-    const f2 dt = S2(P.dt_fd), Mm = S2(P.M), K2 = S2(P.K), lam = S2(P.lam), GQ = S2(P.GammaQ);
-    const f2 AQ = S2(-P.A_Q), CQ = S2(-P.C_Q), four = S2(4.f);
+    const bool qs = pc.meets(oq, wq);
+    // Forward Euler with dt and the factors 1/2 of the central differences
+    // folded into the coefficients (Eq. 1 and Eqs. 11-12):
+    //   phi' = phi + (dt/2) [2M lap(mu) - (J_x(+x) - J_x(-x) + J_y(+y) - J_y(-y))]
+    //   a'   = a + [c a + dt Gamma K lap(a) + (dt lam / 4) E1 + (dt/2) O b - (dt/2) u1.D a]
+    //   b'   = b + [c b + dt Gamma K lap(b) + (dt lam / 4) EX - (dt/2) O a - (dt/2) u1.D b]
+    // with D the undivided central differences (D_x v = v(+x) - v(-x)) and
+    //   E1 = D_x u_x - D_y u_y, EX = D_y u_x + D_x u_y, O = D_y u_x - D_x u_y,
+    //   c  = -dt Gamma (A_Q + C_Q q^2) + dt lam ((D_x u_x + D_y u_y)/2 - (a E1 + b EX)).
+    // The bracket is dt [Gamma H + S - u1.grad Q] with H and S as in the
+    // device helpers: tr E = (D_x u_x + D_y u_y)/2, E0 = (E1, EX)/4,
+    // 4 (Q:E0)/2 = a E1 + b EX, and the rotation part om (b, -a), om = O/2.
+    // Each field takes its increment in one final addition: a constant such as
+    // 1 - dt Gamma A_Q, rounded once and applied to the field every sub-step,
+    // would bias the field itself, not just its increment.
+    const float dt = P.dt_fd, dG = __fmul_rn(dt, P.GammaQ), hdt = 0.5f * dt;
+    const f2 M2x = S2(2.f * P.M), nhdt = S2(-hdt), hdt2 = S2(hdt);
+    const f2 cGA = S2(-__fmul_rn(dG, P.A_Q)), cGC = S2(-__fmul_rn(dG, P.C_Q));
+    const f2 cGK = S2(__fmul_rn(dG, P.K)), lamd = S2(__fmul_rn(dt, P.lam));
+    const f2 lamq = S2(0.25f * __fmul_rn(dt, P.lam));
     auto flux = [&](f2 pv, f2 v1, f2 v2) { return M2(pv, F2(pv, B2(v1, v2), v2)); };
     struct Row {
         f2 mu, ax, ay, qa, qb, jy, ph, jx;
@@ -147,13 +165,16 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
     auto do_row = [&](int y, const Row& Pr, const Row& Cr, const Row& Nr) {
         f2 l, r;
         nbr2(Cr.jx, l, r);
-        const f2 divJ = M2(half, A2(B2(r, l), B2(Nr.jy, Pr.jy)));
+        const f2 dJ = A2(B2(r, l), B2(Nr.jy, Pr.jy));
         nbr2(Cr.mu, l, r);
         const f2 lapmu = F2(m4, Cr.mu, A2(A2(l, r), A2(Nr.mu, Pr.mu)));
-        const f2 nph = F2(dt, F2(Mm, lapmu, make_float2(-divJ.x, -divJ.y)), Cr.ph);
+        const f2 nph = F2(hdt2, F2(M2x, lapmu, N2(dJ)), Cr.ph);
         const int row = o + y;
         const bool qrow = row >= oq && row < oq + TY + 2 * rq;
-        f2 nqa = Cr.qa, nqb = Cr.qb;
+        // A lane reads and writes only its own columns (x-neighbours come by
+        // shuffle), so row y is overwritten in place without a warp barrier.
+        const int c = row * W + pc.c0;
+        st_pair(phi + c, nph, pc.st);
         if (qrow) {
             f2 al, ar, bl, br, uxl, uxr, uyl, uyr;
             nbr2(Cr.qa, al, ar);
@@ -163,33 +184,20 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
             const f2 a = Cr.qa, bq = Cr.qb;
             const f2 lapa = F2(m4, a, A2(A2(al, ar), A2(Nr.qa, Pr.qa)));
             const f2 lapb = F2(m4, bq, A2(A2(bl, br), A2(Nr.qb, Pr.qb)));
-            const f2 cqf = F2(CQ, F2(a, a, M2(bq, bq)), AQ);        // -(A_Q + C_Q q^2)
-            const f2 hh = F2(cqf, a, M2(K2, lapa));
-            const f2 g = F2(cqf, bq, M2(K2, lapb));
-            const f2 Wxx = M2(half, B2(uxr, uxl)), Wxy = M2(half, B2(Nr.ax, Pr.ax));
-            const f2 Wyx = M2(half, B2(uyr, uyl)), Wyy = M2(half, B2(Nr.ay, Pr.ay));
-            const f2 trE = A2(Wxx, Wyy);
-            const f2 e1 = M2(half, B2(Wxx, Wyy));
-            const f2 exy = M2(half, A2(Wxy, Wyx));
-            const f2 om = B2(Wxy, Wyx);
-            const f2 QE2 = M2(four, F2(a, e1, M2(bq, exy)));
-            // -(u1 . grad) a and b, central differences
-            const f2 adv_a = M2(half, F2(Cr.ax, B2(ar, al), M2(Cr.ay, B2(Nr.qa, Pr.qa))));
-            const f2 adv_b = M2(half, F2(Cr.ax, B2(br, bl), M2(Cr.ay, B2(Nr.qb, Pr.qb))));
-            // lam (trE a + e1 - QE2 a) + om b + Gamma h - adv
-            const f2 sa = F2(lam, A2(B2(M2(trE, a), M2(QE2, a)), e1), M2(om, bq));
-            const f2 sb = F2(lam, A2(B2(M2(trE, bq), M2(QE2, bq)), exy), N2(M2(om, a)));
-            const f2 ra = B2(F2(GQ, hh, sa), adv_a);
-            const f2 rb = B2(F2(GQ, g, sb), adv_b);
-            nqa = F2(dt, ra, a);
-            nqb = F2(dt, rb, bq);
-        }
-        __syncwarp();   // every lane has read row y before it is overwritten
-        const int c = row * W + pc.c0;
-        st_pair(phi + c, nph, pc.in0, pc.in1);
-        if (qrow) {
-            st_pair(qa + c, nqa, q0, q1);
-            st_pair(qb + c, nqb, q0, q1);
+            const f2 cg = F2(cGC, F2(a, a, M2(bq, bq)), cGA);      // -dt Gamma (A_Q + C_Q q^2)
+            const f2 Dxx = B2(uxr, uxl), Dyy = B2(Nr.ay, Pr.ay);
+            const f2 Dxy = B2(Nr.ax, Pr.ax), Dyx = B2(uyr, uyl);
+            const f2 E1 = B2(Dxx, Dyy), EX = A2(Dxy, Dyx);
+            const f2 t1 = F2(half, A2(Dxx, Dyy), N2(F2(a, E1, M2(bq, EX))));
+            const f2 cc = F2(lamd, t1, cg);
+            const f2 hO = M2(hdt2, B2(Dxy, Dyx));
+            const f2 nux = M2(nhdt, Cr.ax), nuy = M2(nhdt, Cr.ay);
+            const f2 nqa = A2(a, F2(cc, a, F2(cGK, lapa, F2(lamq, E1, F2(hO, bq,
+                                  F2(nux, B2(ar, al), M2(nuy, B2(Nr.qa, Pr.qa))))))));
+            const f2 nqb = A2(bq, F2(cc, bq, F2(cGK, lapb, F2(lamq, EX, F2(N2(hO), a,
+                                  F2(nux, B2(br, bl), M2(nuy, B2(Nr.qb, Pr.qb))))))));
+            st_pair(qa + c, nqa, qs);
+            st_pair(qb + c, nqb, qs);
         }
     };
     if (y0 < y1) {
@@ -374,11 +382,11 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
                     nbr2(bc, bl, br);
                     const PairStress r =
                         stress2(P, dc, dl, dr, dn, dp, ac, al, ar, an, ap, bc, bl, br, bn, bp);
-                    st_pair(tf_smem + P_MU * A + cc, r.mu, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U1X * A + cc, r.sxx, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U1Y * A + cc, r.sxy, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U2X * A + cc, r.syx, pc.in0, pc.in1);
-                    st_pair(tf_smem + P_U2Y * A + cc, r.syy, pc.in0, pc.in1);
+                    st_pair(tf_smem + P_MU * A + cc, r.mu, pc.st);
+                    st_pair(tf_smem + P_U1X * A + cc, r.sxx, pc.st);
+                    st_pair(tf_smem + P_U1Y * A + cc, r.sxy, pc.st);
+                    st_pair(tf_smem + P_U2X * A + cc, r.syx, pc.st);
+                    st_pair(tf_smem + P_U2Y * A + cc, r.syy, pc.st);
                     dp = dc;
                     dc = dn;
                     ap = ac;

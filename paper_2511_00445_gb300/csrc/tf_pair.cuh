@@ -42,27 +42,28 @@ __device__ __forceinline__ void nbr2(f2 v, f2& l, f2& r) {
 // column o and span w: lanes cover pairs from the one holding column o - 1 to
 // the one holding column o + w (the one-column halo).  Surplus lanes repeat
 // the last pair so that their loads stay in bounds, but their shuffled
-// neighbours are not the pair's true neighbours: they never write (in0, in1
-// false).  in0 / in1: the pair's columns inside the neighbourhood.
+// neighbours are not the pair's true neighbours: they never write.
+// st: the lane owns its pair and the pair meets the neighbourhood.  Where o
+// or o + w is odd, the edge pair also covers one column just outside; the
+// whole pair is stored, and that outside column (one site beyond the radius
+// the next stage reads) takes a value nobody reads.
 struct PairCols {
     int c0;
-    bool in0, in1;
+    bool st;
     __device__ __forceinline__ PairCols(int o, int w, int lane) {
         const int pb = (o - 1) >> 1, pl = (o + w) >> 1;
         const bool own = pb + lane <= pl;
         c0 = 2 * min(pb + lane, pl);
-        in0 = own && c0 >= o && c0 < o + w;
-        in1 = own && c0 + 1 >= o && c0 + 1 < o + w;
+        st = own && c0 + 1 >= o && c0 < o + w;
+    }
+    // st for a narrower neighbourhood [oq, oq + wq) inside this one
+    __device__ __forceinline__ bool meets(int oq, int wq) const {
+        return st && c0 + 1 >= oq && c0 < oq + wq;
     }
 };
 
-__device__ __forceinline__ void st_pair(float* p, f2 v, bool in0, bool in1) {
-    if (in0 && in1) {
-        *reinterpret_cast<float2*>(p) = v;
-    } else {
-        if (in0) p[0] = v.x;
-        if (in1) p[1] = v.y;
-    }
+__device__ __forceinline__ void st_pair(float* p, f2 v, bool st) {
+    if (st) *reinterpret_cast<float2*>(p) = v;
 }
 
 // Chemical potential and fluid-1 stress (elastic + active) for a column pair,
@@ -145,34 +146,36 @@ __device__ __forceinline__ void lbm_site2(const DevParams& P, float d, f2 dlr_x 
     u2 = M2(F2(S2(ad), r1, M2(S2(__fadd_rn(rho.x, ad)), r2)), S2(inv));
     const f2 du = M2(S2(gd), B2(u2, u1));
     const f2 F1 = A2(G1, du), Fv2 = B2(G2, du);
-    // collision, fluids paired: components as (fluid 1, fluid 2)
+    // collision, fluids paired: components as (fluid 1, fluid 2).
+    // d* = (1 - omega) d + omega d^eq + S_i with the BGK + Guo terms split into
+    // the parts even and odd in c_i, so that a direction and its opposite
+    // (c.u and c.F change sign) share every product:
+    //   omega d^eq + S = w [omega Z + G (9 (c.u)(c.F) - 3 u.F)]
+    //                  +/- 3 w [omega rho (c.u) + G (c.F)],
+    //   Z = drho + rho (4.5 (c.u)^2 - 1.5 u^2),  G = 1 - omega/2.
     const f2 UX = P2(u1.x, u2.x), UY = P2(u1.y, u2.y);
     const f2 FX = P2(F1.x, Fv2.x), FY = P2(F1.y, Fv2.y);
     const f2 OM = P2(P.omega1, P.omega2), GU = P2(P.guo1, P.guo2);
-    const f2 usq15 = M2(S2(1.5f), F2(UX, UX, M2(UY, UY)));
-    const f2 uF3 = M2(S2(3.f), F2(UX, FX, M2(UY, FY)));
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int cx = d2q9_cx(i), cy = d2q9_cy(i);
-        f2 cu, cF;
-        if (cx == 0 && cy == 0) {
-            cu = S2(0.f);
-            cF = S2(0.f);
-        } else if (cy == 0) {
-            cu = cx > 0 ? UX : N2(UX);
-            cF = cx > 0 ? FX : N2(FX);
-        } else if (cx == 0) {
-            cu = cy > 0 ? UY : N2(UY);
-            cF = cy > 0 ? FY : N2(FY);
-        } else {
-            cu = cx > 0 ? (cy > 0 ? A2(UX, UY) : B2(UX, UY)) : (cy > 0 ? B2(UY, UX) : N2(A2(UX, UY)));
-            cF = cx > 0 ? (cy > 0 ? A2(FX, FY) : B2(FX, FY)) : (cy > 0 ? B2(FY, FX) : N2(A2(FX, FY)));
-        }
-        const f2 w = S2(d2q9_w(i));
-        const f2 deq = M2(w, F2(rho, B2(M2(cu, F2(S2(4.5f), cu, S2(3.f))), usq15), dr));
-        const f2 src = M2(M2(GU, w), F2(S2(9.f), M2(cu, cF), B2(M2(S2(3.f), cF), uF3)));
-        f[i] = A2(F2(N2(OM), B2(f[i], deq), f[i]), src);
+    const f2 omc = P2(__fsub_rn(1.f, P.omega1), __fsub_rn(1.f, P.omega2));
+    const f2 nusq = M2(S2(-1.5f), F2(UX, UX, M2(UY, UY)));     // -1.5 u^2
+    const f2 nuF3 = M2(S2(-3.f), F2(UX, FX, M2(UY, FY)));      // -3 u.F
+    const f2 orho = M2(OM, rho);
+    {
+        const f2 Z = F2(rho, nusq, dr);
+        f[0] = F2(omc, f[0], M2(S2(d2q9_w(0)), F2(OM, Z, M2(GU, nuF3))));
     }
+    auto pair = [&](int i, int j, f2 cu, f2 cF) {
+        const float w = d2q9_w(i);
+        const f2 Z = F2(rho, F2(M2(S2(4.5f), cu), cu, nusq), dr);
+        const f2 ev = M2(S2(w), F2(OM, Z, M2(GU, F2(S2(9.f), M2(cu, cF), nuF3))));
+        const f2 od = M2(S2(3.f * w), F2(orho, cu, M2(GU, cF)));
+        f[i] = F2(omc, f[i], A2(ev, od));
+        f[j] = F2(omc, f[j], B2(ev, od));
+    };
+    pair(1, 3, UX, FX);                         // c = (+1, 0) and (-1, 0)
+    pair(2, 4, UY, FY);                         // (0, +1) and (0, -1)
+    pair(5, 7, A2(UX, UY), A2(FX, FY));         // (+1, +1) and (-1, -1)
+    pair(6, 8, B2(UY, UX), B2(FY, FX));         // (-1, +1) and (+1, -1)
 }
 
 }  // namespace tfq
