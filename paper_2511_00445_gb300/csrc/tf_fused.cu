@@ -7,6 +7,8 @@
 namespace {
 
 // One tile per CTA: tile (blockIdx.x, blockIdx.y) of instance blockIdx.z.
+// The ny rows are cut into gridDim.y tile rows of floor or ceil(ny / gridDim.y)
+// rows each (at most TY_DEFAULT; the host picks gridDim.y).
 template <bool DO_FD, bool DO_LBM, class S>
 __global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
     __shared__ __align__(8) uint64_t bar;
@@ -15,8 +17,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
         tfp::fence_mbar_init();
     }
     __syncthreads();
-    fused_tile<DO_FD, DO_LBM, S, TY_DEFAULT>(a, blockIdx.z, blockIdx.x * TX,
-                                             blockIdx.y * TY_DEFAULT, &bar, 0);
+    const int y0 = (int)((long long)blockIdx.y * a.ny / gridDim.y);
+    const int y1 = (int)((long long)(blockIdx.y + 1) * a.ny / gridDim.y);
+    fused_tile<DO_FD, DO_LBM, S, TY_DEFAULT>(a, blockIdx.z, blockIdx.x * TX, y0, y1 - y0, &bar, 0);
 }
 
 template <bool DO_FD, bool DO_LBM, class S>
@@ -39,7 +42,7 @@ void launch_as(tf_ctx* ctx) {
     using G = Geo<DO_FD, DO_LBM, TY_DEFAULT>;
     using T = typename S::T;
     DevBuffers& d = ctx->d;
-    const dim3 grid((ctx->nx + TX - 1) / TX, (ctx->ny + TY_DEFAULT - 1) / TY_DEFAULT, ctx->batch);
+    const dim3 grid((ctx->nx + TX - 1) / TX, ctx->tile_rows, ctx->batch);
     const int fc = ctx->fcur, pc = ctx->pcur, uc = ctx->ucur;
     const TileArgs<S> a{static_cast<const T*>(d.f[fc]), static_cast<T*>(d.f[fc ^ 1]),
                         d.phi[pc], d.phi[pc ^ 1], d.Q[pc], d.Q[pc ^ 1], d.u[uc], d.u[uc ^ 1],
@@ -75,7 +78,38 @@ cudaError_t tf_configure_fused_kernels() {
     return e;
 }
 
+// Tile rows of the per-context launches.  When the tiles of TY_DEFAULT rows
+// fit in one wave of resident CTAs, the rows are cut finer (down to tiles of
+// kMinTileRows rows) so that the wave is as full as possible: at one wave the
+// step takes as long as one SM's tiles, and shorter tiles shorten that.
+// Otherwise the fewest tile rows of at most TY_DEFAULT rows are used.
+constexpr int kMinTileRows = 8;
+
+int tile_rows_for(int nx, int ny, int batch, long long slots) {
+    const long long per_row = (long long)((nx + TX - 1) / TX) * batch;   // tiles per tile row
+    const int need = (ny + TY_DEFAULT - 1) / TY_DEFAULT;
+    const long long fit = slots / per_row;          // tile rows that one wave holds
+    if (fit <= need) return need;
+    const int most = ny / kMinTileRows > need ? ny / kMinTileRows : need;
+    return (int)(fit < most ? fit : most);
+}
+
+cudaError_t plan_tile_rows(tf_ctx* ctx) {
+    if (ctx->tile_rows > 0) return cudaSuccess;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_fused<true, true, PopF32>, NT, Geo<true, true, TY_DEFAULT>::SMEM);
+    if (e != cudaSuccess) return e;
+    ctx->tile_rows = tile_rows_for(ctx->nx, ctx->ny, ctx->batch, (long long)sms * per_sm);
+    return cudaSuccess;
+}
+
 cudaError_t tf_fused_steps(tf_ctx* ctx, int64_t n) {
+    cudaError_t pe = plan_tile_rows(ctx);
+    if (pe != cudaSuccess) return pe;
     for (int64_t it = 0; it < n; ++it) {
         cudaError_t e = ctx->fd_pending ? launch<true, true>(ctx) : launch<false, true>(ctx);
         if (e != cudaSuccess) return e;
@@ -87,6 +121,8 @@ cudaError_t tf_fused_steps(tf_ctx* ctx, int64_t n) {
 
 cudaError_t tf_fused_flush(tf_ctx* ctx) {
     if (!ctx->fd_pending) return cudaSuccess;
+    cudaError_t pe = plan_tile_rows(ctx);
+    if (pe != cudaSuccess) return pe;
     cudaError_t e = launch<true, false>(ctx);
     ctx->fd_pending = false;
     return e;

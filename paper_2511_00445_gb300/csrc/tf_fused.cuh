@@ -74,8 +74,8 @@ enum { P_PHI = 0, P_MU, P_U1X, P_U1Y, P_U2X, P_U2Y, P_QA, P_QB };
 // in place (a lane touches only its own columns in shared memory); the rows
 // just above and below a band belong to other warps and are captured in
 // registers before a barrier.
-template <int RH, int W, int A, int TY>
-__device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
+template <int RH, int W, int A>
+__device__ __forceinline__ void fd_substep(const DevParams& P, int th, int rp, int rq) {
     using namespace tfq;
     float* __restrict__ phi = tf_smem + P_PHI * A;
     float* __restrict__ mu = tf_smem + P_MU * A;
@@ -92,7 +92,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
 
     // (a) chemical potential on radius ra = rp + 1 (reads phi on ra + 1)
     {
-        const int ra = rp + 1, w = TX + 2 * ra, h = TY + 2 * ra, o = RH - ra;
+        const int ra = rp + 1, w = TX + 2 * ra, h = th + 2 * ra, o = RH - ra;
         const PairCols pc(o, w, lane);
         const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
         if (y0 < y1) {
@@ -113,7 +113,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
     __syncthreads();
 
     // (b) phi on radius rp, Q on radius rq
-    const int w = TX + 2 * rp, h = TY + 2 * rp, o = RH - rp;
+    const int w = TX + 2 * rp, h = th + 2 * rp, o = RH - rp;
     const PairCols pc(o, w, lane);
     const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
     const int oq = RH - rq, wq = TX + 2 * rq;     // Q neighbourhood (shared coordinates)
@@ -170,7 +170,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int rp, int rq) {
         const f2 lapmu = F2(m4, Cr.mu, A2(A2(l, r), A2(Nr.mu, Pr.mu)));
         const f2 nph = F2(hdt2, F2(M2x, lapmu, N2(dJ)), Cr.ph);
         const int row = o + y;
-        const bool qrow = row >= oq && row < oq + TY + 2 * rq;
+        const bool qrow = row >= oq && row < oq + th + 2 * rq;
         // A lane reads and writes only its own columns (x-neighbours come by
         // shuffle), so row y is overwritten in place without a warp barrier.
         const int c = row * W + pc.c0;
@@ -271,8 +271,10 @@ struct TileArgs {
     int* err;
 };
 
-// One TX x TY tile (origin x0, y0) of instance b: loads, pending sub-steps,
-// LBM, stores.  `bar` is this CTA's initialised mbarrier and `phase` the
+// One tile of TX columns and th <= TY rows (origin x0, y0) of instance b:
+// loads, pending sub-steps, LBM, stores.  Every value a tile stores depends
+// only on the state inside its dependency cone, so results do not depend on
+// how the grid is cut into tiles.  `bar` is this CTA's initialised mbarrier and `phase` the
 // number of tiles the CTA has already loaded with it (the wait parity).  A CTA
 // that processes several tiles must pass through __syncthreads() between
 // them (each thread ends a tile with a generic-to-async proxy fence).
@@ -280,7 +282,7 @@ struct TileArgs {
 // MULTI: the launch runs several steps, so the population source was written
 // by other CTAs earlier in the same launch; it is then read through L2 only.
 template <bool DO_FD, bool DO_LBM, class S, int TY, bool MULTI = false>
-__device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, int y0,
+__device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, int y0, int th,
                                            uint64_t* bar, uint32_t phase) {
     using G = Geo<DO_FD, DO_LBM, TY>;
     constexpr int RH = G::RH, W = G::W, H = G::H, A = G::A;
@@ -310,11 +312,13 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
     auto dst_plane = [&](int pl) -> float* {
         return tf_smem + (pl == 0 ? P_PHI : (pl < 3 ? P_QA + pl - 1 : P_U1X + pl - 3)) * A;
     };
+    const int hr = th + 2 * RH;     // loaded rows (<= H)
     if (bulk) {
         if (threadIdx.x == 0)
-            tfp::mbar_arrive_expect_tx(bar, (uint32_t)(G::NLOAD * A * sizeof(float)));
+            tfp::mbar_arrive_expect_tx(bar, (uint32_t)(G::NLOAD * hr * W * sizeof(float)));
         for (int t = threadIdx.x; t < G::NLOAD * H; t += NT) {
             const int pl = t / H, ly = t - pl * H;
+            if (ly >= hr) continue;
             const int gy = wrapc(y0 - RH + ly, ny);
             bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, W, nx, bar);
         }
@@ -322,6 +326,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             const typename S::T* F = fsrc + 18 * b * N;
             for (int t = threadIdx.x; t < 18 * (TY + 2); t += NT) {
                 const int i = t / (TY + 2), r = t - i * (TY + 2);
+                if (r >= th + 2) continue;
                 prefetch_row(F + (long long)i * N, wrapc(y0 - 1 + r, ny), x0 - PF, TX + 2 * PF, nx);
             }
         }
@@ -334,7 +339,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             return false;
         }
     } else {
-        for (int i = threadIdx.x; i < A; i += NT) {
+        for (int i = threadIdx.x; i < hr * W; i += NT) {
             const int ly = i / W, lx = i - ly * W;
             const long long g = (long long)wrapc(y0 - RH + ly, ny) * nx + wrapc(x0 - RH + lx, nx);
 #pragma unroll
@@ -350,7 +355,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         for (int st = 0; st < NS_FUSED; ++st) {
             const int rp = G::R_END + 2 * (NS_FUSED - 1 - st);
             const int rq = G::R_END + (NS_FUSED - 1 - st);
-            fd_substep<RH, W, A, TY>(P, rp, rq);
+            fd_substep<RH, W, A>(P, th, rp, rq);
         }
     }
 
@@ -364,9 +369,10 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             const float* phi = tf_smem + P_PHI * A;
             const float* qa = tf_smem + P_QA * A;
             const float* qb = tf_smem + P_QB * A;
-            constexpr int o = RH - 1, w = TX + 2, h = TY + 2, NW = NT / 32;
+            constexpr int o = RH - 1, w = TX + 2, NW = NT / 32;
+            const int h = th + 2;
             const PairCols pc(o, w, tx);
-            constexpr int bh = (h + NW - 1) / NW;
+            const int bh = (h + NW - 1) / NW;
             const int y0 = ty * bh, y1 = min(h, y0 + bh);
             if (y0 < y1) {
                 const int col = pc.c0;
@@ -410,7 +416,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         typename S::T* D2 = D1 + 9 * N;
         float* uo = u_out + 4 * b * N;
 #pragma unroll 1
-        for (int r = ty; r < TY; r += NT / 32) {
+        for (int r = ty; r < th; r += NT / 32) {
             const int x = x0 + tx, y = y0 + r;
             if (x >= nx || y >= ny) continue;
             const int c = (RH + r) * W + RH + tx;
@@ -448,7 +454,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         // ---- store phi^{k+1}, Q^{k+1} of the interior
         float* po = phi_out + b * N;
         float* qo = Q_out + 2 * b * N;
-        for (int r = ty; r < TY; r += NT / 32) {
+        for (int r = ty; r < th; r += NT / 32) {
             const int x = x0 + tx, y = y0 + r;
             if (x >= nx || y >= ny) continue;
             const int c = (RH + r) * W + RH + tx;
