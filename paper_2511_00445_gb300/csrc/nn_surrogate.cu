@@ -1,6 +1,7 @@
 // Convolutional surrogate of the coupled step (declared in include/twofluid.h):
 // U-Net forward / backward with tcgen05 GEMMs (nn_tc.cuh), Adam, training
 // pairs captured from solver contexts, and prediction back into a context.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -90,8 +91,65 @@ cudaError_t run_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Row-walking forward convolution (tcg::k_conv_walk): for rows of a multiple
+// of 128 pixels and up to 128 source channels, so that the weights and a
+// ring of at least four source rows fit in shared memory.  The ring depth S
+// and the CTAs per SM are chosen together to keep the most source rows in
+// flight per SM (CTAs x (S - 3)); the rows of each (image, segment, output
+// tile) are then cut into rb blocks so that the grid fills the resident CTA
+// slots once.
+constexpr int kWalkMaxCs = 128;
+constexpr int kWalkDynSmem = 227 * 1024 - 1024;   // per-CTA limit less the static part
+constexpr int kSmemPerSM = 228 * 1024;
+
+cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
+    static bool configured = false;
+    static int sms = 0, regs = 0, static_smem = 0;
+    if (!configured) {
+        int dev = 0;
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tcg::k_conv_walk<tcg::ROW_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWalkDynSmem);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tcg::k_conv_walk<tcg::ROW_BN>);
+        if (e != cudaSuccess) return e;
+        regs = fa.numRegs > 0 ? fa.numRegs : 1;
+        static_smem = (int)fa.sharedSizeBytes;
+        configured = true;
+    }
+    int best_s = 0, best_cta = 0, best_score = -1;
+    for (int S = 4; S <= tcg::WALK_MAX_SLOTS; ++S) {
+        const int smem = tcg::walk_smem_bytes(r.Cs, S);
+        if (smem > kWalkDynSmem) break;
+        int cta = kSmemPerSM / (smem + static_smem + 1024);          // 1 KB reserved per CTA
+        cta = std::min(cta, 65536 / (tcg::ROW_NT * regs));
+        cta = std::min(cta, 2048 / tcg::ROW_NT);
+        cta = std::min(cta, 512 / (2 * tcg::ROW_BN));                // tensor-memory columns
+        const int score = cta * (S - 3);
+        if (cta >= 1 && score >= best_score) {
+            best_score = score;
+            best_s = S;
+            best_cta = cta;
+        }
+    }
+    if (best_s == 0) return cudaErrorInvalidValue;
+    const int segs = r.W / tcg::ROW_T, tiles = (r.Nout + tcg::ROW_BN - 1) / tcg::ROW_BN;
+    const long long units = (long long)r.B * segs * tiles;
+    long long rb = ((long long)sms * best_cta + units - 1) / units;
+    if (rb < 1) rb = 1;
+    if (rb > r.H) rb = r.H;
+    const tcg::ConvWalkArgs a{r.src, r.w, r.bias, r.out, r.B, r.H, r.W, r.Cs, r.Nout, r.relu,
+                              (int)rb, best_s, r.err};
+    const dim3 grid((unsigned)(r.B * segs * rb), (unsigned)tiles);
+    tcg::k_conv_walk<tcg::ROW_BN><<<grid, tcg::ROW_NT, tcg::walk_smem_bytes(r.Cs, best_s), st>>>(a);
+    return cudaGetLastError();
+}
+
 template <bool GRAD>
 cudaError_t conv_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
+    if (!GRAD && a.W % tcg::ROW_T == 0 && a.Cs <= kWalkMaxCs) return run_walk(a, st);
     return run_rows<tcg::ROW_BN, GRAD>(a, st);
 }
 

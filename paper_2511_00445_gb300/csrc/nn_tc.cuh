@@ -59,6 +59,21 @@ __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
+// One tcgen05.mma (kind::f16, cta_group::1) accumulating into tensor memory
+// when acc is nonzero, overwriting it otherwise.
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+// Round two floats to BF16 (nearest even) and pack them, the first in the low half.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (uint32_t it = 0; it < kPolls; ++it) {
         uint32_t done;
@@ -310,20 +325,24 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // Descriptors are linear in their address field (address >> 4, below
+            // 2^14 here): offsets in 16-byte units are added to base descriptors.
+            const uint64_t ad0 = smem_desc(smem_u32(As), HR * 16, 128);
+            const uint64_t bd0 = smem_desc(smem_u32(Bs), BN * 16, 128);
+            const uint32_t idesc = instr_desc(BM, BN);
+            uint32_t acc = ch > 0 ? 1u : 0u;
+#pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
                 // source pixel of output pixel r for this tap: staged row (1 + dy), column r + 1 + dx
                 // (the staging already applied the sign of the row offset)
                 const int dx = sgn * (tap % 3 - 1);
-                const int row0 = (tap / 3) * Tp + 1 + dx;
+                uint64_t ad = ad0 + (uint64_t)((tap / 3) * Tp + 1 + dx);
+                uint64_t bd = bd0 + (uint64_t)((tap * (ROW_CC / 16) * BN * 32) >> 4);
                 for (int s = 0; s < csteps; ++s) {
-                    const uint64_t ad = smem_desc(smem_u32(As) + (2 * s * HR + row0) * 16, HR * 16, 128);
-                    const int slice = tap * (ROW_CC / 16) + s;
-                    const uint64_t bd = smem_desc(smem_u32(Bs) + slice * BN * 32, BN * 16, 128);
-                    const uint32_t acc = (ch > 0 || tap > 0 || s > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tbase),
-                        "l"(ad), "l"(bd), "r"(instr_desc(BM, BN)), "r"(acc));
+                    mma_f16(tbase, ad, bd, idesc, acc);
+                    acc = 1;
+                    ad += 2 * HR;              // next 16-channel step: two group blocks
+                    bd += (BN * 32) >> 4;      // next weight slice
                 }
             }
             asm volatile(
@@ -361,19 +380,22 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
                 for (int j = 0; j < 16; ++j)
                     if (n + j < a.Nout) d[j] += __uint_as_float(r[j]);
             } else {
-                __align__(16) __nv_bfloat16 o[16];
+                float z[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    float z = __uint_as_float(r[j]) + (n + j < a.Nout ? a.bias[n + j] : 0.f);
-                    if (a.relu) z = fmaxf(z, 0.f);
-                    o[j] = __float2bfloat16_rn(z);
+                    z[j] = __uint_as_float(r[j]) + (n + j < a.Nout ? a.bias[n + j] : 0.f);
+                    if (a.relu) z[j] = fmaxf(z[j], 0.f);
                 }
                 __nv_bfloat16* d = a.out + p * a.Nout + n;
                 if (n + 16 <= a.Nout) {
-                    reinterpret_cast<uint4*>(d)[0] = reinterpret_cast<const uint4*>(o)[0];
-                    reinterpret_cast<uint4*>(d)[1] = reinterpret_cast<const uint4*>(o)[1];
+                    reinterpret_cast<uint4*>(d)[0] = make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]),
+                                                                pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]));
+                    reinterpret_cast<uint4*>(d)[1] = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]),
+                                                                pack_bf16(z[12], z[13]), pack_bf16(z[14], z[15]));
                 } else {
-                    for (int j = 0; j < 16 && n + j < a.Nout; ++j) d[j] = o[j];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n + j < a.Nout) d[j] = __float2bfloat16_rn(z[j]);
                 }
             }
         }
@@ -383,6 +405,249 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
                      "r"(TCOLS));
+}
+
+// ---------------------------------------------------------------------------
+// Row-walking 3x3 convolution (forward) for rows of a multiple of 128 pixels.
+//
+// One CTA owns the 128-pixel segment x0 .. x0 + 127 of image b, output
+// channels n0 .. n0 + BN - 1, and a run of consecutive output rows
+// [ya, yb).  It loads the weights of all its source-channel chunks once (one
+// bulk copy of the pre-tiled blocks) and keeps a ring of S (4 .. 8) source
+// rows in shared memory, all source channels, in the staging layout of
+// k_conv_rows (16-byte pixel rows, one 130-row block per 8-channel group).
+// Output row i reads source rows i - 1, i, i + 1; at that point source rows
+// up to i + S - 2 are already on their way (the copies run S - 3 rows ahead of
+// their use), and the epilogue of row i - 1 drains the other of two
+// tensor-memory accumulators while the MMAs of row i run.  Per output row the MMAs are issued in
+// k_conv_rows' order (chunk, tap, 16-channel step), so both kernels
+// accumulate the same products in the same sequence.
+// ---------------------------------------------------------------------------
+struct ConvWalkArgs {
+    const __nv_bfloat16* src;   // NHWC, Cs channels
+    const __nv_bfloat16* w;     // pre-tiled weights, see row_wtile_index
+    const float* bias;
+    __nv_bfloat16* out;         // NHWC BF16, Nout channels
+    int B, H, W, Cs, Nout, relu;
+    int rb;                     // row blocks per (image, segment, output tile)
+    int slots;                  // ring depth S, 4 .. WALK_MAX_SLOTS
+    int* err;
+};
+
+constexpr int WALK_MAX_SLOTS = 8;
+constexpr int WALK_ROWS = ROW_T + 2;    // staged pixel rows per 8-channel group
+
+// 8-channel groups staged per source row (source channels padded to K = 16 steps)
+__host__ __device__ constexpr int walk_groups(int Cs) { return 2 * ((Cs + 15) / 16); }
+
+__host__ __device__ constexpr int walk_smem_bytes(int Cs, int slots) {
+    return ((Cs + ROW_CC - 1) / ROW_CC) * ROW_WTILE + slots * walk_groups(Cs) * WALK_ROWS * 16;
+}
+
+// cp.async.wait_group takes an immediate: wait until at most n (1 .. 5) of
+// this thread's most recent copy groups are still pending.
+__device__ __forceinline__ void cp_async_wait_upto(int n) {
+    switch (n) {
+        case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+        case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+        case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+        case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        default: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
+    static_assert(BN == ROW_BN, "weights are pre-tiled for ROW_BN output channels");
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t wbar, mbar[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nch = (a.Cs + ROW_CC - 1) / ROW_CC, cg = walk_groups(a.Cs), csteps = cg / 2;
+    const uint32_t slot_bytes = (uint32_t)cg * WALK_ROWS * 16;
+    const int S = a.slots;
+    const int g_first = tid % cg, q_first = tid / cg, g_step = ROW_NT % cg, q_step = ROW_NT / cg;
+    unsigned char* Bs = tc_smem;
+    unsigned char* Rs = tc_smem + nch * ROW_WTILE;
+    const int segs = a.W / ROW_T;
+    int u = blockIdx.x;
+    const int blk = u % a.rb;
+    u /= a.rb;
+    const int seg = u % segs, b = u / segs;
+    const int ya = (int)((long long)blk * a.H / a.rb), yb = (int)((long long)(blk + 1) * a.H / a.rb);
+    const int rows = yb - ya, x0 = seg * ROW_T, n0 = blockIdx.y * BN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(2 * BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&wbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tmem_base;
+    if (tid == 0) {
+        const uint32_t wbytes = (uint32_t)nch * ROW_WTILE;
+        tfp::mbar_arrive_expect_tx(&wbar, wbytes);
+        tfp::bulk_g2s(Bs, reinterpret_cast<const unsigned char*>(a.w) + (long long)blockIdx.y * wbytes,
+                      wbytes, &wbar);
+    }
+    // source row j (output-row coordinates: image row ya + j, periodic) into
+    // ring slot (j + S) mod S, by 16-byte asynchronous copies (zero past Cs)
+    auto stage = [&](int j) {
+        int yy = ya + j;
+        yy = yy < 0 ? yy + a.H : (yy >= a.H ? yy - a.H : yy);
+        unsigned char* dst = Rs + (uint32_t)((j + S) % S) * slot_bytes;
+        const __nv_bfloat16* rowp = a.src + (size_t)(b * a.H + yy) * a.W * a.Cs;
+        int g = g_first, q = q_first;       // element i = q * cg + g, stepping by ROW_NT
+        for (int i = tid; i < WALK_ROWS * cg; i += ROW_NT) {
+            const int c = 8 * g;
+            int xx = x0 - 1 + q;
+            xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
+            const bool in = c < a.Cs;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             smem_u32(dst + (g * WALK_ROWS + q) * 16)),
+                         "l"(rowp + (size_t)xx * a.Cs + (in ? c : 0)), "r"(in ? 16 : 0)
+                         : "memory");
+            g += g_step;
+            q += q_step;
+            if (g >= cg) {
+                g -= cg;
+                ++q;
+            }
+        }
+    };
+    // this thread's 16 output channels (BN / 2 = 16: one block per thread)
+    static_assert(BN == 32, "one 16-column block per thread");
+    const int c0 = (warp >> 2) * 16;
+    float bias[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) bias[j] = n0 + c0 + j < a.Nout ? a.bias[n0 + c0 + j] : 0.f;
+    auto epilogue = [&](int i) {
+        const int lane_row = (warp & 3) * 32 + (tid & 31);
+        const size_t p = (size_t)(b * a.H + ya + i) * a.W + x0 + lane_row;
+        if (n0 + c0 < a.Nout) {
+            uint32_t r[16];
+            const uint32_t taddr =
+                tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((i & 1) * BN + c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            const int n = n0 + c0;
+            float z[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                z[j] = __uint_as_float(r[j]) + bias[j];
+                if (a.relu) z[j] = fmaxf(z[j], 0.f);
+            }
+            __nv_bfloat16* d = a.out + p * a.Nout + n;
+            if (n + 16 <= a.Nout) {
+                reinterpret_cast<uint4*>(d)[0] = make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]),
+                                                            pack_bf16(z[4], z[5]), pack_bf16(z[6], z[7]));
+                reinterpret_cast<uint4*>(d)[1] = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]),
+                                                            pack_bf16(z[12], z[13]), pack_bf16(z[14], z[15]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (n + j < a.Nout) d[j] = __float2bfloat16_rn(z[j]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    };
+    // Copy groups: sources -1 .. 1, then one group per source 2 .. S - 3;
+    // iteration i commits the group of source i + S - 2, so the group of
+    // source i + 1 has S - 3 younger groups when row i needs it.
+    const int D = S - 3;
+    stage(-1);
+    stage(0);
+    stage(1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int j = 2; j <= S - 3; ++j) {
+        if (j <= rows) stage(j);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    bool ok = tfp::wait_bounded(&wbar, 0, kPolls);
+    int issued = 0, drained = 0;   // output rows whose MMAs were issued / seen complete
+    for (int i = 0; i < rows; ++i) {
+        if (i >= 1) {
+            ok = ok && mbar_wait(&mbar[(i - 1) & 1], ((i - 1) >> 1) & 1);
+            if (ok) drained = i;
+        }
+        // source i + S - 2 goes into the slot of source i - 2, read by row i - 1 only
+        if (ok && i + S - 2 <= rows) stage(i + S - 2);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        cp_async_wait_upto(D);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // Descriptors are linear in their address field (address >> 4, far
+            // below 2^14 here), so offsets are added to a base descriptor.
+            const uint32_t acc_col = tbase + (uint32_t)((i & 1) * BN);
+            const uint32_t idesc = instr_desc(BM, BN);
+            const int sm1 = (i - 1 + S) % S, s0 = i % S, sp1 = (i + 1) % S;
+            const uint64_t dsl[3] = {smem_desc(smem_u32(Rs) + (uint32_t)sm1 * slot_bytes, WALK_ROWS * 16, 128),
+                                     smem_desc(smem_u32(Rs) + (uint32_t)s0 * slot_bytes, WALK_ROWS * 16, 128),
+                                     smem_desc(smem_u32(Rs) + (uint32_t)sp1 * slot_bytes, WALK_ROWS * 16, 128)};
+            const uint64_t bd0 = smem_desc(smem_u32(Bs), BN * 16, 128);
+            uint32_t acc = 0;
+            for (int ch = 0; ch < nch; ++ch) {
+                const int nst = min(ROW_CC / 16, csteps - ch * (ROW_CC / 16));
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    // A: slot of source row i + dy, K-step gs = ch * 4 + s, pixel column 1 + dx
+                    uint64_t ad = dsl[tap / 3] + (uint64_t)((2 * ch * (ROW_CC / 16) * WALK_ROWS + 1 + tap % 3 - 1));
+                    uint64_t bd = bd0 + (uint64_t)((ch * ROW_WTILE + tap * (ROW_CC / 16) * BN * 32) >> 4);
+                    for (int st = 0; st < nst; ++st) {
+                        mma_f16(acc_col, ad, bd, idesc, acc);
+                        acc = 1;
+                        ad += 2 * WALK_ROWS;        // next 16-channel step: two group blocks
+                        bd += (BN * 32) >> 4;       // next weight slice
+                    }
+                }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&mbar[i & 1])));
+        }
+        issued = i + 1;
+        if (i >= 1) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            epilogue(i - 1);
+        }
+    }
+    if (ok && rows > 0) {
+        ok = mbar_wait(&mbar[(rows - 1) & 1], ((rows - 1) >> 1) & 1);
+        ok = __syncthreads_and(ok) != 0;
+        if (ok) {
+            drained = rows;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            epilogue(rows - 1);
+        }
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(a.err, TF_ERR_TIMEOUT);
+        // let issued MMAs finish (bounded) before their tensor memory is freed
+        for (int i = drained; i < issued; ++i) mbar_wait(&mbar[i & 1], (i >> 1) & 1);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                     "r"(2 * BN));
 }
 
 }  // namespace tcg

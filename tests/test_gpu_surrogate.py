@@ -76,6 +76,25 @@ def test_forward_and_gradients_match_oracle(levels, c0, n):
     assert off == sur.n_params
 
 
+@pytest.mark.parametrize("levels,c0,n,batch", [(2, 32, 128, 2), (2, 32, 256, 1), (1, 16, 256, 1)])
+def test_forward_row_walk_matches_oracle(levels, c0, n, batch):
+    """Rows of 128 and 256 pixels run the row-walking convolution (source rows
+    held in a ring, several output rows per CTA, two 128-pixel segments per
+    row at 256); 16 output channels leave half an output tile empty.  Beside
+    the normwise bar, the largest pointwise error is bounded too, so that a
+    single wrong output row or segment cannot hide in the norm."""
+    rng = np.random.default_rng(10 + levels + n)
+    net = as_fp32_net(OS.init_net(levels, c0, B.SUR_IN, B.SUR_OUT, rng))
+    x = bf16_round(rng.standard_normal((batch, n, n, B.SUR_IN)))
+    sur = B.Surrogate(levels=levels, base_channels=c0, nx=n, ny=n, max_batch=batch, max_pairs=1,
+                      horizon=1)
+    sur.set_weights(flat(net))
+    want, _ = OS.forward(net, x.astype(np.float64))
+    got = sur.forward(x)
+    assert relerr(got, want) <= 3e-2
+    assert np.abs(got - want).max() <= 3e-2 * np.abs(want).max()
+
+
 def _pairs(sur, zetas, seeds, n_per, horizon, burn, nx):
     """Capture (state, state + horizon) pairs of every instance and seed."""
     slot = 0
