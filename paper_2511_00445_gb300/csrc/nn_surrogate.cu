@@ -75,19 +75,34 @@ cudaError_t run_gemm(const Op& op, int splits, cudaStream_t st) {
 }
 
 // Row-segment convolutions (forward and input gradient, tcg::k_conv_rows).
-template <int BN, bool GRAD>
+template <int BN, bool GRAD, int NACC>
 cudaError_t run_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(tcg::k_conv_rows<BN, GRAD>,
+        cudaError_t e = cudaFuncSetAttribute(tcg::k_conv_rows<BN, GRAD, NACC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              tcg::row_smem_bytes<BN>());
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int segs = (a.W + tcg::ROW_T - 1) / tcg::ROW_T;
-    const dim3 grid(segs * a.H * a.B, (a.Nout + BN - 1) / BN);
-    tcg::k_conv_rows<BN, GRAD><<<grid, tcg::ROW_NT, tcg::row_smem_bytes<BN>(), st>>>(a);
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    // the most rows per CTA that still gives every SM a CTA (else one row):
+    // packed rows make each MMA do more useful work, so they win as long as
+    // the grid covers the SMs (measured on the 4 x 256^2 prediction)
+    const int segs = (a.W + tcg::ROW_T - 1) / tcg::ROW_T, tiles = (a.Nout + BN - 1) / BN;
+    const long long want = sms;
+    int R = tcg::row_group(a.W, NACC, GRAD);
+    while (R > 1 && (long long)segs * ((a.H + R - 1) / R) * a.B * tiles < want) --R;
+    tcg::ConvRowArgs r = a;
+    r.rows = R;
+    const dim3 grid(segs * ((a.H + R - 1) / R) * a.B, tiles);
+    tcg::k_conv_rows<BN, GRAD, NACC><<<grid, tcg::ROW_NT, tcg::row_smem_bytes<BN>(), st>>>(r);
     return cudaGetLastError();
 }
 
@@ -147,10 +162,14 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Forward: rows of a multiple of 128 pixels with few source channels walk;
+// rows of at most 64 pixels pack several output rows into two accumulators.
 template <bool GRAD>
 cudaError_t conv_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
-    if (!GRAD && a.W % tcg::ROW_T == 0 && a.Cs <= kWalkMaxCs) return run_walk(a, st);
-    return run_rows<tcg::ROW_BN, GRAD>(a, st);
+    if (GRAD) return run_rows<tcg::ROW_BN, true, 1>(a, st);
+    if (a.W % tcg::ROW_T == 0 && a.Cs <= kWalkMaxCs) return run_walk(a, st);
+    if (a.W <= 64) return run_rows<tcg::ROW_BN, false, 2>(a, st);
+    return run_rows<tcg::ROW_BN, false, 1>(a, st);
 }
 
 // Bytes of one layer's pre-tiled weights (tcg::row_wtile_index).
@@ -302,18 +321,30 @@ __global__ void k_bias_grad(const bf16* __restrict__ dzT, long long P, float* __
     if (threadIdx.x == 0) atomicAdd(db + blockIdx.x, red[0]);
 }
 
-// Head: pred[p][o] = bh[o] + sum_c Wh[o][c] h[p][c] (FP32 weights).
+// Head: pred[p][o] = bh[o] + sum_c Wh[o][c] h[p][c] (FP32 weights, summed in
+// channel order).  One thread per pixel reads its C channels as 16-byte
+// pieces (C a multiple of 8); the weights sit in shared memory (dynamic,
+// (COUT * C + COUT) floats).
 __global__ void k_head(const bf16* __restrict__ h, const float* __restrict__ Wh,
                        const float* __restrict__ bh, float* __restrict__ pred, long long P, int C) {
+    extern __shared__ float head_w[];
+    for (int i = threadIdx.x; i < COUT * C + COUT; i += EB) head_w[i] = i < COUT * C ? Wh[i] : bh[i - COUT * C];
+    __syncthreads();
     const long long p = (long long)blockIdx.x * EB + threadIdx.x;
     if (p >= P) return;
     float acc[COUT];
 #pragma unroll
-    for (int o = 0; o < COUT; ++o) acc[o] = bh[o];
-    for (int c = 0; c < C; ++c) {
-        const float v = __bfloat162float(h[p * C + c]);
+    for (int o = 0; o < COUT; ++o) acc[o] = head_w[COUT * C + o];
+    const uint4* hp = reinterpret_cast<const uint4*>(h + p * C);
+    for (int g = 0; g < C / 8; ++g) {
+        const uint4 v = hp[g];
+        const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) acc[o] += Wh[o * C + c] * v;
+        for (int k = 0; k < 8; ++k) {
+            const float x = __uint_as_float(k & 1 ? w4[k >> 1] & 0xFFFF0000u : w4[k >> 1] << 16);
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) acc[o] = fmaf(head_w[o * C + 8 * g + k], x, acc[o]);
+        }
     }
 #pragma unroll
     for (int o = 0; o < COUT; ++o) pred[p * COUT + o] = acc[o];
@@ -698,8 +729,8 @@ cudaError_t forward_pass(tf_surrogate* s, int B) {
     }
     const Tensor& d0 = s->tensors[s->dec0_t];
     const long long P0 = s->pixels(0, B);
-    k_head<<<blocks(P0), EB, 0, st>>>(s->at<bf16>(d0.act), P + s->head_w, P + s->head_b,
-                                      s->at<float>(s->pred_off), P0, d0.C);
+    k_head<<<blocks(P0), EB, (COUT * d0.C + COUT) * sizeof(float), st>>>(
+        s->at<bf16>(d0.act), P + s->head_w, P + s->head_b, s->at<float>(s->pred_off), P0, d0.C);
     return cudaGetLastError();
 }
 

@@ -214,6 +214,14 @@ __global__ void __launch_bounds__(NTHREADS) k_gemm(const Op op, int chunks_per_s
 //   GRAD = false: out[p][n] = relu?(bias[n] + sum_{tap, c} w[n][tap][c] src[p + d(tap)][c])
 //   GRAD = true : dx[p][n] += sum_{tap, c} w[n][tap][c] src[p - d(tap)][c]
 // (the input gradient with w the transposed weights wt[cin][tap][cout]).
+// Short rows (one segment, T = W < 128) pack several output rows into the
+// MMA tile in the forward direction: R + 2 source rows are staged with pitch
+// Tp = T + 2, output row r takes tile rows r Tp .. r Tp + T - 1 (its two halo
+// positions are discarded), and every tap is still one start-address shift.
+// NACC tensor-memory accumulators extend the tile to NACC x 128 rows (the
+// second accumulator's A operand starts 128 staged rows further), so
+// up to (NACC * 128 - T) / Tp + 1 output rows per CTA (the launcher may pick
+// fewer to keep the grid wide).
 // ---------------------------------------------------------------------------
 struct ConvRowArgs {
     const __nv_bfloat16* src;   // NHWC, Cs channels
@@ -223,6 +231,7 @@ struct ConvRowArgs {
     float* dx;                  // gradient: NHWC FP32, Nout channels (accumulated)
     int B, H, W, Cs, Nout, relu;
     int* err;
+    int rows;                   // output rows per CTA, 1 .. row_group(W, NACC, GRAD) (set by the launcher)
 };
 
 constexpr int ROW_T = 128;      // output pixels per CTA
@@ -255,10 +264,16 @@ __host__ __device__ inline long long row_wtile_index(int n, int tap, int c, int 
     return ((long long)t * nch + ch) * ROW_WTILE + off_in;
 }
 
-template <int BN, bool GRAD>
+// Most output rows one CTA can pack (the launcher's upper bound for rows).
+__host__ __device__ inline int row_group(int W, int nacc, bool grad) {
+    return grad || W > ROW_T ? 1 : (nacc * 128 - W) / (W + 2) + 1;
+}
+
+template <int BN, bool GRAD, int NACC = 1>
 __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
     static_assert(BN == ROW_BN, "weights are pre-tiled for ROW_BN output channels");
-    constexpr int TCOLS = BN < 32 ? 32 : BN;
+    static_assert(NACC == 1 || (NACC == 2 && !GRAD), "two accumulators in the forward direction only");
+    constexpr int TCOLS = NACC * (BN < 32 ? 32 : BN);
     constexpr int HR = row_halo_rows(ROW_T);          // staged rows per 8-channel block
     constexpr int A_BYTES = 8 * HR * 16;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -268,7 +283,9 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
     unsigned char* Bs = tc_smem + A_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int segs = (a.W + ROW_T - 1) / ROW_T;
-    const int seg = blockIdx.x % segs, y = (blockIdx.x / segs) % a.H, b = blockIdx.x / (segs * a.H);
+    const int R = a.rows, groups = (a.H + R - 1) / R;
+    const int seg = blockIdx.x % segs, y = ((blockIdx.x / segs) % groups) * R, b = blockIdx.x / (segs * groups);
+    const int rows_here = min(R, a.H - y);
     const int x0 = seg * ROW_T, T = min(ROW_T, a.W - x0), Tp = T + 2;
     const int n0 = blockIdx.y * BN;
     const int sgn = GRAD ? -1 : 1;
@@ -305,7 +322,7 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
         }
         // stage the source rows: pixel q of row r (q = 0 .. Tp-1) at block g, row
         // r*Tp + q, by asynchronous 16-byte copies (zero-filled past Cs)
-        const int na = 3 * Tp * cgroups;
+        const int na = (R + 2) * Tp * cgroups;
         for (int i = tid; i < na; i += ROW_NT) {
             const int g = i % cgroups, q = (i / cgroups) % Tp, r = i / (cgroups * Tp);
             const int c = c_base + 8 * g;
@@ -339,7 +356,9 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
                 uint64_t ad = ad0 + (uint64_t)((tap / 3) * Tp + 1 + dx);
                 uint64_t bd = bd0 + (uint64_t)((tap * (ROW_CC / 16) * BN * 32) >> 4);
                 for (int s = 0; s < csteps; ++s) {
-                    mma_f16(tbase, ad, bd, idesc, acc);
+#pragma unroll
+                    for (int q = 0; q < NACC; ++q)   // accumulator q: tile rows 128 q ..
+                        mma_f16(tbase + (uint32_t)(q * BN), ad + (uint64_t)(q * 128), bd, idesc, acc);
                     acc = 1;
                     ad += 2 * HR;              // next 16-channel step: two group blocks
                     bd += (BN * 32) >> 4;      // next weight slice
@@ -356,14 +375,19 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
     }
     ok = __syncthreads_and(ok) != 0;   // the loads below are warp-collective
     if (!ok && tid == 0) atomicExch(a.err, TF_ERR_TIMEOUT);
-    if (ok) {
-        const int lane_row = (warp & 3) * 32 + (tid & 31);   // tensor-memory lane = output row
-        const size_t p = (size_t)(b * a.H + y) * a.W + x0 + lane_row;
+#pragma unroll 1
+    for (int q = 0; q < NACC && ok; ++q) {
+        // tensor-memory lane of accumulator q = tile row m = 128 q + lane_row:
+        // output row m / Tp of the group, pixel m % Tp (valid below T)
+        const int lane_row = (warp & 3) * 32 + (tid & 31);
+        const int m = q * 128 + lane_row, rr = m / Tp, xq = m - rr * Tp;
+        const bool valid = xq < T && rr < rows_here;
+        const size_t p = (size_t)(b * a.H + y + rr) * a.W + x0 + xq;
         const int half = warp >> 2;                          // columns [half * BN/2, (half+1) * BN/2)
 #pragma unroll 1
         for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2) && n0 + c0 < a.Nout; c0 += 16) {
             uint32_t r[16];
-            const uint32_t taddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * BN + c0);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -372,7 +396,7 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (lane_row >= T) continue;   // rows past the segment hold discarded results
+            if (!valid) continue;   // halo positions and rows past the group are discarded
             const int n = n0 + c0;
             if (GRAD) {
                 float* d = a.dx + p * a.Nout + n;
