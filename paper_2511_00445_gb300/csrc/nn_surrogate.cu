@@ -156,7 +156,7 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
     if (rb < 1) rb = 1;
     if (rb > r.H) rb = r.H;
     const tcg::ConvWalkArgs a{r.src, r.w, r.bias, r.out, r.B, r.H, r.W, r.Cs, r.Nout, r.relu,
-                              (int)rb, best_s, r.err};
+                              (int)rb, best_s, r.err, r.src2, r.C1};
     const dim3 grid((unsigned)(r.B * segs * rb), (unsigned)tiles);
     tcg::k_conv_walk<tcg::ROW_BN><<<grid, tcg::ROW_NT, tcg::walk_smem_bytes(r.Cs, best_s), st>>>(a);
     return cudaGetLastError();
@@ -696,10 +696,14 @@ size_t plan(tf_surrogate* s) {
 }
 
 // ---------------------------------------------------------------- passes
-cudaError_t forward_pass(tf_surrogate* s, int B) {
+// keep_cat: write every concatenation [upsampled, skip] into its tensor (the
+// backward pass reads it).  A forward-only pass leaves them virtual: the
+// convolution that consumes one reads the two parts in place.
+cudaError_t forward_pass(tf_surrogate* s, int B, bool keep_cat) {
     cudaStream_t st = s->stream;
     int* err = s->at<int>(s->err_off);
     const float* P = s->at<float>(s->p_off);
+    int virt_cat = -1, virt_up = -1, virt_skip = -1;   // the pending virtual concatenation
     for (const Op& op : s->ops) {
         if (op.kind == OP_CONV) {
             const Conv& cv = s->convs[op.a];
@@ -708,6 +712,12 @@ cudaError_t forward_pass(tf_surrogate* s, int B) {
             tcg::ConvRowArgs g{s->at<bf16>(ti.act), s->at<bf16>(cv.wb), P + cv.b_off,
                                s->at<bf16>(s->tensors[cv.out_t].act), nullptr,
                                B, H, W, cv.cin, cv.cout, 1, err};
+            if (cv.in_t == virt_cat) {
+                g.src = s->at<bf16>(s->tensors[virt_up].act);
+                g.src2 = s->at<bf16>(s->tensors[virt_skip].act);
+                g.C1 = s->tensors[virt_up].C;
+                virt_cat = -1;
+            }
             cudaError_t e = conv_rows<false>(g, st);
             if (e != cudaSuccess) return e;
         } else if (op.kind == OP_POOL) {
@@ -715,6 +725,10 @@ cudaError_t forward_pass(tf_surrogate* s, int B) {
             const int H = s->cfg.ny >> a.level, W = s->cfg.nx >> a.level;
             k_pool<<<blocks((long long)B * H * W * a.C / 32), EB, 0, st>>>(
                 s->at<bf16>(a.act), s->at<bf16>(s->tensors[op.b].act), B, H, W, a.C);
+        } else if (!keep_cat) {
+            virt_cat = op.c;
+            virt_up = op.a;
+            virt_skip = op.b;
         } else {
             const Tensor& up = s->tensors[op.a];
             const Tensor& sk = s->tensors[op.b];
@@ -940,7 +954,7 @@ int tf_sur_forward(tf_surrogate* s, const float* x, int batch, float* out) {
     if (!x || !out || batch < 1 || batch > s->cfg.max_batch) return sfail(s, TF_ERR_ARG, "bad batch or null array");
     int rc = upload_x(s, x, batch);
     if (rc != TF_OK) return rc;
-    SCK(s, forward_pass(s, batch));
+    SCK(s, forward_pass(s, batch, false));
     if ((rc = check_status(s)) != TF_OK) return rc;
     SCK(s, cudaMemcpyAsync(out, s->at<float>(s->pred_off), s->pixels(0, batch) * COUT * 4,
                            cudaMemcpyDeviceToHost, s->stream));
@@ -958,7 +972,7 @@ int tf_sur_gradients(tf_surrogate* s, const float* x, const float* target, int b
     if (rc != TF_OK) return rc;
     SCK(s, cudaMemcpyAsync(s->at<float>(s->tgt_off), target, s->pixels(0, batch) * COUT * 4,
                            cudaMemcpyHostToDevice, s->stream));
-    SCK(s, forward_pass(s, batch));
+    SCK(s, forward_pass(s, batch, true));
     double l = 0.0;
     SCK(s, backward_pass(s, batch, &l));
     if ((rc = check_status(s)) != TF_OK) return rc;
@@ -1038,7 +1052,7 @@ int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, 
         k_assemble<<<blocks((long long)batch * N), EB, 0, s->stream>>>(
             s->at<float>(s->data_off), s->at<int>(s->idx_off), s->at<float>(s->zeta_off), s->norm,
             s->zscale, N, batch, s->at<bf16>(s->tensors[s->x_t].act), s->at<float>(s->tgt_off));
-        SCK(s, forward_pass(s, batch));
+        SCK(s, forward_pass(s, batch, true));
         double l = 0.0;
         SCK(s, backward_pass(s, batch, losses ? &l : nullptr));
         if (losses) losses[it] = l;
@@ -1080,7 +1094,7 @@ int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst) {
     k_assemble<<<blocks((long long)nb * N), EB, 0, s->stream>>>(
         raw, s->at<int>(s->idx_off), zslot, s->norm, s->zscale, N, nb,
         s->at<bf16>(s->tensors[s->x_t].act), nullptr);
-    SCK(s, forward_pass(s, nb));
+    SCK(s, forward_pass(s, nb, false));
     for (int k = 0; k < nb; ++k)
         k_writeback<<<blocks(N), EB, 0, s->stream>>>(
             raw + (long long)k * 14 * N, s->at<float>(s->pred_off) + (long long)k * N * COUT, s->norm,

@@ -232,7 +232,22 @@ struct ConvRowArgs {
     int B, H, W, Cs, Nout, relu;
     int* err;
     int rows;                   // output rows per CTA, 1 .. row_group(W, NACC, GRAD) (set by the launcher)
+    // Forward only: with src2 set, the source is the concatenation of src
+    // upsampled 2x by repetition (H/2 x W/2, C1 channels) and src2 (H x W,
+    // Cs - C1 channels), read in place instead of from a materialised copy.
+    const __nv_bfloat16* src2 = nullptr;
+    int C1 = 0;
 };
+
+// Address of the 16-byte piece of channels c .. c + 7 (c < Cs, a multiple
+// of 8) of source pixel (b, yy, xx), for a plain or a concatenated source.
+__device__ __forceinline__ const __nv_bfloat16* src_piece(const __nv_bfloat16* src,
+                                                          const __nv_bfloat16* src2, int C1, int H,
+                                                          int W, int Cs, int b, int yy, int xx, int c) {
+    if (src2 == nullptr) return src + ((size_t)(b * H + yy) * W + xx) * Cs + c;
+    if (c < C1) return src + ((size_t)(b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * C1 + c;
+    return src2 + ((size_t)(b * H + yy) * W + xx) * (Cs - C1) + (c - C1);
+}
 
 constexpr int ROW_T = 128;      // output pixels per CTA
 constexpr int ROW_CC = 64;      // source channels per chunk
@@ -330,7 +345,8 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
             yy = yy < 0 ? yy + a.H : (yy >= a.H ? yy - a.H : yy);
             xx = xx < 0 ? xx + a.W : (xx >= a.W ? xx - a.W : xx);
             const bool in = c < a.Cs;
-            const __nv_bfloat16* src = a.src + ((size_t)(b * a.H + yy) * a.W + xx) * a.Cs + (in ? c : 0);
+            const __nv_bfloat16* src =
+                src_piece(a.src, a.src2, a.C1, a.H, a.W, a.Cs, b, yy, xx, in ? c : 0);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
                              smem_u32(As + (g * HR + r * Tp + q) * 16)),
                          "l"(src), "r"(in ? 16 : 0)
@@ -456,6 +472,8 @@ struct ConvWalkArgs {
     int rb;                     // row blocks per (image, segment, output tile)
     int slots;                  // ring depth S, 4 .. WALK_MAX_SLOTS
     int* err;
+    const __nv_bfloat16* src2;  // concatenated source, as in ConvRowArgs (or null)
+    int C1;
 };
 
 constexpr int WALK_MAX_SLOTS = 8;
@@ -528,7 +546,6 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
         int yy = ya + j;
         yy = yy < 0 ? yy + a.H : (yy >= a.H ? yy - a.H : yy);
         unsigned char* dst = Rs + (uint32_t)((j + S) % S) * slot_bytes;
-        const __nv_bfloat16* rowp = a.src + (size_t)(b * a.H + yy) * a.W * a.Cs;
         int g = g_first, q = q_first;       // element i = q * cg + g, stepping by ROW_NT
         for (int i = tid; i < WALK_ROWS * cg; i += ROW_NT) {
             const int c = 8 * g;
@@ -537,7 +554,8 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
             const bool in = c < a.Cs;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
                              smem_u32(dst + (g * WALK_ROWS + q) * 16)),
-                         "l"(rowp + (size_t)xx * a.Cs + (in ? c : 0)), "r"(in ? 16 : 0)
+                         "l"(src_piece(a.src, a.src2, a.C1, a.H, a.W, a.Cs, b, yy, xx, in ? c : 0)),
+                         "r"(in ? 16 : 0)
                          : "memory");
             g += g_step;
             q += q_step;
