@@ -75,13 +75,13 @@ cudaError_t run_gemm(const Op& op, int splits, cudaStream_t st) {
 }
 
 // Row-segment convolutions (forward and input gradient, tcg::k_conv_rows).
-template <int BN, bool GRAD, int NACC>
+template <int BN, int CC, bool GRAD, int NACC>
 cudaError_t run_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(tcg::k_conv_rows<BN, GRAD, NACC>,
+        cudaError_t e = cudaFuncSetAttribute(tcg::k_conv_rows<BN, CC, GRAD, NACC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             tcg::row_smem_bytes<BN>());
+                                             tcg::row_smem_bytes<BN, CC>());
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -102,7 +102,7 @@ cudaError_t run_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
     tcg::ConvRowArgs r = a;
     r.rows = R;
     const dim3 grid(segs * ((a.H + R - 1) / R) * a.B, tiles);
-    tcg::k_conv_rows<BN, GRAD, NACC><<<grid, tcg::ROW_NT, tcg::row_smem_bytes<BN>(), st>>>(r);
+    tcg::k_conv_rows<BN, CC, GRAD, NACC><<<grid, tcg::ROW_NT, tcg::row_smem_bytes<BN, CC>(), st>>>(r);
     return cudaGetLastError();
 }
 
@@ -114,6 +114,8 @@ cudaError_t run_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
 // tile) are then cut into rb blocks so that the grid fills the resident CTA
 // slots once.
 constexpr int kWalkMaxCs = 128;
+
+bool walks_forward(int W, int Cs) { return W % tcg::ROW_T == 0 && Cs <= kWalkMaxCs; }
 constexpr int kWalkDynSmem = 227 * 1024 - 1024;   // per-CTA limit less the static part
 constexpr int kSmemPerSM = 228 * 1024;
 
@@ -162,20 +164,25 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Forward: rows of a multiple of 128 pixels with few source channels walk;
-// rows of at most 64 pixels pack several output rows into two accumulators.
+// Forward: rows of a multiple of 128 pixels with few source channels walk
+// (walks_forward); other layers run the row-segment kernel with the layer's
+// weight layout (a.bn), rows of at most 64 pixels packing several output
+// rows into two accumulators.
 template <bool GRAD>
 cudaError_t conv_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
-    if (GRAD) return run_rows<tcg::ROW_BN, true, 1>(a, st);
-    if (a.W % tcg::ROW_T == 0 && a.Cs <= kWalkMaxCs) return run_walk(a, st);
-    if (a.W <= 64) return run_rows<tcg::ROW_BN, false, 2>(a, st);
-    return run_rows<tcg::ROW_BN, false, 1>(a, st);
+    if (GRAD) return run_rows<tcg::ROW_BN, tcg::ROW_CC, true, 1>(a, st);
+    if (walks_forward(a.W, a.Cs)) return run_walk(a, st);
+    if (a.bn == 64)
+        return a.W <= 64 ? run_rows<64, 32, false, 2>(a, st) : run_rows<64, 32, false, 1>(a, st);
+    if (a.W <= 64) return run_rows<tcg::ROW_BN, tcg::ROW_CC, false, 2>(a, st);
+    return run_rows<tcg::ROW_BN, tcg::ROW_CC, false, 1>(a, st);
 }
 
-// Bytes of one layer's pre-tiled weights (tcg::row_wtile_index).
-size_t wtile_bytes(int nout, int cs) {
-    return (size_t)((nout + tcg::ROW_BN - 1) / tcg::ROW_BN) * ((cs + tcg::ROW_CC - 1) / tcg::ROW_CC) *
-           tcg::ROW_WTILE;
+// Bytes of one layer's pre-tiled weights: bn = 32 (tcg::row_wtile_index,
+// 32 outputs x 64 source channels per block) or 64 (64 x 32).
+size_t wtile_bytes(int nout, int cs, int bn = 32) {
+    const int cc = bn == 64 ? 32 : tcg::ROW_CC;
+    return (size_t)((nout + bn - 1) / bn) * ((cs + cc - 1) / cc) * tcg::ROW_WTILE;
 }
 
 template <class Op>
@@ -416,14 +423,15 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
 // forward pass (rows o, source channels c) and for the input gradient (rows
 // c, source channels o).  Tile entries outside the layer stay zero.
 __global__ void k_weights_bf16(const float* __restrict__ w, unsigned char* __restrict__ wf,
-                               unsigned char* __restrict__ wg, int cout, int cin) {
+                               unsigned char* __restrict__ wg, int cout, int cin, int bn) {
     const long long n = (long long)cout * 9 * cin;
     const long long i = (long long)blockIdx.x * EB + threadIdx.x;
     if (i >= n) return;
     const int c = (int)(i % cin);
     const int tap = (int)((i / cin) % 9), o = (int)(i / (9LL * cin));
     const bf16 v = __float2bfloat16_rn(w[i]);
-    *reinterpret_cast<bf16*>(wf + tcg::row_wtile_index(o, tap, c, cin)) = v;
+    *reinterpret_cast<bf16*>(wf + (bn == 64 ? tcg::wtile_index<64, 32>(o, tap, c, cin)
+                                             : tcg::row_wtile_index(o, tap, c, cin))) = v;
     *reinterpret_cast<bf16*>(wg + tcg::row_wtile_index(c, tap, o, cout)) = v;
 }
 
@@ -547,6 +555,7 @@ struct Conv {
     long long w_off, b_off;      // offsets into the flat FP32 parameter vector
     size_t wb, wt;               // byte offsets of the BF16 copies
     int in_t, out_t;             // activation tensors
+    int bn = 32;                 // forward weight layout (see forward_bn)
 };
 struct Tensor {
     int C, level;
@@ -624,6 +633,12 @@ size_t plan(tf_surrogate* s) {
     auto conv = [&](int in_t, int cout) {
         const Tensor t = s->tensors[in_t];
         Conv cv{t.C, cout, t.level, np, np + (long long)cout * 9 * t.C, 0, 0, in_t, 0};
+        // forward layers on the row-segment kernel with a multiple of 64
+        // outputs take 64-wide output tiles (half the MMAs of 32-wide ones),
+        // except on rows under 64 pixels, whose grids are too small to halve
+        // (measured: slower there on the 4 x 256^2 prediction)
+        const int W = c.nx >> t.level;
+        cv.bn = !walks_forward(W, t.C) && W >= 64 && cout % 64 == 0 && t.C % 32 == 0 ? 64 : 32;
         np += (long long)cout * 9 * t.C + cout;
         cv.out_t = tensor(cout, t.level);
         s->convs.push_back(cv);
@@ -667,7 +682,7 @@ size_t plan(tf_surrogate* s) {
     s->m_off = take(np * 4);
     s->v_off = take(np * 4);
     for (Conv& cv : s->convs) {
-        cv.wb = take(wtile_bytes(cv.cout, cv.cin));
+        cv.wb = take(wtile_bytes(cv.cout, cv.cin, cv.bn));
         cv.wt = take(wtile_bytes(cv.cin, cv.cout));
     }
     long long max_cp = 0;
@@ -712,6 +727,7 @@ cudaError_t forward_pass(tf_surrogate* s, int B, bool keep_cat) {
             tcg::ConvRowArgs g{s->at<bf16>(ti.act), s->at<bf16>(cv.wb), P + cv.b_off,
                                s->at<bf16>(s->tensors[cv.out_t].act), nullptr,
                                B, H, W, cv.cin, cv.cout, 1, err};
+            g.bn = cv.bn;
             if (cv.in_t == virt_cat) {
                 g.src = s->at<bf16>(s->tensors[virt_up].act);
                 g.src2 = s->at<bf16>(s->tensors[virt_skip].act);
@@ -836,7 +852,7 @@ cudaError_t refresh_bf16(tf_surrogate* s) {
     const float* P = s->at<float>(s->p_off);
     for (const Conv& cv : s->convs)
         k_weights_bf16<<<blocks((long long)cv.cout * 9 * cv.cin), EB, 0, s->stream>>>(
-            P + cv.w_off, s->at<unsigned char>(cv.wb), s->at<unsigned char>(cv.wt), cv.cout, cv.cin);
+            P + cv.w_off, s->at<unsigned char>(cv.wb), s->at<unsigned char>(cv.wt), cv.cout, cv.cin, cv.bn);
     return cudaGetLastError();
 }
 

@@ -237,6 +237,7 @@ struct ConvRowArgs {
     // Cs - C1 channels), read in place instead of from a materialised copy.
     const __nv_bfloat16* src2 = nullptr;
     int C1 = 0;
+    int bn = 32;                // forward weight layout: 32 (x 64 source channels) or 64 (x 32)
 };
 
 // Address of the 16-byte piece of channels c .. c + 7 (c < Cs, a multiple
@@ -258,9 +259,16 @@ __host__ __device__ constexpr int row_halo_rows(int T) {
     return 3 * (T + 2) > 2 * (T + 2) + 2 + ROW_T ? 3 * (T + 2) : 2 * (T + 2) + 2 + ROW_T;
 }
 
-template <int BN>
+// Bytes of one pre-tiled weight block: BN output channels x CC source
+// channels x 9 taps (BF16); the same 36 KB for 32 x 64 and 64 x 32.
+template <int BN, int CC>
+constexpr int wtile_bytes_of() {
+    return 9 * (CC / 16) * BN * 32;
+}
+
+template <int BN, int CC = 64>
 constexpr int row_smem_bytes() {
-    return 8 * row_halo_rows(ROW_T) * 16 + 36 * BN * 32;
+    return (CC / 8) * row_halo_rows(ROW_T) * 16 + wtile_bytes_of<BN, CC>();
 }
 
 // Weights pre-tiled in the shared-memory image k_conv_rows stages: for output
@@ -270,13 +278,19 @@ constexpr int row_smem_bytes() {
 // for a layer with Cs source channels:
 constexpr int ROW_BN = 32;
 constexpr int ROW_WTILE = 36 * ROW_BN * 32;
+// General layout for a tile of BNt output channels and chunks of CCt source
+// channels (blocks of 9 * CCt / 16 slices of BNt x 16 K-major core matrices).
+template <int BNt, int CCt>
+__host__ __device__ inline long long wtile_index(int n, int tap, int c, int Cs) {
+    const int nch = (Cs + CCt - 1) / CCt;
+    const int t = n / BNt, nn = n % BNt, ch = c / CCt, cc = c % CCt;
+    const int slice = tap * (CCt / 16) + cc / 16, k = cc % 16;
+    const long long off_in = (long long)slice * BNt * 32 +
+                             (((k >> 3) * (BNt >> 3) + (nn >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2);
+    return ((long long)t * nch + ch) * wtile_bytes_of<BNt, CCt>() + off_in;
+}
 __host__ __device__ inline long long row_wtile_index(int n, int tap, int c, int Cs) {
-    const int nch = (Cs + ROW_CC - 1) / ROW_CC;
-    const int t = n / ROW_BN, nn = n % ROW_BN, ch = c / ROW_CC, cc = c % ROW_CC;
-    const int slice = tap * (ROW_CC / 16) + cc / 16, k = cc % 16;
-    const long long off_in = (long long)slice * ROW_BN * 32 +
-                             (((k >> 3) * (ROW_BN >> 3) + (nn >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2);
-    return ((long long)t * nch + ch) * ROW_WTILE + off_in;
+    return wtile_index<ROW_BN, ROW_CC>(n, tap, c, Cs);
 }
 
 // Most output rows one CTA can pack (the launcher's upper bound for rows).
@@ -284,13 +298,16 @@ __host__ __device__ inline int row_group(int W, int nacc, bool grad) {
     return grad || W > ROW_T ? 1 : (nacc * 128 - W) / (W + 2) + 1;
 }
 
-template <int BN, bool GRAD, int NACC = 1>
+// BN x CC: output-tile width and source chunk of the weight layout
+// (32 x 64, or 64 x 32 for forward layers with at least 64 outputs).
+template <int BN, int CC, bool GRAD, int NACC = 1>
 __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
-    static_assert(BN == ROW_BN, "weights are pre-tiled for ROW_BN output channels");
+    static_assert((BN == 32 && CC == 64) || (BN == 64 && CC == 32 && !GRAD), "weight layouts");
     static_assert(NACC == 1 || (NACC == 2 && !GRAD), "two accumulators in the forward direction only");
-    constexpr int TCOLS = NACC * (BN < 32 ? 32 : BN);
+    constexpr int TCOLS = NACC * BN;
+    constexpr int WTILE = wtile_bytes_of<BN, CC>();
     constexpr int HR = row_halo_rows(ROW_T);          // staged rows per 8-channel block
-    constexpr int A_BYTES = 8 * HR * 16;
+    constexpr int A_BYTES = (CC / 8) * HR * 16;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t bar, wbar;
     __shared__ uint32_t tmem_base;
@@ -321,19 +338,19 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
     const uint32_t tbase = tmem_base;
     uint32_t phase = 0;
     bool ok = true;
-    const int nchunks = (a.Cs + ROW_CC - 1) / ROW_CC;
+    const int nchunks = (a.Cs + CC - 1) / CC;
     const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(a.w) +
-                                (long long)blockIdx.y * nchunks * ROW_WTILE;
+                                (long long)blockIdx.y * nchunks * WTILE;
     const uint4 zero = make_uint4(0, 0, 0, 0);
     for (int ch = 0; ch < nchunks; ++ch) {
-        const int c_base = ch * ROW_CC;
-        const int csteps = min(ROW_CC, (a.Cs - c_base + 15) & ~15) / 16;   // K = 16 steps
+        const int c_base = ch * CC;
+        const int csteps = min(CC, (a.Cs - c_base + 15) & ~15) / 16;       // K = 16 steps
         const int cgroups = 2 * csteps;                                    // 8-channel groups
         // the chunk's weights: one bulk copy of the pre-tiled block (lands while
         // the threads stage the source rows)
         if (tid == 0) {
-            tfp::mbar_arrive_expect_tx(&wbar, (uint32_t)ROW_WTILE);
-            tfp::bulk_g2s(Bs, wsrc + (long long)ch * ROW_WTILE, (uint32_t)ROW_WTILE, &wbar);
+            tfp::mbar_arrive_expect_tx(&wbar, (uint32_t)WTILE);
+            tfp::bulk_g2s(Bs, wsrc + (long long)ch * WTILE, (uint32_t)WTILE, &wbar);
         }
         // stage the source rows: pixel q of row r (q = 0 .. Tp-1) at block g, row
         // r*Tp + q, by asynchronous 16-byte copies (zero-filled past Cs)
@@ -370,7 +387,7 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_rows(const ConvRowArgs a) {
                 // (the staging already applied the sign of the row offset)
                 const int dx = sgn * (tap % 3 - 1);
                 uint64_t ad = ad0 + (uint64_t)((tap / 3) * Tp + 1 + dx);
-                uint64_t bd = bd0 + (uint64_t)((tap * (ROW_CC / 16) * BN * 32) >> 4);
+                uint64_t bd = bd0 + (uint64_t)((tap * (CC / 16) * BN * 32) >> 4);
                 for (int s = 0; s < csteps; ++s) {
 #pragma unroll
                     for (int q = 0; q < NACC; ++q)   // accumulator q: tile rows 128 q ..
