@@ -119,6 +119,7 @@ bool walks_forward(int W, int Cs) { return W % tcg::ROW_T == 0 && Cs <= kWalkMax
 constexpr int kWalkDynSmem = 227 * 1024 - 1024;   // per-CTA limit less the static part
 constexpr int kSmemPerSM = 228 * 1024;
 
+template <int BN, int CC>
 cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
     static bool configured = false;
     static int sms = 0, regs = 0, static_smem = 0;
@@ -128,9 +129,9 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tcg::k_conv_walk<tcg::ROW_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(tcg::k_conv_walk<BN, CC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kWalkDynSmem);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tcg::k_conv_walk<tcg::ROW_BN>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, tcg::k_conv_walk<BN, CC>);
         if (e != cudaSuccess) return e;
         regs = fa.numRegs > 0 ? fa.numRegs : 1;
         static_smem = (int)fa.sharedSizeBytes;
@@ -138,12 +139,12 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
     }
     int best_s = 0, best_cta = 0, best_score = -1;
     for (int S = 4; S <= tcg::WALK_MAX_SLOTS; ++S) {
-        const int smem = tcg::walk_smem_bytes(r.Cs, S);
+        const int smem = tcg::walk_smem_bytes<BN, CC>(r.Cs, S);
         if (smem > kWalkDynSmem) break;
         int cta = kSmemPerSM / (smem + static_smem + 1024);          // 1 KB reserved per CTA
         cta = std::min(cta, 65536 / (tcg::ROW_NT * regs));
         cta = std::min(cta, 2048 / tcg::ROW_NT);
-        cta = std::min(cta, 512 / (2 * tcg::ROW_BN));                // tensor-memory columns
+        cta = std::min(cta, 512 / (2 * BN));                         // tensor-memory columns
         const int score = cta * (S - 3);
         if (cta >= 1 && score >= best_score) {
             best_score = score;
@@ -152,7 +153,7 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
         }
     }
     if (best_s == 0) return cudaErrorInvalidValue;
-    const int segs = r.W / tcg::ROW_T, tiles = (r.Nout + tcg::ROW_BN - 1) / tcg::ROW_BN;
+    const int segs = r.W / tcg::ROW_T, tiles = (r.Nout + BN - 1) / BN;
     const long long units = (long long)r.B * segs * tiles;
     long long rb = ((long long)sms * best_cta + units - 1) / units;
     if (rb < 1) rb = 1;
@@ -160,7 +161,7 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
     const tcg::ConvWalkArgs a{r.src, r.w, r.bias, r.out, r.B, r.H, r.W, r.Cs, r.Nout, r.relu,
                               (int)rb, best_s, r.err, r.src2, r.C1};
     const dim3 grid((unsigned)(r.B * segs * rb), (unsigned)tiles);
-    tcg::k_conv_walk<tcg::ROW_BN><<<grid, tcg::ROW_NT, tcg::walk_smem_bytes(r.Cs, best_s), st>>>(a);
+    tcg::k_conv_walk<BN, CC><<<grid, tcg::ROW_NT, tcg::walk_smem_bytes<BN, CC>(r.Cs, best_s), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -171,7 +172,8 @@ cudaError_t run_walk(const tcg::ConvRowArgs& r, cudaStream_t st) {
 template <bool GRAD>
 cudaError_t conv_rows(const tcg::ConvRowArgs& a, cudaStream_t st) {
     if (GRAD) return run_rows<tcg::ROW_BN, tcg::ROW_CC, true, 1>(a, st);
-    if (walks_forward(a.W, a.Cs)) return run_walk(a, st);
+    if (walks_forward(a.W, a.Cs))
+        return a.bn == 64 ? run_walk<64, 32>(a, st) : run_walk<tcg::ROW_BN, tcg::ROW_CC>(a, st);
     if (a.bn == 64)
         return a.W <= 64 ? run_rows<64, 32, false, 2>(a, st) : run_rows<64, 32, false, 1>(a, st);
     if (a.W <= 64) return run_rows<tcg::ROW_BN, tcg::ROW_CC, false, 2>(a, st);
@@ -633,12 +635,14 @@ size_t plan(tf_surrogate* s) {
     auto conv = [&](int in_t, int cout) {
         const Tensor t = s->tensors[in_t];
         Conv cv{t.C, cout, t.level, np, np + (long long)cout * 9 * t.C, 0, 0, in_t, 0};
-        // forward layers on the row-segment kernel with a multiple of 64
-        // outputs take 64-wide output tiles (half the MMAs of 32-wide ones),
-        // except on rows under 64 pixels, whose grids are too small to halve
-        // (measured: slower there on the 4 x 256^2 prediction)
+        // forward layers with a multiple of 64 outputs take 64-wide output
+        // tiles (half the MMAs of 32-wide ones): on the row-segment kernel for
+        // rows of at least 64 pixels (narrower rows leave too small a grid:
+        // measured slower on the 4 x 256^2 prediction), and on the walking
+        // kernel up to 96 source channels (weights and a four-row ring must fit)
         const int W = c.nx >> t.level;
-        cv.bn = !walks_forward(W, t.C) && W >= 64 && cout % 64 == 0 && t.C % 32 == 0 ? 64 : 32;
+        const bool walk = walks_forward(W, t.C);
+        cv.bn = cout % 64 == 0 && t.C % 32 == 0 && (walk ? t.C <= 96 : W >= 64) ? 64 : 32;
         np += (long long)cout * 9 * t.C + cout;
         cv.out_t = tensor(cout, t.level);
         s->convs.push_back(cv);

@@ -499,8 +499,9 @@ constexpr int WALK_ROWS = ROW_T + 2;    // staged pixel rows per 8-channel group
 // 8-channel groups staged per source row (source channels padded to K = 16 steps)
 __host__ __device__ constexpr int walk_groups(int Cs) { return 2 * ((Cs + 15) / 16); }
 
+template <int BN = ROW_BN, int CC = ROW_CC>
 __host__ __device__ constexpr int walk_smem_bytes(int Cs, int slots) {
-    return ((Cs + ROW_CC - 1) / ROW_CC) * ROW_WTILE + slots * walk_groups(Cs) * WALK_ROWS * 16;
+    return ((Cs + CC - 1) / CC) * wtile_bytes_of<BN, CC>() + slots * walk_groups(Cs) * WALK_ROWS * 16;
 }
 
 // cp.async.wait_group takes an immediate: wait until at most n (1 .. 5) of
@@ -515,19 +516,22 @@ __device__ __forceinline__ void cp_async_wait_upto(int n) {
     }
 }
 
-template <int BN>
+// BN x CC: weight layout as in k_conv_rows (32 x 64, or 64 x 32).
+template <int BN, int CC>
 __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
-    static_assert(BN == ROW_BN, "weights are pre-tiled for ROW_BN output channels");
+    static_assert((BN == 32 && CC == 64) || (BN == 64 && CC == 32), "weight layouts");
+    constexpr int WTILE = wtile_bytes_of<BN, CC>();
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t wbar, mbar[2];
     __shared__ uint32_t tmem_base;
+    __shared__ __align__(16) float sbias[BN];   // this tile's bias (0 past Nout)
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nch = (a.Cs + ROW_CC - 1) / ROW_CC, cg = walk_groups(a.Cs), csteps = cg / 2;
+    const int nch = (a.Cs + CC - 1) / CC, cg = walk_groups(a.Cs), csteps = cg / 2;
     const uint32_t slot_bytes = (uint32_t)cg * WALK_ROWS * 16;
     const int S = a.slots;
     const int g_first = tid % cg, q_first = tid / cg, g_step = ROW_NT % cg, q_step = ROW_NT / cg;
     unsigned char* Bs = tc_smem;
-    unsigned char* Rs = tc_smem + nch * ROW_WTILE;
+    unsigned char* Rs = tc_smem + nch * WTILE;
     const int segs = a.W / ROW_T;
     int u = blockIdx.x;
     const int blk = u % a.rb;
@@ -535,6 +539,7 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
     const int seg = u % segs, b = u / segs;
     const int ya = (int)((long long)blk * a.H / a.rb), yb = (int)((long long)(blk + 1) * a.H / a.rb);
     const int rows = yb - ya, x0 = seg * ROW_T, n0 = blockIdx.y * BN;
+    if (tid < BN) sbias[tid] = n0 + tid < a.Nout ? a.bias[n0 + tid] : 0.f;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tmem_base;
     if (tid == 0) {
-        const uint32_t wbytes = (uint32_t)nch * ROW_WTILE;
+        const uint32_t wbytes = (uint32_t)nch * WTILE;
         tfp::mbar_arrive_expect_tx(&wbar, wbytes);
         tfp::bulk_g2s(Bs, reinterpret_cast<const unsigned char*>(a.w) + (long long)blockIdx.y * wbytes,
                       wbytes, &wbar);
@@ -582,16 +587,15 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
             }
         }
     };
-    // this thread's 16 output channels (BN / 2 = 16: one block per thread)
-    static_assert(BN == 32, "one 16-column block per thread");
-    const int c0 = (warp >> 2) * 16;
-    float bias[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) bias[j] = n0 + c0 + j < a.Nout ? a.bias[n0 + c0 + j] : 0.f;
+    // warps w and w + 4 share tensor-memory lanes 32 (w % 4) ..; each takes half
+    // of the BN output columns, in blocks of 16
     auto epilogue = [&](int i) {
         const int lane_row = (warp & 3) * 32 + (tid & 31);
         const size_t p = (size_t)(b * a.H + ya + i) * a.W + x0 + lane_row;
-        if (n0 + c0 < a.Nout) {
+#pragma unroll
+        for (int blk = 0; blk < BN / 32; ++blk) {
+            const int c0 = (warp >> 2) * (BN / 2) + 16 * blk;
+            if (n0 + c0 >= a.Nout) break;   // uniform per warp
             uint32_t r[16];
             const uint32_t taddr =
                 tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((i & 1) * BN + c0);
@@ -607,7 +611,7 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
             float z[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                z[j] = __uint_as_float(r[j]) + bias[j];
+                z[j] = __uint_as_float(r[j]) + sbias[c0 + j];
                 if (a.relu) z[j] = fmaxf(z[j], 0.f);
             }
             __nv_bfloat16* d = a.out + p * a.Nout + n;
@@ -663,12 +667,12 @@ __global__ void __launch_bounds__(ROW_NT) k_conv_walk(const ConvWalkArgs a) {
             const uint64_t bd0 = smem_desc(smem_u32(Bs), BN * 16, 128);
             uint32_t acc = 0;
             for (int ch = 0; ch < nch; ++ch) {
-                const int nst = min(ROW_CC / 16, csteps - ch * (ROW_CC / 16));
+                const int nst = min(CC / 16, csteps - ch * (CC / 16));
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     // A: slot of source row i + dy, K-step gs = ch * 4 + s, pixel column 1 + dx
-                    uint64_t ad = dsl[tap / 3] + (uint64_t)((2 * ch * (ROW_CC / 16) * WALK_ROWS + 1 + tap % 3 - 1));
-                    uint64_t bd = bd0 + (uint64_t)((ch * ROW_WTILE + tap * (ROW_CC / 16) * BN * 32) >> 4);
+                    uint64_t ad = dsl[tap / 3] + (uint64_t)((2 * ch * (CC / 16) * WALK_ROWS + 1 + tap % 3 - 1));
+                    uint64_t bd = bd0 + (uint64_t)((ch * WTILE + tap * (CC / 16) * BN * 32) >> 4);
                     for (int st = 0; st < nst; ++st) {
                         mma_f16(acc_col, ad, bd, idesc, acc);
                         acc = 1;
