@@ -75,6 +75,23 @@ def test_ensemble_matches_groups_stepped_alone():
     assert ens.launches() == 2
 
 
+@pytest.mark.parametrize("nx,ny,storage", [(1024, 1024, B.STORE_F32), (1040, 1000, B.STORE_F32),
+                                          (1030, 1000, B.STORE_F32), (1024, 1024, B.STORE_F16)])
+def test_large_grid_matches_grid_stepped_alone(nx, ny, storage):
+    """Grids of several waves of tiles: the persistent ensemble launch (its
+    own tile numbering, populations read through L2 within the launch) and
+    the per-context launches agree bit for bit, also with a ragged last tile
+    column and row (1040 x 1000), rows that are not 16-byte multiples (1030:
+    per-element tile loads) and 16-bit population storage."""
+    spec = [[B.SolverParams(nx=nx, ny=ny, zeta=0.01, storage=storage)]]
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.step(1)
+    ens.step(5)
+    ens.sync()
+    assert_same(grp, alone(spec, 6))
+
+
 def test_ensemble_autotune_steps_are_real_steps():
     """Six candidates (tile heights 32/24/16, one or two CTAs per SM) each run
     real steps; the trajectory equals stepping alone."""
