@@ -131,8 +131,8 @@ k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int st
             const TileArgs<S> a{static_cast<const T*>(G.f[fp]), static_cast<T*>(G.f[fp ^ 1]),
                                 G.phi[pp], G.phi[pp ^ 1], G.Q[pp], G.Q[pp ^ 1], G.u[up],
                                 G.u[up ^ 1], G.prm, G.nx, G.ny, G.err};
-            const int y0 = tyi * TY, th = min(TY, G.ny - y0);
-            if (!fused_tile<DO_FD, DO_LBM, S, TY, true>(a, b, txi * TX, y0, th, &bar, phase)) {
+            const int y0 = tyi * TY, th = min(TY, G.ny - y0), x0 = txi * TX, tw = min(TX, G.nx - x0);
+            if (!fused_tile<DO_FD, DO_LBM, S, TY, true>(a, b, x0, y0, tw, th, &bar, phase)) {
                 if (threadIdx.x == 0) atomicExch(&ctl->abort, 1);
                 return;
             }

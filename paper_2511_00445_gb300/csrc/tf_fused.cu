@@ -6,11 +6,33 @@
 
 namespace {
 
+// Two tile geometries: narrow (TX x TY_DEFAULT, the 100 KB layout) for grids
+// whose tiles fit in one wave of resident CTAs, wide (TX_WIDE x TY_WIDE) for
+// larger grids.  The wide layout's extra shared memory leaves less of the
+// unified L1 for the population pulls, which cost the one-wave 4 x 256^2
+// sweep 1-3%, while its wider rows cut the sub-step work per site on large
+// grids (+5-6% at 1024^2 and 2048^2, measured).
+template <bool WIDE>
+struct CtxGeo {
+    static constexpr int TXM = WIDE ? TX_WIDE : TX;
+    static constexpr int TYM = WIDE ? TY_WIDE : TY_DEFAULT;
+};
+
+// Column cut of the per-context tiles: gridDim.x tile columns of at most
+// TXM columns; when nx is a multiple of 4 every tile starts on a multiple of 4
+// (16-byte rows for the bulk copies).
+__host__ __device__ inline int tile_col(int k, int ntx, int nx) {
+    return nx % 4 == 0 ? 4 * (int)((long long)k * (nx / 4) / ntx) : (int)((long long)k * nx / ntx);
+}
+
 // One tile per CTA: tile (blockIdx.x, blockIdx.y) of instance blockIdx.z.
 // The ny rows are cut into gridDim.y tile rows of floor or ceil(ny / gridDim.y)
-// rows each (at most TY_DEFAULT; the host picks gridDim.y).
-template <bool DO_FD, bool DO_LBM, class S>
+// rows each (at most TYM; the host picks gridDim.y), the nx columns into
+// gridDim.x tile columns of at most TXM columns (tile_col; the host picks
+// gridDim.x).
+template <bool DO_FD, bool DO_LBM, class S, bool WIDE>
 __global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
+    using C = CtxGeo<WIDE>;
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         tfp::mbar_init(&bar, 1);
@@ -19,14 +41,19 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
     __syncthreads();
     const int y0 = (int)((long long)blockIdx.y * a.ny / gridDim.y);
     const int y1 = (int)((long long)(blockIdx.y + 1) * a.ny / gridDim.y);
-    fused_tile<DO_FD, DO_LBM, S, TY_DEFAULT>(a, blockIdx.z, blockIdx.x * TX, y0, y1 - y0, &bar, 0);
+    const int x0 = tile_col(blockIdx.x, gridDim.x, a.nx), x1 = tile_col(blockIdx.x + 1, gridDim.x, a.nx);
+    fused_tile<DO_FD, DO_LBM, S, C::TYM, false, C::TXM>(a, blockIdx.z, x0, y0, x1 - x0, y1 - y0, &bar, 0);
 }
 
 template <bool DO_FD, bool DO_LBM, class S>
 cudaError_t configure_one() {
-    return cudaFuncSetAttribute(k_fused<DO_FD, DO_LBM, S>,
+    cudaError_t e = cudaFuncSetAttribute(k_fused<DO_FD, DO_LBM, S, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Geo<DO_FD, DO_LBM, TY_DEFAULT, TX>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fused<DO_FD, DO_LBM, S, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Geo<DO_FD, DO_LBM, TY_DEFAULT>::SMEM);
+                                (int)Geo<DO_FD, DO_LBM, TY_WIDE, TX_WIDE>::SMEM);
 }
 
 template <class S>
@@ -37,27 +64,28 @@ cudaError_t configure() {
     return e;
 }
 
-template <bool DO_FD, bool DO_LBM, class S>
+template <bool DO_FD, bool DO_LBM, class S, bool WIDE>
 void launch_as(tf_ctx* ctx) {
-    using G = Geo<DO_FD, DO_LBM, TY_DEFAULT>;
+    using G = Geo<DO_FD, DO_LBM, CtxGeo<WIDE>::TYM, CtxGeo<WIDE>::TXM>;
     using T = typename S::T;
     DevBuffers& d = ctx->d;
-    const dim3 grid((ctx->nx + TX - 1) / TX, ctx->tile_rows, ctx->batch);
+    const dim3 grid(ctx->tile_cols, ctx->tile_rows, ctx->batch);
     const int fc = ctx->fcur, pc = ctx->pcur, uc = ctx->ucur;
     const TileArgs<S> a{static_cast<const T*>(d.f[fc]), static_cast<T*>(d.f[fc ^ 1]),
                         d.phi[pc], d.phi[pc ^ 1], d.Q[pc], d.Q[pc ^ 1], d.u[uc], d.u[uc ^ 1],
                         d.prm, ctx->nx, ctx->ny, d.flags};
-    k_fused<DO_FD, DO_LBM, S><<<grid, NT, G::SMEM, ctx->stream>>>(a);
+    k_fused<DO_FD, DO_LBM, S, WIDE><<<grid, NT, G::SMEM, ctx->stream>>>(a);
 }
 
 template <bool DO_FD, bool DO_LBM>
 cudaError_t launch(tf_ctx* ctx) {
+    const bool w = ctx->wide_tiles;
     if (ctx->storage == TF_STORE_F16)
-        launch_as<DO_FD, DO_LBM, PopF16>(ctx);
+        w ? launch_as<DO_FD, DO_LBM, PopF16, true>(ctx) : launch_as<DO_FD, DO_LBM, PopF16, false>(ctx);
     else if (ctx->storage == TF_STORE_BF16)
-        launch_as<DO_FD, DO_LBM, PopBF16>(ctx);
+        w ? launch_as<DO_FD, DO_LBM, PopBF16, true>(ctx) : launch_as<DO_FD, DO_LBM, PopBF16, false>(ctx);
     else
-        launch_as<DO_FD, DO_LBM, PopF32>(ctx);
+        w ? launch_as<DO_FD, DO_LBM, PopF32, true>(ctx) : launch_as<DO_FD, DO_LBM, PopF32, false>(ctx);
     if (DO_LBM) {
         ctx->fcur ^= 1;
         ctx->ucur ^= 1;
@@ -85,9 +113,16 @@ cudaError_t tf_configure_fused_kernels() {
 // Otherwise the fewest tile rows of at most TY_DEFAULT rows are used.
 constexpr int kMinTileRows = 8;
 
-int tile_rows_for(int nx, int ny, int batch, long long slots) {
-    const long long per_row = (long long)((nx + TX - 1) / TX) * batch;   // tiles per tile row
-    const int need = (ny + TY_DEFAULT - 1) / TY_DEFAULT;
+// Narrow tiles while a step fits in one wave of resident CTAs (there the step
+// lasts one SM's pair of tiles, so shorter tile rows matter more than wider
+// tiles); wide tiles beyond.
+bool wide_for(int nx, int ny, int batch, long long slots) {
+    return (long long)((nx + TX - 1) / TX) * ((ny + TY_DEFAULT - 1) / TY_DEFAULT) * batch > slots;
+}
+
+int tile_rows_for(int ntx, int ny, int tym, int batch, long long slots) {
+    const long long per_row = (long long)ntx * batch;   // tiles per tile row
+    const int need = (ny + tym - 1) / tym;
     const long long fit = slots / per_row;          // tile rows that one wave holds
     if (fit <= need) return need;
     const int most = ny / kMinTileRows > need ? ny / kMinTileRows : need;
@@ -101,9 +136,13 @@ cudaError_t plan_tile_rows(tf_ctx* ctx) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_fused<true, true, PopF32>, NT, Geo<true, true, TY_DEFAULT>::SMEM);
+            &per_sm, k_fused<true, true, PopF32, false>, NT, Geo<true, true, TY_DEFAULT, TX>::SMEM);
     if (e != cudaSuccess) return e;
-    ctx->tile_rows = tile_rows_for(ctx->nx, ctx->ny, ctx->batch, (long long)sms * per_sm);
+    const long long slots = (long long)sms * per_sm;
+    ctx->wide_tiles = wide_for(ctx->nx, ctx->ny, ctx->batch, slots);
+    const int txm = ctx->wide_tiles ? TX_WIDE : TX, tym = ctx->wide_tiles ? TY_WIDE : TY_DEFAULT;
+    ctx->tile_cols = (ctx->nx + txm - 1) / txm;
+    ctx->tile_rows = tile_rows_for(ctx->tile_cols, ctx->ny, tym, ctx->batch, slots);
     return cudaSuccess;
 }
 

@@ -31,8 +31,12 @@
 
 namespace {
 
-constexpr int TX = 32;              // tile width: one column pair per lane
-constexpr int TY_DEFAULT = 32;      // tile height of the per-context path
+constexpr int TX = 32;              // tile width of the ensemble kernel
+constexpr int TY_DEFAULT = 32;      // tile height of the per-context path (narrow tiles)
+// Wide per-context tiles for grids of several waves (see Geo): 40 x 30 fills
+// the 32 column-pair lanes at the widest sub-step in 108 KB of shared memory.
+constexpr int TX_WIDE = 40;
+constexpr int TY_WIDE = 30;
 constexpr int NT = 256;        // threads per CTA: 32 x 8
 constexpr int NS_FUSED = 5;    // sub-steps handled by the fused kernel (Sec. III)
 constexpr uint32_t kWaitPolls = 1u << 22;
@@ -47,12 +51,21 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 
 constexpr int round4(int v) { return (v + 3) & ~3; }
 
-template <bool DO_FD, bool DO_LBM, int TY>
+// TXM: the widest tile.  A warp row of a sub-step costs the same however
+// many of its 32 column pairs are used, so sub-step work per site falls with
+// the tile width; 40 columns plus the widest neighbourhood (2 x 11) plus the
+// one-column halo of each side fill exactly 64 columns.
+template <bool DO_FD, bool DO_LBM, int TY, int TXM = TX>
 struct Geo {
     static constexpr int R_END = DO_LBM ? 2 : 0;                  // phi/Q radius after FD
     static constexpr int RH_NEED = R_END + (DO_FD ? 2 * NS_FUSED : 0);
     static constexpr int RH = round4(RH_NEED < 4 ? 4 : RH_NEED);  // loaded halo, 16-byte aligned
-    static constexpr int W = TX + 2 * RH;
+    static constexpr int W = TXM + 2 * RH;
+    // lanes of the widest paired row (PairCols): the chemical potential of the
+    // first sub-step on radius RH_NEED - 1, or the stress stage on radius 1
+    static constexpr int RA = DO_FD ? RH_NEED - 1 : 1;
+    static constexpr int LANES = ((RH - RA + TXM + 2 * RA) >> 1) - ((RH - RA - 1) >> 1) + 1;
+    static_assert(LANES <= 32, "widest paired row within the 32 lanes of a warp");
     static constexpr int H = TY + 2 * RH;
     static constexpr int A = W * H;                              // floats per smem plane
     static constexpr int NPLANES = 8;                            // phi mu u1x u1y u2x u2y qa qb
@@ -75,7 +88,7 @@ enum { P_PHI = 0, P_MU, P_U1X, P_U1Y, P_U2X, P_U2Y, P_QA, P_QB };
 // just above and below a band belong to other warps and are captured in
 // registers before a barrier.
 template <int RH, int W, int A>
-__device__ __forceinline__ void fd_substep(const DevParams& P, int th, int rp, int rq) {
+__device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, int rp, int rq) {
     using namespace tfq;
     float* __restrict__ phi = tf_smem + P_PHI * A;
     float* __restrict__ mu = tf_smem + P_MU * A;
@@ -92,7 +105,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int th, int rp, i
 
     // (a) chemical potential on radius ra = rp + 1 (reads phi on ra + 1)
     {
-        const int ra = rp + 1, w = TX + 2 * ra, h = th + 2 * ra, o = RH - ra;
+        const int ra = rp + 1, w = tw + 2 * ra, h = th + 2 * ra, o = RH - ra;
         const PairCols pc(o, w, lane);
         const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
         if (y0 < y1) {
@@ -113,10 +126,10 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int th, int rp, i
     __syncthreads();
 
     // (b) phi on radius rp, Q on radius rq
-    const int w = TX + 2 * rp, h = th + 2 * rp, o = RH - rp;
+    const int w = tw + 2 * rp, h = th + 2 * rp, o = RH - rp;
     const PairCols pc(o, w, lane);
     const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
-    const int oq = RH - rq, wq = TX + 2 * rq;     // Q neighbourhood (shared coordinates)
+    const int oq = RH - rq, wq = tw + 2 * rq;     // Q neighbourhood (shared coordinates)
     const bool qs = pc.meets(oq, wq);
     // Forward Euler with dt and the factors 1/2 of the central differences
     // folded into the coefficients (Eq. 1 and Eqs. 11-12):
@@ -271,7 +284,7 @@ struct TileArgs {
     int* err;
 };
 
-// One tile of TX columns and th <= TY rows (origin x0, y0) of instance b:
+// One tile of tw <= TXM columns and th <= TY rows (origin x0, y0) of instance b:
 // loads, pending sub-steps, LBM, stores.  Every value a tile stores depends
 // only on the state inside its dependency cone, so results do not depend on
 // how the grid is cut into tiles.  `bar` is this CTA's initialised mbarrier and `phase` the
@@ -281,10 +294,10 @@ struct TileArgs {
 // Returns false after a bulk-copy timeout (reported in *err).
 // MULTI: the launch runs several steps, so the population source was written
 // by other CTAs earlier in the same launch; it is then read through L2 only.
-template <bool DO_FD, bool DO_LBM, class S, int TY, bool MULTI = false>
-__device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, int y0, int th,
-                                           uint64_t* bar, uint32_t phase) {
-    using G = Geo<DO_FD, DO_LBM, TY>;
+template <bool DO_FD, bool DO_LBM, class S, int TY, bool MULTI = false, int TXM = TX>
+__device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, int y0, int tw,
+                                           int th, uint64_t* bar, uint32_t phase) {
+    using G = Geo<DO_FD, DO_LBM, TY, TXM>;
     constexpr int RH = G::RH, W = G::W, H = G::H, A = G::A;
     const typename S::T* __restrict__ fsrc = a.fsrc;
     typename S::T* __restrict__ fdst = a.fdst;
@@ -313,21 +326,27 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         return tf_smem + (pl == 0 ? P_PHI : (pl < 3 ? P_QA + pl - 1 : P_U1X + pl - 3)) * A;
     };
     const int hr = th + 2 * RH;     // loaded rows (<= H)
+    const int wr = tw + 2 * RH;     // loaded columns (<= W; a multiple of 4 whenever bulk)
     if (bulk) {
         if (threadIdx.x == 0)
-            tfp::mbar_arrive_expect_tx(bar, (uint32_t)(G::NLOAD * hr * W * sizeof(float)));
+            tfp::mbar_arrive_expect_tx(bar, (uint32_t)(G::NLOAD * hr * wr * sizeof(float)));
         for (int t = threadIdx.x; t < G::NLOAD * H; t += NT) {
             const int pl = t / H, ly = t - pl * H;
             if (ly >= hr) continue;
             const int gy = wrapc(y0 - RH + ly, ny);
-            bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, W, nx, bar);
+            bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, wr, nx, bar);
         }
         if (DO_LBM && pref) {
+            // columns x0 - 1 .. x0 + tw widened to whole 16-byte units (PF
+            // elements): tiles start on multiples of 4 only, and the bulk
+            // prefetch needs 16-byte aligned starts and sizes
+            const int xs = ((x0 - 1 + PF) / PF - 1) * PF;             // floor to PF (x0 - 1 >= -1)
+            const int xe = (x0 + tw + 1 + PF - 1) / PF * PF;           // ceil to PF
             const typename S::T* F = fsrc + 18 * b * N;
             for (int t = threadIdx.x; t < 18 * (TY + 2); t += NT) {
                 const int i = t / (TY + 2), r = t - i * (TY + 2);
                 if (r >= th + 2) continue;
-                prefetch_row(F + (long long)i * N, wrapc(y0 - 1 + r, ny), x0 - PF, TX + 2 * PF, nx);
+                prefetch_row(F + (long long)i * N, wrapc(y0 - 1 + r, ny), xs, xe - xs, nx);
             }
         }
         const bool ok = tfp::wait_bounded(bar, phase & 1u, kWaitPolls);
@@ -339,12 +358,12 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             return false;
         }
     } else {
-        for (int i = threadIdx.x; i < hr * W; i += NT) {
-            const int ly = i / W, lx = i - ly * W;
+        for (int i = threadIdx.x; i < hr * wr; i += NT) {
+            const int ly = i / wr, lx = i - ly * wr;
             const long long g = (long long)wrapc(y0 - RH + ly, ny) * nx + wrapc(x0 - RH + lx, nx);
 #pragma unroll
             for (int pl = 0; pl < G::NLOAD; ++pl)
-                dst_plane(pl)[i] = MULTI ? __ldcg(src_plane(pl) + g) : src_plane(pl)[g];
+                dst_plane(pl)[ly * W + lx] = MULTI ? __ldcg(src_plane(pl) + g) : src_plane(pl)[g];
         }
         __syncthreads();
     }
@@ -355,7 +374,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         for (int st = 0; st < NS_FUSED; ++st) {
             const int rp = G::R_END + 2 * (NS_FUSED - 1 - st);
             const int rq = G::R_END + (NS_FUSED - 1 - st);
-            fd_substep<RH, W, A>(P, th, rp, rq);
+            fd_substep<RH, W, A>(P, tw, th, rp, rq);
         }
     }
 
@@ -369,8 +388,8 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             const float* phi = tf_smem + P_PHI * A;
             const float* qa = tf_smem + P_QA * A;
             const float* qb = tf_smem + P_QB * A;
-            constexpr int o = RH - 1, w = TX + 2, NW = NT / 32;
-            const int h = th + 2;
+            constexpr int o = RH - 1, NW = NT / 32;
+            const int w = tw + 2, h = th + 2;
             const PairCols pc(o, w, tx);
             const int bh = (h + NW - 1) / NW;
             const int y0 = ty * bh, y1 = min(h, y0 + bh);
@@ -415,11 +434,11 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         typename S::T* D1 = fdst + 18 * b * N;
         typename S::T* D2 = D1 + 9 * N;
         float* uo = u_out + 4 * b * N;
-#pragma unroll 1
-        for (int r = ty; r < th; r += NT / 32) {
-            const int x = x0 + tx, y = y0 + r;
-            if (x >= nx || y >= ny) continue;
-            const int c = (RH + r) * W + RH + tx;
+        // the LBM update of site (r, cx) of the tile
+        auto lbm_site = [&](int r, int cx) {
+            const int x = x0 + cx, y = y0 + r;
+            if (x >= nx || y >= ny) return;
+            const int c = (RH + r) * W + RH + cx;
             const int xp = x + 1 < nx ? x + 1 : 0, xm = x > 0 ? x - 1 : nx - 1;
             const int yp = y + 1 < ny ? y + 1 : 0, ym = y > 0 ? y - 1 : ny - 1;
             f2 f[9];
@@ -448,16 +467,37 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             uo[N + g] = u1.y;
             uo[2 * N + g] = u2.x;
             uo[3 * N + g] = u2.y;
+        };
+        if (tw == 32) {
+            // one tile row per warp pass, one column per lane (y uniform in a warp)
+#pragma unroll 1
+            for (int r = ty; r < th; r += NT / 32) lbm_site(r, tx);
+        } else {
+            // the tile's tw x th sites in row-major order, one per thread (a warp
+            // may span two rows); (r, cx) advance by NT sites per pass
+            int r = threadIdx.x / tw, cx = threadIdx.x - r * tw;
+            const int dr = NT / tw, dc = NT - dr * tw;
+#pragma unroll 1
+            for (int site = threadIdx.x; site < tw * th; site += NT) {
+                lbm_site(r, cx);
+                cx += dc;
+                r += dr;
+                if (cx >= tw) {
+                    cx -= tw;
+                    ++r;
+                }
+            }
         }
     }
     if constexpr (DO_FD) {
         // ---- store phi^{k+1}, Q^{k+1} of the interior
         float* po = phi_out + b * N;
         float* qo = Q_out + 2 * b * N;
-        for (int r = ty; r < th; r += NT / 32) {
-            const int x = x0 + tx, y = y0 + r;
+        for (int site = threadIdx.x; site < tw * th; site += NT) {
+            const int r = site / tw, cx = site - r * tw;
+            const int x = x0 + cx, y = y0 + r;
             if (x >= nx || y >= ny) continue;
-            const int c = (RH + r) * W + RH + tx;
+            const int c = (RH + r) * W + RH + cx;
             const long long g = (long long)y * nx + x;
             po[g] = tf_smem[P_PHI * A + c];
             qo[g] = tf_smem[P_QA * A + c];

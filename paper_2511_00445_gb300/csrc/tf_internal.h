@@ -131,6 +131,8 @@ struct tf_ctx {
     int ucur = 0;                    // velocity buffer written by the last fused launch
     bool fd_pending = false;         // fused path: sub-steps of the last step not yet applied
     int tile_rows = 0;               // fused path: tile rows per instance (0: not planned yet)
+    int tile_cols = 0;               // fused path: tile columns per instance
+    bool wide_tiles = false;         // fused path: the wide tile geometry
     int64_t steps = 0;
     int64_t launches = 0;            // kernels launched by this context
     int n_shell = 0;
