@@ -292,8 +292,9 @@ int tf_ensemble_step(tf_ensemble* ens, int64_t n);
  * (TF_ERR_TIMEOUT after a bounded wait ran out). */
 int tf_ensemble_sync(tf_ensemble* ens);
 
-/* Tile-shape autotuner: candidate k = 0..5 is tile height {32, 24, 16}[k/2]
- * with {2, 1}[k%2] resident CTAs per SM.  Each candidate runs one launch of
+/* Tile-shape autotuner: candidate k = 0..5 is tile shape (columns x rows)
+ * {32 x 32, 32 x 24, 40 x 30}[k/2] with {2, 1}[k%2] resident CTAs per SM
+ * (40-column tiles: columns cut at multiples of 4, up to 40 wide).  Each candidate runs one launch of
  * `steps_per_candidate` (>= 1) real steps timed with CUDA events; the fastest
  * becomes the configuration.  Every candidate computes bitwise the same
  * trajectory, so the tuning steps are ordinary steps: the ensemble advances
@@ -301,8 +302,8 @@ int tf_ensemble_sync(tf_ensemble* ens);
  * Synchronous. */
 int tf_ensemble_autotune(tf_ensemble* ens, int steps_per_candidate);
 
-/* Current configuration: tile height, CTAs per SM, grid size of the
- * persistent launch, tiles per step; us_per_step (may be NULL) receives the
+/* Current configuration: tile height (30 means the 40 x 30 shape), CTAs per
+ * SM, grid size of the persistent launch, tiles per step; us_per_step (may be NULL) receives the
  * TF_ENS_CANDIDATES autotuner timings in microseconds per step (0 before
  * tf_ensemble_autotune).  *graphs = 1 when launches replay CUDA graphs, 0
  * when they are issued directly (stream capture unavailable). */

@@ -2,7 +2,7 @@
 // different grid sizes stepped together by one persistent cooperative kernel.
 //
 // Work-list: tile t of a step is found by scanning the groups' first-tile
-// offsets (per tile height); within a group the tiles are numbered instance
+// offsets (per tile shape); within a group the tiles are numbered instance
 // by instance, row-major.  CTAs take tiles from a per-step atomic ticket
 // counter (dynamic balance across uneven instance sizes), run the same
 // per-tile code as the per-context kernel (tf_fused.cuh), and meet at a grid
@@ -19,8 +19,11 @@
 
 namespace {
 
-constexpr int kTileY[3] = {32, 24, 16};       // candidate tile heights
-constexpr int kCandidates = TF_ENS_CANDIDATES; // tile height x CTAs per SM {2, 1}
+// Candidate tile shapes (columns x rows): the 32-column shapes cut columns at
+// multiples of 32, the wide one like the per-context wide tiles (tile_col).
+constexpr int kTileX[3] = {TX, TX, TX_WIDE};
+constexpr int kTileY[3] = {32, 24, TY_WIDE};
+constexpr int kCandidates = TF_ENS_CANDIDATES; // tile shape x CTAs per SM {2, 1}
 constexpr uint32_t kBarrierPolls = 1u << 23;   // x ~128 ns sleeps: about one second
 constexpr int64_t kMaxStepsPerLaunch = 1024;
 
@@ -31,8 +34,9 @@ struct EnsGroup {
     float* u[2];
     const DevParams* prm;
     int* err;                // the group's device status word
-    int nx, ny, batch, tiles_x;
-    long long begin[3];      // first tile of the group for tile heights 32, 24, 16
+    int nx, ny, batch;
+    int tiles_x[3];          // tile columns per tile shape
+    long long begin[3];      // first tile of the group per tile shape
 };
 
 struct EnsCtl {
@@ -43,9 +47,9 @@ struct EnsCtl {
     int pad[3];
 };
 
-template <int TY>
-constexpr int ty_index() {
-    return TY == 32 ? 0 : (TY == 24 ? 1 : 2);
+template <int TY, int TXW>
+constexpr int shape_index() {
+    return TXW == TX_WIDE ? 2 : (TY == 32 ? 0 : 1);
 }
 
 // All CTAs of the launch meet here.  Thread 0 of each CTA arrives on a
@@ -93,11 +97,11 @@ __device__ __forceinline__ bool grid_barrier(EnsCtl* ctl, int k, int* err) {
 // `steps` lattice steps of every tile of every group.  Parities fpar, ppar,
 // upar select the current population, phi/Q and velocity buffers at step 0;
 // each step flips the ones it writes.
-template <bool DO_FD, bool DO_LBM, class S, int TY>
+template <bool DO_FD, bool DO_LBM, class S, int TY, int TXW>
 __global__ void __launch_bounds__(NT, 2)
 k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int steps, int fpar,
       int ppar, int upar, EnsCtl* ctl) {
-    constexpr int TI = ty_index<TY>();
+    constexpr int TI = shape_index<TY, TXW>();
     using T = typename S::T;
     __shared__ __align__(8) uint64_t bar;
     __shared__ long long s_ticket;
@@ -124,15 +128,18 @@ k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int st
             while (g + 1 < n_groups && groups[g + 1].begin[TI] <= t) ++g;
             const EnsGroup& G = groups[g];
             const long long local = t - G.begin[TI];
-            const long long per = (long long)G.tiles_x * ((G.ny + TY - 1) / TY);
+            const int ntx = G.tiles_x[TI];
+            const long long per = (long long)ntx * ((G.ny + TY - 1) / TY);
             const int b = (int)(local / per);
             const long long r = local - (long long)b * per;
-            const int tyi = (int)(r / G.tiles_x), txi = (int)(r - (long long)tyi * G.tiles_x);
+            const int tyi = (int)(r / ntx), txi = (int)(r - (long long)tyi * ntx);
             const TileArgs<S> a{static_cast<const T*>(G.f[fp]), static_cast<T*>(G.f[fp ^ 1]),
                                 G.phi[pp], G.phi[pp ^ 1], G.Q[pp], G.Q[pp ^ 1], G.u[up],
                                 G.u[up ^ 1], G.prm, G.nx, G.ny, G.err};
-            const int y0 = tyi * TY, th = min(TY, G.ny - y0), x0 = txi * TX, tw = min(TX, G.nx - x0);
-            if (!fused_tile<DO_FD, DO_LBM, S, TY, true>(a, b, x0, y0, tw, th, &bar, phase)) {
+            const int y0 = tyi * TY, th = min(TY, G.ny - y0);
+            const int x0 = TXW == TX ? txi * TX : tile_col(txi, ntx, G.nx);
+            const int tw = TXW == TX ? min(TX, G.nx - x0) : tile_col(txi + 1, ntx, G.nx) - x0;
+            if (!fused_tile<DO_FD, DO_LBM, S, TY, true, TXW>(a, b, x0, y0, tw, th, &bar, phase)) {
                 if (threadIdx.x == 0) atomicExch(&ctl->abort, 1);
                 return;
             }
@@ -149,10 +156,10 @@ typedef void (*EnsKernel)(const EnsGroup*, int, long long, int, int, int, int, E
 
 template <class S>
 EnsKernel pick(int mode, int ti) {
-    if (mode == kPrologue) return k_ens<false, true, S, 32>;
-    if (ti == 0) return k_ens<true, true, S, 32>;
-    if (ti == 1) return k_ens<true, true, S, 24>;
-    return k_ens<true, true, S, 16>;
+    if (mode == kPrologue) return k_ens<false, true, S, 32, TX>;
+    if (ti == 0) return k_ens<true, true, S, 32, TX>;
+    if (ti == 1) return k_ens<true, true, S, 24, TX>;
+    return k_ens<true, true, S, TY_WIDE, TX_WIDE>;
 }
 
 EnsKernel kernel_for(int storage, int mode, int ti) {
@@ -165,7 +172,7 @@ size_t smem_for(int mode, int ti) {
     if (mode == kPrologue) return Geo<false, true, 32>::SMEM;
     if (ti == 0) return Geo<true, true, 32>::SMEM;
     if (ti == 1) return Geo<true, true, 24>::SMEM;
-    return Geo<true, true, 16>::SMEM;
+    return Geo<true, true, TY_WIDE, TX_WIDE>::SMEM;
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -340,10 +347,10 @@ int normalise(tf_ensemble* e) {
         G.nx = c->nx;
         G.ny = c->ny;
         G.batch = c->batch;
-        G.tiles_x = (c->nx + TX - 1) / TX;
         for (int ti = 0; ti < 3; ++ti) {
+            G.tiles_x[ti] = (c->nx + kTileX[ti] - 1) / kTileX[ti];
             G.begin[ti] = begin[ti];
-            begin[ti] += (long long)c->batch * G.tiles_x * ((c->ny + kTileY[ti] - 1) / kTileY[ti]);
+            begin[ti] += (long long)c->batch * G.tiles_x[ti] * ((c->ny + kTileY[ti] - 1) / kTileY[ti]);
         }
     }
     for (int ti = 0; ti < 3; ++ti) e->tiles[ti] = begin[ti];
@@ -368,19 +375,19 @@ bool members_in_step(const tf_ensemble* e) {
     return true;
 }
 
-template <bool DO_FD, bool DO_LBM, class S, int TY>
+template <bool DO_FD, bool DO_LBM, class S, int TY, int TXW>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(k_ens<DO_FD, DO_LBM, S, TY>,
+    return cudaFuncSetAttribute(k_ens<DO_FD, DO_LBM, S, TY, TXW>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Geo<DO_FD, DO_LBM, TY>::SMEM);
+                                (int)Geo<DO_FD, DO_LBM, TY, TXW>::SMEM);
 }
 
 template <class S>
 cudaError_t configure_storage() {
-    cudaError_t e = set_smem<false, true, S, 32>();
-    if (e == cudaSuccess) e = set_smem<true, true, S, 32>();
-    if (e == cudaSuccess) e = set_smem<true, true, S, 24>();
-    if (e == cudaSuccess) e = set_smem<true, true, S, 16>();
+    cudaError_t e = set_smem<false, true, S, 32, TX>();
+    if (e == cudaSuccess) e = set_smem<true, true, S, 32, TX>();
+    if (e == cudaSuccess) e = set_smem<true, true, S, 24, TX>();
+    if (e == cudaSuccess) e = set_smem<true, true, S, TY_WIDE, TX_WIDE>();
     return e;
 }
 

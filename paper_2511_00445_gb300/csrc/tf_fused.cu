@@ -18,13 +18,6 @@ struct CtxGeo {
     static constexpr int TYM = WIDE ? TY_WIDE : TY_DEFAULT;
 };
 
-// Column cut of the per-context tiles: gridDim.x tile columns of at most
-// TXM columns; when nx is a multiple of 4 every tile starts on a multiple of 4
-// (16-byte rows for the bulk copies).
-__host__ __device__ inline int tile_col(int k, int ntx, int nx) {
-    return nx % 4 == 0 ? 4 * (int)((long long)k * (nx / 4) / ntx) : (int)((long long)k * nx / ntx);
-}
-
 // One tile per CTA: tile (blockIdx.x, blockIdx.y) of instance blockIdx.z.
 // The ny rows are cut into gridDim.y tile rows of floor or ceil(ny / gridDim.y)
 // rows each (at most TYM; the host picks gridDim.y), the nx columns into

@@ -51,6 +51,13 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 
 constexpr int round4(int v) { return (v + 3) & ~3; }
 
+// First column of tile column k of ntx (k = ntx gives nx): when nx is a
+// multiple of 4 every tile starts on a multiple of 4 (16-byte rows for the
+// bulk copies); widths differ by at most 4.
+__host__ __device__ inline int tile_col(int k, int ntx, int nx) {
+    return nx % 4 == 0 ? 4 * (int)((long long)k * (nx / 4) / ntx) : (int)((long long)k * nx / ntx);
+}
+
 // TXM: the widest tile.  A warp row of a sub-step costs the same however
 // many of its 32 column pairs are used, so sub-step work per site falls with
 // the tile width; 40 columns plus the widest neighbourhood (2 x 11) plus the

@@ -93,7 +93,7 @@ def test_large_grid_matches_grid_stepped_alone(nx, ny, storage):
 
 
 def test_ensemble_autotune_steps_are_real_steps():
-    """Six candidates (tile heights 32/24/16, one or two CTAs per SM) each run
+    """Six candidates (tile shapes 32x32, 32x24 and 40x30, one or two CTAs per SM) each run
     real steps; the trajectory equals stepping alone."""
     spec = groups_spec()
     grp = make_groups(spec)
@@ -104,7 +104,7 @@ def test_ensemble_autotune_steps_are_real_steps():
     assert_same(grp, alone(spec, 1 + 12 + 3))
     cfg = ens.config()
     assert all(us > 0 for us in cfg["us_per_step"])
-    assert cfg["tile_y"] in (16, 24, 32) and cfg["ctas_per_sm"] in (1, 2)
+    assert cfg["tile_y"] in (24, 30, 32) and cfg["ctas_per_sm"] in (1, 2)
 
 
 def test_ensemble_member_reads_between_calls():
