@@ -11,7 +11,8 @@
 // LBM-only prologue and an FD-only epilogue restores the plain state
 // (f*, phi^{k+1}, Q^{k+1}) before any read.
 //
-// One CTA owns a TX x TY interior tile of one instance:
+// One CTA owns an interior tile of tw x th sites of one instance (tw <= 32 or
+// 40 columns, th <= 32 or 30 rows, fixed per launch by the host; see Geo):
 //  1. the phi, Q and u planes of the tile plus a halo are brought into shared
 //     memory by bulk copies (one per row segment, periodic wrap handled by
 //     splitting segments), and the population rows the tile will pull are
@@ -31,8 +32,8 @@
 
 namespace {
 
-constexpr int TX = 32;              // tile width of the ensemble kernel
-constexpr int TY_DEFAULT = 32;      // tile height of the per-context path (narrow tiles)
+constexpr int TX = 32;              // width of the narrow tiles (per-context and ensemble)
+constexpr int TY_DEFAULT = 32;      // height of the narrow per-context tiles
 // Wide per-context tiles for grids of several waves (see Geo): 40 x 30 fills
 // the 32 column-pair lanes at the widest sub-step in 108 KB of shared memory.
 constexpr int TX_WIDE = 40;
