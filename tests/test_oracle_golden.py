@@ -1,0 +1,128 @@
+"""The oracle against the parameter values the paper prints (Sec. III, IV).
+
+The paper prints no worked example with output values; what it prints is the
+parameter set of its runs.  `golden/sec3_parameters.txt` holds those values
+with their citations, and these tests check that the oracle's defaults, its
+BGK viscosity, its drag and the seeded initial condition agree with them.
+"""
+from __future__ import annotations
+
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import oracle.twofluid as O
+from paper_2511_00445_gb300 import inputs
+
+GOLDEN = Path(__file__).parent / "golden" / "sec3_parameters.txt"
+
+
+def _printed() -> dict:
+    vals = {}
+    for line in GOLDEN.read_text().splitlines():
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, value = line.split()[:2]
+        vals[name] = float(value)
+    return vals
+
+
+P = _printed()
+
+
+def _amp_sin(field, k, y):
+    """Amplitude of the sin(k y) component of a (ny, nx) field."""
+    return 2 * np.mean(field * np.sin(k * y))
+
+
+def test_fixture_is_complete():
+    for name in ("nx", "ny", "dt", "n_sub", "rho1", "rho2", "eta1", "eta2",
+                 "M_phi", "A", "kappa", "gamma", "Gamma_Q", "K", "phi0",
+                 "dphi0", "dQ"):
+        assert name in P, name
+
+
+def test_oracle_defaults_follow_printed_parameters():
+    """Mobility, double-well prefactor, gradient coefficient, rotational
+    diffusion, rest densities and the sub-step count are the printed ones.
+    (Drag, Frank constant, activity and tau are workload parameters.)"""
+    p = O.Params()
+    assert p.M == P["M_phi"]
+    assert p.A_ch == P["A"]
+    assert p.kappa == P["kappa"]
+    assert p.Gamma_Q == P["Gamma_Q"]
+    assert p.rho1 == P["rho1"] and p.rho2 == P["rho2"]
+    assert p.n_sub == int(P["n_sub"])
+
+
+def test_printed_interface_width():
+    """A = 0.05 and kappa = 0.1 give the tanh interface width
+    W = sqrt(2 kappa / A) = 2 lattice spacings (Eq. 2 with f = A phi^2 (1-phi)^2)."""
+    assert math.sqrt(2 * P["kappa"] / P["A"]) == pytest.approx(2.0, abs=1e-15)
+
+
+def test_printed_viscosity_sets_tau_two():
+    """eta = 0.5 at rho = 1 (Sec. III) is tau = 1/2 + 3 eta / rho = 2 in lattice
+    units; a shear wave run by the oracle at that tau decays at (eta/rho) k^2."""
+    eta, rho = P["eta1"], P["rho1"]
+    assert P["eta2"] == eta and P["rho2"] == rho
+    tau = 0.5 + 3 * eta / rho
+    assert tau == 2.0
+    N = 128   # long wave: the lattice's O(k^4) correction at tau = 2 stays below 0.3%
+    k = 2 * np.pi / N
+    p = O.Params().with_(nx=4, ny=N, tau1=tau, tau2=tau, rho1=rho, rho2=rho,
+                         lam=0.0, zeta=0.0, gamma=0.0)
+    y = np.arange(N)[:, None] * np.ones((1, 4))
+    u = np.stack([1e-4 * np.sin(k * y), np.zeros_like(y)])
+    Z = np.zeros_like(y)
+    s = O.state_from_fields(np.full_like(y, P["phi0"]), Z, Z, p, u, u)
+    a0 = _amp_sin(O.macro(s, p)["u1"][0], k, y)
+    T = 300
+    s = O.run(s, p, T)
+    a1 = _amp_sin(O.macro(s, p)["u1"][0], k, y)
+    nu = -math.log(a1 / a0) / T / (k * k)
+    assert nu == pytest.approx(eta / rho, rel=0.01)
+
+
+def test_printed_drag_relaxes_phase_difference():
+    """gamma = 0.1 at phi = phi0 = 0.5: with both fluids at rest but for a
+    uniform velocity of fluid 1, the implicit drag of Eq. (4)-(5) scales the
+    velocity difference by (1 - g)/(1 + g) per step, g = gamma phi (1 - phi),
+    while the sum is conserved."""
+    p = O.Params().with_(nx=4, ny=4, gamma=P["gamma"], lam=0.0, zeta=0.0)
+    Z = np.zeros((4, 4))
+    u1 = np.stack([np.full((4, 4), 1e-3), Z])
+    s = O.state_from_fields(np.full((4, 4), P["phi0"]), Z, Z, p, u1, 0 * u1)
+    mc = O.macro(s, p)
+    d0 = (mc["u1"] - mc["u2"])[0].mean()
+    s0 = (mc["u1"] + mc["u2"])[0].mean()
+    T = 20
+    s = O.run(s, p, T)
+    mc = O.macro(s, p)
+    d1 = (mc["u1"] - mc["u2"])[0].mean()
+    s1 = (mc["u1"] + mc["u2"])[0].mean()
+    g = P["gamma"] * P["phi0"] * (1 - P["phi0"])
+    assert d1 / d0 == pytest.approx(((1 - g) / (1 + g)) ** T, rel=1e-10)
+    assert s1 == pytest.approx(s0, rel=1e-12)
+
+
+def test_initial_concentration_has_printed_amplitude():
+    """phi = phi0 + dphi0 xi with xi uniform on [-1, 1] (Sec. III): on the
+    printed 256 x 256 domain the seeded draws stay inside phi0 +- dphi0, have
+    mean phi0 and standard deviation dphi0 / sqrt(3)."""
+    nx, ny = int(P["nx"]), int(P["ny"])
+    u_phi, u_theta = inputs.initial_draws(0, nx, ny)
+    phi = P["phi0"] + P["dphi0"] * (2 * u_phi - 1)
+    n = nx * ny
+    sd = P["dphi0"] / math.sqrt(3)
+    assert phi.min() >= P["phi0"] - P["dphi0"]
+    assert phi.max() < P["phi0"] + P["dphi0"]
+    assert abs(phi.mean() - P["phi0"]) < 4 * sd / math.sqrt(n)
+    assert phi.std() == pytest.approx(sd, rel=0.02)
+    # director angles cover [0, pi) uniformly
+    theta = np.pi * u_theta
+    assert theta.min() >= 0 and theta.max() < np.pi
+    assert abs(theta.mean() - np.pi / 2) < 4 * (np.pi / math.sqrt(12)) / math.sqrt(n)
