@@ -1,0 +1,82 @@
+"""Long runs: the statistics the paper reports from its simulations, from the
+GPU against the FP64 oracle over 2000 steps.
+
+Configuration: 64 x 64, seed 0, phi = 0.5 + U(-0.01, 0.01), director angle
+U(0, pi) with S = 0.01, zeta = 0.005, lambda = 0.7, K = 0.04, drag 0.01,
+tau = 1 (the correctness configuration).  Pointwise agreement is not expected
+to last through a chaotic run, so the bar is on statistics: the domain length
+L(t) (Sec. IV, Eq. 27) within 5% at every recorded time and on its mean over
+the second half (L_c), and the kinetic-energy spectrum (Eq. 22) averaged over
+the second half within 5% per shell, for the shells holding at least 1% of the
+energy.  The FP32 path and both 16-bit population storage modes are held to
+the same bar.
+"""
+import numpy as np
+import pytest
+
+from oracle import twofluid as O
+from paper_2511_00445_gb300 import _binding as B
+
+from helpers import oracle_params, read_state
+
+pytestmark = pytest.mark.gpu
+
+STEPS, EVERY = 2000, 100
+TOL_STAT = 0.05
+CFG = B.SolverParams(nx=64, ny=64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2511_00445_gb300 import build
+    build.build()
+
+
+def make(storage):
+    tf = B.TwoFluid(CFG.with_(storage=storage))
+    tf.init_fields(0, phi0=0.5, dphi=0.01, S0=0.01)
+    tf.sync()
+    return tf
+
+
+@pytest.fixture(scope="module")
+def oracle_record():
+    """L(t), E(k) and E at every 100 steps of the oracle's run, started
+    from the GPU's initial state read back exactly."""
+    tf = make(B.STORE_F32)
+    s = read_state(tf, 0)
+    op = oracle_params(CFG)
+    L, E = [], []
+    for _ in range(STEPS // EVERY):
+        s = O.run(s, op, EVERY)
+        L.append(O.length_scale(s.phi))
+        mc = O.macro(s, op)
+        E.append(O.energy_spectrum(O.mixture_velocity(s.phi, mc["u1"], mc["u2"]))[0])
+    return np.array(L), np.array(E)
+
+
+def gpu_record(storage):
+    tf = make(storage)
+    L, E = [], []
+    for _ in range(STEPS // EVERY):
+        tf.step(EVERY)
+        L.append(tf.length_scale(0))
+        E.append(tf.energy_spectrum(0)[0])
+    return np.array(L), np.array(E)
+
+
+@pytest.mark.parametrize("storage", [B.STORE_F32, B.STORE_F16, B.STORE_BF16],
+                         ids=["f32", "f16", "bf16"])
+def test_length_and_spectrum_statistics(storage, oracle_record):
+    Lw, Ew = oracle_record
+    L, E = gpu_record(storage)
+    assert np.all(np.isfinite(L)) and np.all(np.isfinite(E))
+    rel_L = np.abs(L / Lw - 1)
+    assert rel_L.max() <= TOL_STAT, rel_L
+    half = len(Lw) // 2
+    assert abs(L[half:].mean() / Lw[half:].mean() - 1) <= TOL_STAT
+    Em, Ewm = E[half:].mean(axis=0), Ew[half:].mean(axis=0)
+    big = Ewm >= 0.01 * Ewm.sum()
+    assert big.sum() >= 2
+    rel_E = np.abs(Em[big] / Ewm[big] - 1)
+    assert rel_E.max() <= TOL_STAT, rel_E
