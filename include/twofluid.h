@@ -239,7 +239,14 @@ size_t tf_state_bytes(const tf_ctx* ctx);
 
 /* End-to-end entry point with HOST buffers: copy the raw state from
  * `h_in` (ideally pinned; NULL keeps the device state), advance n steps,
- * copy the raw state to `h_out` (NULL skips), and synchronise. */
+ * copy the raw state to `h_out` (NULL skips), and synchronise.  Both buffers
+ * hold tf_state_bytes(ctx) bytes.  On a batch of several instances with
+ * n_sub = 5 the call is pipelined per instance: the upload of instance b + 1
+ * and the download of instance b - 1 overlap the steps of instance b, on
+ * streams the context owns (forked from and joined back to its stream).  An
+ * instance's piece of `h_in` is read before its piece of `h_out` is written,
+ * so the two may be one buffer.  Results are bitwise those of the
+ * unpipelined sequence. */
 int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out);
 
 /* Checkpoint / resume of the whole context (header + raw state), bitwise. */

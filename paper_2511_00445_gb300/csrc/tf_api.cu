@@ -191,9 +191,27 @@ int tf_create(const tf_params* params, int batch, void* d_workspace, size_t work
     return TF_OK;
 }
 
+// Streams and events of the host-buffer pipeline (see advance_pipelined).
+static void release_pipeline(tf_ctx* ctx) {
+    for (auto& g : ctx->host_graphs) cudaGraphExecDestroy(g.exec);
+    ctx->host_graphs.clear();
+    for (cudaStream_t s : ctx->lanes) cudaStreamSynchronize(s);
+    if (ctx->xfer_in) cudaStreamSynchronize(ctx->xfer_in);
+    if (ctx->xfer_out) cudaStreamSynchronize(ctx->xfer_out);
+    for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
+    for (cudaStream_t s : ctx->lanes) cudaStreamDestroy(s);
+    if (ctx->xfer_in) cudaStreamDestroy(ctx->xfer_in);
+    if (ctx->xfer_out) cudaStreamDestroy(ctx->xfer_out);
+    if (ctx->xfer_cap) cudaStreamDestroy(ctx->xfer_cap);
+    ctx->events.clear();
+    ctx->lanes.clear();
+    ctx->xfer_in = ctx->xfer_out = ctx->xfer_cap = nullptr;
+}
+
 int tf_destroy(tf_ctx* ctx) {
     if (!ctx) return TF_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    release_pipeline(ctx);
     delete ctx;
     return e == cudaSuccess ? TF_OK : TF_ERR_CUDA;
 }
@@ -484,9 +502,168 @@ static int copy_state(tf_ctx* ctx, void* host, bool to_host) {
     return TF_OK;
 }
 
+// Compute lanes of the pipeline: instances are dealt to them in turn, so that
+// the steps of several instances can run at once when they outlast the copies.
+constexpr int kLanes = 4;
+
+static cudaError_t make_pipeline(tf_ctx* ctx) {
+    if (ctx->xfer_in) return cudaSuccess;
+    const int lanes = ctx->batch < kLanes ? ctx->batch : kLanes;
+    const int events = 2 * ctx->batch + lanes + 3;
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->xfer_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->xfer_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->xfer_cap, cudaStreamNonBlocking);
+    for (int k = 0; k < lanes && e == cudaSuccess; ++k) {
+        cudaStream_t s = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) ctx->lanes.push_back(s);
+    }
+    for (int k = 0; k < events && e == cudaSuccess; ++k) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) ctx->events.push_back(ev);
+    }
+    if (e != cudaSuccess) release_pipeline(ctx);
+    return e;
+}
+
+#define PCK(x)                                  \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
+
+// Host-buffer advance of a batch on the fused path, pipelined per instance.
+// Instance b's upload, steps and download are queued on their own, so the
+// upload of instance b + 1 and the download of instance b - 1 overlap the
+// steps of instance b.  Uploads queue on one stream and downloads on another,
+// both in instance order, so each instance's copies get the whole bandwidth of
+// their direction; the steps of instance b run on lane b mod kLanes once its
+// upload is done.  All side streams fork from and join back to `origin`.
+// Every instance moves through the same buffer cursors, so the cursors
+// afterwards (*end) are those of any one instance.  The raw state is
+// [f: B x 18 x N][phi: B x N][Q: B x 2 x N] on both sides, so an instance is
+// three contiguous pieces.
+static cudaError_t enqueue_pipeline(tf_ctx* ctx, cudaStream_t origin, const void* h_in, int64_t n,
+                                    void* h_out, FusedCursor* end) {
+    const size_t N = (size_t)ctx->N, B = (size_t)ctx->batch;
+    const size_t pf = 18 * N * tf_pop_bytes(ctx->storage), pp = N * sizeof(float), pq = 2 * pp;
+    const size_t off[3] = {0, B * pf, B * pf + B * pp}, len[3] = {pf, pp, pq};
+    const int L = (int)ctx->lanes.size();
+    cudaEvent_t* ev_in = ctx->events.data();               // [B]
+    cudaEvent_t* ev_done = ev_in + B;                     // [B]
+    cudaEvent_t* ev_join = ev_done + B;                   // [L + 2]
+    cudaEvent_t ev_fork = ev_join[L + 2];
+    PCK(cudaEventRecord(ev_fork, origin));
+    PCK(cudaStreamWaitEvent(ctx->xfer_in, ev_fork, 0));
+    PCK(cudaStreamWaitEvent(ctx->xfer_out, ev_fork, 0));
+    for (int k = 0; k < L; ++k) PCK(cudaStreamWaitEvent(ctx->lanes[k], ev_fork, 0));
+    const FusedCursor start{ctx->fcur, ctx->pcur, ctx->ucur, h_in ? false : ctx->fd_pending};
+    *end = start;
+    for (size_t b = 0; b < B; ++b) {
+        cudaStream_t lane = ctx->lanes[b % L];
+        if (h_in) {
+            char* dev[3] = {(char*)ctx->d.f[start.fcur], (char*)ctx->d.phi[start.pcur],
+                            (char*)ctx->d.Q[start.pcur]};
+            for (int k = 0; k < 3; ++k)
+                PCK(cudaMemcpyAsync(dev[k] + b * len[k], (const char*)h_in + off[k] + b * len[k], len[k],
+                                    cudaMemcpyHostToDevice, ctx->xfer_in));
+            PCK(cudaEventRecord(ev_in[b], ctx->xfer_in));
+            PCK(cudaStreamWaitEvent(lane, ev_in[b], 0));
+        }
+        FusedCursor cur = start;
+        PCK(tf_fused_span(ctx, (int)b, 1, n, h_out != nullptr, lane, &cur));
+        *end = cur;
+        if (h_out) {
+            PCK(cudaEventRecord(ev_done[b], lane));
+            PCK(cudaStreamWaitEvent(ctx->xfer_out, ev_done[b], 0));
+            const char* dev[3] = {(const char*)ctx->d.f[cur.fcur], (const char*)ctx->d.phi[cur.pcur],
+                                  (const char*)ctx->d.Q[cur.pcur]};
+            for (int k = 0; k < 3; ++k)
+                PCK(cudaMemcpyAsync((char*)h_out + off[k] + b * len[k], dev[k] + b * len[k], len[k],
+                                    cudaMemcpyDeviceToHost, ctx->xfer_out));
+        }
+    }
+    for (int k = 0; k < L; ++k) {
+        PCK(cudaEventRecord(ev_join[k], ctx->lanes[k]));
+        PCK(cudaStreamWaitEvent(origin, ev_join[k], 0));
+    }
+    PCK(cudaEventRecord(ev_join[L], ctx->xfer_out));
+    PCK(cudaStreamWaitEvent(origin, ev_join[L], 0));
+    PCK(cudaEventRecord(ev_join[L + 1], ctx->xfer_in));
+    PCK(cudaStreamWaitEvent(origin, ev_join[L + 1], 0));
+    return cudaSuccess;
+}
+
+static bool pinned_or_null(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+// The pipeline is some fifty stream operations, whose enqueueing would set the
+// pace of a one-step call.  For pinned buffers it is captured once (on the
+// private capture stream) into a CUDA graph per (buffers, n, cursors) and
+// replayed on the context's stream; other host memory is enqueued directly.
+constexpr size_t kHostGraphs = 4;
+
+static int advance_pipelined(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
+    TF_CK(ctx, make_pipeline(ctx));
+    FusedCursor probe{ctx->fcur, ctx->pcur, ctx->ucur, ctx->fd_pending};
+    TF_CK(ctx, tf_fused_span(ctx, 0, 1, 0, false, ctx->stream, &probe));   // plans the tiles only
+    FusedCursor end{};
+    const bool pending = h_in ? false : ctx->fd_pending;
+    if (pinned_or_null(h_in) && pinned_or_null(h_out)) {
+        tf_ctx::HostGraph* g = nullptr;
+        for (auto& c : ctx->host_graphs)
+            if (c.in == h_in && c.out == h_out && c.n == n && c.fcur == ctx->fcur && c.pcur == ctx->pcur &&
+                c.ucur == ctx->ucur && c.fd_pending == pending)
+                g = &c;
+        if (!g) {
+            const int64_t launches0 = ctx->launches;
+            TF_CK(ctx, cudaStreamBeginCapture(ctx->xfer_cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_pipeline(ctx, ctx->xfer_cap, h_in, n, h_out, &end);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(ctx->xfer_cap, &graph);
+            if (e == cudaSuccess) e = e2;
+            cudaGraphExec_t exec = nullptr;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            TF_CK(ctx, e);
+            if (ctx->host_graphs.size() == kHostGraphs) {
+                cudaGraphExecDestroy(ctx->host_graphs.front().exec);
+                ctx->host_graphs.erase(ctx->host_graphs.begin());
+            }
+            ctx->host_graphs.push_back({h_in, h_out, n, ctx->fcur, ctx->pcur, ctx->ucur, pending, exec,
+                                        end.fcur, end.pcur, end.ucur, end.fd_pending,
+                                        ctx->launches - launches0});
+            g = &ctx->host_graphs.back();
+            ctx->launches = launches0;
+        }
+        TF_CK(ctx, cudaGraphLaunch(g->exec, ctx->stream));
+        end = {g->fcur_end, g->pcur_end, g->ucur_end, g->fd_pending_end};
+        ctx->launches += g->launches;
+    } else {
+        TF_CK(ctx, enqueue_pipeline(ctx, ctx->stream, h_in, n, h_out, &end));
+    }
+    ctx->fcur = end.fcur;
+    ctx->pcur = end.pcur;
+    ctx->ucur = end.ucur;
+    ctx->fd_pending = end.fd_pending;
+    ctx->steps += n;
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
 int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
     if (!ctx) return TF_ERR_ARG;
     if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
+    if (ctx->batch > 1 && (h_in || h_out) && tf_fused_supported(ctx))
+        return advance_pipelined(ctx, h_in, n, h_out);
     int rc;
     if (h_in) {
         ctx->fd_pending = false;  // the uploaded raw state is a plain state

@@ -57,35 +57,72 @@ cudaError_t configure() {
     return e;
 }
 
+// Launch target: instances [inst0, inst0 + count) on `stream`, reading and
+// writing the buffers the cursors in `cur` name.  The kernels address
+// instance blockIdx.z from their base pointers, so a span is the same kernel
+// on bases offset by inst0.
+struct Span {
+    int inst0, count, tile_rows;
+    cudaStream_t stream;
+    FusedCursor* cur;
+};
+
 template <bool DO_FD, bool DO_LBM, class S, bool WIDE>
-void launch_as(tf_ctx* ctx) {
+void launch_as(tf_ctx* ctx, const Span& sp) {
     using G = Geo<DO_FD, DO_LBM, CtxGeo<WIDE>::TYM, CtxGeo<WIDE>::TXM>;
     using T = typename S::T;
     DevBuffers& d = ctx->d;
-    const dim3 grid(ctx->tile_cols, ctx->tile_rows, ctx->batch);
-    const int fc = ctx->fcur, pc = ctx->pcur, uc = ctx->ucur;
-    const TileArgs<S> a{static_cast<const T*>(d.f[fc]), static_cast<T*>(d.f[fc ^ 1]),
-                        d.phi[pc], d.phi[pc ^ 1], d.Q[pc], d.Q[pc ^ 1], d.u[uc], d.u[uc ^ 1],
-                        d.prm, ctx->nx, ctx->ny, d.flags};
-    k_fused<DO_FD, DO_LBM, S, WIDE><<<grid, NT, G::SMEM, ctx->stream>>>(a);
+    const dim3 grid(ctx->tile_cols, sp.tile_rows, sp.count);
+    const int fc = sp.cur->fcur, pc = sp.cur->pcur, uc = sp.cur->ucur;
+    const long long N = ctx->N, b0 = sp.inst0;
+    const TileArgs<S> a{static_cast<const T*>(d.f[fc]) + b0 * 18 * N, static_cast<T*>(d.f[fc ^ 1]) + b0 * 18 * N,
+                        d.phi[pc] + b0 * N, d.phi[pc ^ 1] + b0 * N, d.Q[pc] + b0 * 2 * N,
+                        d.Q[pc ^ 1] + b0 * 2 * N, d.u[uc] + b0 * 4 * N, d.u[uc ^ 1] + b0 * 4 * N,
+                        d.prm + b0, ctx->nx, ctx->ny, d.flags};
+    k_fused<DO_FD, DO_LBM, S, WIDE><<<grid, NT, G::SMEM, sp.stream>>>(a);
 }
 
 template <bool DO_FD, bool DO_LBM>
-cudaError_t launch(tf_ctx* ctx) {
+cudaError_t launch(tf_ctx* ctx, const Span& sp) {
     const bool w = ctx->wide_tiles;
     if (ctx->storage == TF_STORE_F16)
-        w ? launch_as<DO_FD, DO_LBM, PopF16, true>(ctx) : launch_as<DO_FD, DO_LBM, PopF16, false>(ctx);
+        w ? launch_as<DO_FD, DO_LBM, PopF16, true>(ctx, sp) : launch_as<DO_FD, DO_LBM, PopF16, false>(ctx, sp);
     else if (ctx->storage == TF_STORE_BF16)
-        w ? launch_as<DO_FD, DO_LBM, PopBF16, true>(ctx) : launch_as<DO_FD, DO_LBM, PopBF16, false>(ctx);
+        w ? launch_as<DO_FD, DO_LBM, PopBF16, true>(ctx, sp) : launch_as<DO_FD, DO_LBM, PopBF16, false>(ctx, sp);
     else
-        w ? launch_as<DO_FD, DO_LBM, PopF32, true>(ctx) : launch_as<DO_FD, DO_LBM, PopF32, false>(ctx);
+        w ? launch_as<DO_FD, DO_LBM, PopF32, true>(ctx, sp) : launch_as<DO_FD, DO_LBM, PopF32, false>(ctx, sp);
     if (DO_LBM) {
-        ctx->fcur ^= 1;
-        ctx->ucur ^= 1;
+        sp.cur->fcur ^= 1;
+        sp.cur->ucur ^= 1;
     }
-    if (DO_FD) ctx->pcur ^= 1;
+    if (DO_FD) sp.cur->pcur ^= 1;
     ctx->launches += 1;
     return cudaGetLastError();
+}
+
+// n steps (LBM-only first when nothing is pending), then the pending
+// sub-steps when `flush`.
+cudaError_t run(tf_ctx* ctx, const Span& sp, int64_t n, bool flush) {
+    for (int64_t it = 0; it < n; ++it) {
+        cudaError_t e = sp.cur->fd_pending ? launch<true, true>(ctx, sp) : launch<false, true>(ctx, sp);
+        if (e != cudaSuccess) return e;
+        sp.cur->fd_pending = true;
+    }
+    if (flush && sp.cur->fd_pending) {
+        cudaError_t e = launch<true, false>(ctx, sp);
+        sp.cur->fd_pending = false;
+        return e;
+    }
+    return cudaSuccess;
+}
+
+FusedCursor cursor_of(const tf_ctx* ctx) { return {ctx->fcur, ctx->pcur, ctx->ucur, ctx->fd_pending}; }
+
+void set_cursor(tf_ctx* ctx, const FusedCursor& c) {
+    ctx->fcur = c.fcur;
+    ctx->pcur = c.pcur;
+    ctx->ucur = c.ucur;
+    ctx->fd_pending = c.fd_pending;
 }
 
 }  // namespace
@@ -140,22 +177,31 @@ cudaError_t plan_tile_rows(tf_ctx* ctx) {
 }
 
 cudaError_t tf_fused_steps(tf_ctx* ctx, int64_t n) {
-    cudaError_t pe = plan_tile_rows(ctx);
-    if (pe != cudaSuccess) return pe;
-    for (int64_t it = 0; it < n; ++it) {
-        cudaError_t e = ctx->fd_pending ? launch<true, true>(ctx) : launch<false, true>(ctx);
-        if (e != cudaSuccess) return e;
-        ctx->fd_pending = true;
-        ctx->steps += 1;
-    }
-    return cudaSuccess;
+    cudaError_t e = plan_tile_rows(ctx);
+    if (e != cudaSuccess) return e;
+    FusedCursor c = cursor_of(ctx);
+    e = run(ctx, Span{0, ctx->batch, ctx->tile_rows, ctx->stream, &c}, n, false);
+    set_cursor(ctx, c);
+    if (e == cudaSuccess) ctx->steps += n;
+    return e;
 }
 
 cudaError_t tf_fused_flush(tf_ctx* ctx) {
     if (!ctx->fd_pending) return cudaSuccess;
-    cudaError_t pe = plan_tile_rows(ctx);
-    if (pe != cudaSuccess) return pe;
-    cudaError_t e = launch<true, false>(ctx);
-    ctx->fd_pending = false;
+    cudaError_t e = plan_tile_rows(ctx);
+    if (e != cudaSuccess) return e;
+    FusedCursor c = cursor_of(ctx);
+    e = run(ctx, Span{0, ctx->batch, ctx->tile_rows, ctx->stream, &c}, 0, true);
+    set_cursor(ctx, c);
     return e;
+}
+
+cudaError_t tf_fused_span(tf_ctx* ctx, int inst0, int count, int64_t n, bool flush,
+                          cudaStream_t stream, FusedCursor* cur) {
+    cudaError_t e = plan_tile_rows(ctx);
+    if (e != cudaSuccess) return e;
+    // The batch's tile plan: spans of different instances, launched on
+    // different streams, then share the resident CTA slots as one batched
+    // launch would.
+    return run(ctx, Span{inst0, count, ctx->tile_rows, stream, cur}, n, flush);
 }

@@ -140,6 +140,26 @@ struct tf_ctx {
     int red_blocks = 0;
     int shell_blocks = 0;
     std::string last_error;
+    // Host-buffer pipeline of a batch (tf_advance_host), created on first use
+    // and released by tf_destroy: one stream for uploads, one for downloads,
+    // compute lanes, their events, and a private stream to capture on (the
+    // context's stream may be the legacy default stream, which cannot be).
+    cudaStream_t xfer_in = nullptr, xfer_out = nullptr, xfer_cap = nullptr;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> events;
+    // Captured pipelines for pinned buffers, keyed by what they bake in.
+    struct HostGraph {
+        const void* in;
+        void* out;
+        int64_t n;
+        int fcur, pcur, ucur;
+        bool fd_pending;
+        cudaGraphExec_t exec;
+        int fcur_end, pcur_end, ucur_end;
+        bool fd_pending_end;
+        int64_t launches;
+    };
+    std::vector<HostGraph> host_graphs;
 };
 
 // Workspace carving (tf_api.cu).
@@ -161,6 +181,17 @@ bool tf_fused_supported(const tf_ctx* ctx);
 cudaError_t tf_fused_steps(tf_ctx* ctx, int64_t n);
 cudaError_t tf_fused_flush(tf_ctx* ctx);
 cudaError_t tf_configure_fused_kernels();
+// Buffer cursors of the fused path (the fields of tf_ctx of the same names).
+struct FusedCursor {
+    int fcur, pcur, ucur;
+    bool fd_pending;
+};
+// Fused launches of instances [inst0, inst0 + count) only, on `stream`: n
+// steps, then the pending sub-steps when `flush`.  The launches start from the
+// cursors in *cur and advance them; the context's own cursors and step count
+// are left alone (every instance of a context moves through the same buffers).
+cudaError_t tf_fused_span(tf_ctx* ctx, int inst0, int count, int64_t n, bool flush,
+                          cudaStream_t stream, FusedCursor* cur);
 // Evaluate mu, the fluid-1 stress, the Guo velocities, densities and the
 // non-drag force sum of the current state into d.mu, d.tau and macro_out
 // ([B][8][N]: u1x u1y u2x u2y rho1 rho2 (G1+G2)x (G1+G2)y).

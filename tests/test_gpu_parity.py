@@ -302,6 +302,47 @@ def test_advance_host_equals_device_steps():
     assert torch.equal(h_in, h_out)
 
 
+@pytest.mark.parametrize("storage", [B.STORE_F32, B.STORE_F16], ids=["f32", "f16"])
+def test_advance_host_batch_pipeline_bitwise(storage):
+    """On a batch the host-buffer entry point runs pipelined per instance
+    (the uploads, steps and downloads of different instances overlap on the
+    context's own streams; five instances wrap around its four compute
+    lanes; pinned buffers replay a captured graph, pageable ones are enqueued
+    directly).  Every use of it gives bitwise the state of plain device steps:
+    a download that first completes pending sub-steps, an upload alone from
+    pageable memory, an upload and a download through one buffer, and an
+    upload followed by steps that leave sub-steps pending."""
+    import torch
+    ps = [CFG0.with_(nx=40, ny=36, zeta=z, storage=storage) for z in (0.0, 0.002, 0.005, 0.01, 0.02)]
+    fields = [B.FIELD_PHI, B.FIELD_QXX, B.FIELD_QXY, B.FIELD_U1X, B.FIELD_U2Y] + \
+             [B.FIELD_F1 + i for i in range(9)] + [B.FIELD_F2 + i for i in (0, 3, 8)]
+
+    def same(x, y):
+        for inst in range(len(ps)):
+            for fld in fields:
+                assert np.array_equal(x.read_field(inst, fld), y.read_field(inst, fld)), (inst, fld)
+
+    a, b = make(ps, seed=3), make(ps, seed=3)
+    h = torch.empty(a.state_bytes(), dtype=torch.uint8, pin_memory=True)
+    a.step(4)
+    b.step(4)
+    a.advance_host(None, 3, h.data_ptr())          # pending sub-steps, 3 steps, download
+    b.step(3)
+    same(a, b)
+    c = B.TwoFluid(ps)
+    hp = h.numpy().copy()                          # pageable memory: enqueued, not captured
+    c.advance_host(hp.ctypes.data, 0, None)        # upload only
+    same(c, b)
+    a.advance_host(h.data_ptr(), 2, h.data_ptr())  # one buffer in and out
+    b.step(2)
+    same(a, b)
+    d = B.TwoFluid(ps)
+    d.advance_host(h.data_ptr(), 5, None)          # upload, steps, sub-steps left pending
+    b.step(5)
+    same(d, b)
+    assert a.step_count() == 9 and b.step_count() == 14 and d.step_count() == 5
+
+
 def test_argument_errors():
     tf = make(CFG0.with_(nx=8, ny=8))
     for call in (lambda: tf.read_field(1, B.FIELD_PHI), lambda: tf.read_field(0, 99),
