@@ -15,19 +15,22 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 constexpr int EB = 256;             // threads of the element-wise kernels
+constexpr int kHeadBlocks = 608;    // pixel ranges of the head's parameter gradient
 constexpr int CIN = TF_SUR_IN, COUT = TF_SUR_OUT;
 
 __device__ __forceinline__ int wrap_i(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // ------------------------------------------------------------ GEMM operations
-// Weight gradient: dW[o][tap][c] += sum_p dz[p][o] in[p + d(tap)][c] over a
-// split of the pixels, from channel-major copies dzT[o][p] and inT[c][p].
+// Weight gradient: dW[o][tap][c] = sum_p dz[p][o] in[p + d(tap)][c], from
+// channel-major copies dzT[o][p] and inT[c][p].  Split z of the pixels writes
+// its partial sums to part[z][M][N]; k_sum_splits then adds the splits in
+// order, so training is reproducible bit for bit (no floating-point atomics).
 struct ConvBwdW {
     int M, N, K;         // M = cout, N = 9 cin, K = pixels
     int* err;
     const bf16* dzT;
     const bf16* inT;
-    float* dw;
+    float* part;
     int H, W, cin;
     __device__ uint4 a_chunk(int m, int k8) const {
         const int k = k8 * 8;
@@ -48,14 +51,23 @@ struct ConvBwdW {
         return *reinterpret_cast<const uint4*>(v);
     }
     __device__ void epilogue(int m, int n0, const float (&v)[16]) const {
+        float* dst = part + ((size_t)blockIdx.z * M + m) * N + n0;
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-            if (n0 + j < N) atomicAdd(dw + (size_t)m * N + n0 + j, v[j]);
+            if (n0 + j < N) dst[j] = v[j];
     }
 };
 
+// Splits the pixel range of a weight-gradient GEMM is cut into: about two
+// CTAs per SM of 152 over the output tiles (an upper bound; run_gemm may use
+// fewer, never more).
+inline int wgrad_splits(int M, int N) {
+    const int tiles = ((M + 127) / 128) * ((N + 63) / 64);
+    return (304 + tiles - 1) / tiles;
+}
+
 template <int BN, class Op>
-cudaError_t run_gemm(const Op& op, int splits, cudaStream_t st) {
+cudaError_t run_gemm(const Op& op, int splits, cudaStream_t st, int* used_splits) {
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(tcg::k_gemm<BN, Op>,
@@ -71,6 +83,7 @@ cudaError_t run_gemm(const Op& op, int splits, cudaStream_t st) {
     splits = (chunks + per - 1) / per;
     const dim3 grid((op.M + tcg::BM - 1) / tcg::BM, (op.N + BN - 1) / BN, splits);
     tcg::k_gemm<BN, Op><<<grid, tcg::NTHREADS, tcg::smem_bytes<BN>(), st>>>(op, per);
+    *used_splits = splits;
     return cudaGetLastError();
 }
 
@@ -188,11 +201,11 @@ size_t wtile_bytes(int nout, int cs, int bn = 32) {
 }
 
 template <class Op>
-cudaError_t gemm(const Op& op, int splits, cudaStream_t st) {
-    if (op.N >= 128) return run_gemm<128>(op, splits, st);
-    if (op.N >= 64) return run_gemm<64>(op, splits, st);
-    if (op.N >= 32) return run_gemm<32>(op, splits, st);
-    return run_gemm<16>(op, splits, st);
+cudaError_t gemm(const Op& op, int splits, cudaStream_t st, int* used_splits) {
+    if (op.N >= 128) return run_gemm<128>(op, splits, st, used_splits);
+    if (op.N >= 64) return run_gemm<64>(op, splits, st, used_splits);
+    if (op.N >= 32) return run_gemm<32>(op, splits, st, used_splits);
+    return run_gemm<16>(op, splits, st, used_splits);
 }
 
 // ------------------------------------------------------ element-wise kernels
@@ -378,34 +391,47 @@ __global__ void k_loss(const float* __restrict__ pred, const float* __restrict__
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// Head backward: dh[p][c] += sum_o Wh[o][c] dpred[p][o]; dWh, dbh by block sums.
+// Head backward, input part: dh[p][c] += sum_o Wh[o][c] dpred[p][o].
 __global__ void k_head_bwd(const bf16* __restrict__ h, const float* __restrict__ dpred,
-                           const float* __restrict__ Wh, float* __restrict__ dh,
-                           float* __restrict__ dWh, float* __restrict__ dbh, long long P, int C) {
-    extern __shared__ float acc[];   // COUT * C + COUT
-    for (int k = threadIdx.x; k < COUT * C + COUT; k += EB) acc[k] = 0.f;
-    __syncthreads();
+                           const float* __restrict__ Wh, float* __restrict__ dh, long long P, int C) {
     for (long long p = (long long)blockIdx.x * EB + threadIdx.x; p < P; p += (long long)gridDim.x * EB) {
         float g[COUT];
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) {
-            g[o] = dpred[p * COUT + o];
-            atomicAdd(&acc[COUT * C + o], g[o]);
-        }
+        for (int o = 0; o < COUT; ++o) g[o] = dpred[p * COUT + o];
         for (int c = 0; c < C; ++c) {
-            const float v = __bfloat162float(h[p * C + c]);
             float s = 0.f;
 #pragma unroll
-            for (int o = 0; o < COUT; ++o) {
-                s += Wh[o * C + c] * g[o];
-                atomicAdd(&acc[o * C + c], g[o] * v);
-            }
+            for (int o = 0; o < COUT; ++o) s += Wh[o * C + c] * g[o];
             dh[p * C + c] += s;
         }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < COUT * C; k += EB) atomicAdd(dWh + k, acc[k]);
-    for (int k = threadIdx.x; k < COUT; k += EB) atomicAdd(dbh + k, acc[COUT * C + k]);
+}
+
+// Head backward, parameter part: block b sums pixels [b P / nb, (b + 1) P / nb)
+// in order; thread k owns entry k of [dWh (COUT x C) | dbh (COUT)]:
+// dWh[o][c] = sum_p dpred[p][o] h[p][c], dbh[o] = sum_p dpred[p][o].  Each
+// block writes its partial row part[b][.]; k_head_sum adds the rows in order.
+__global__ void k_head_wgrad(const bf16* __restrict__ h, const float* __restrict__ dpred,
+                             float* __restrict__ part, long long P, int C) {
+    const int nk = COUT * C + COUT;
+    const long long p0 = (long long)blockIdx.x * P / gridDim.x, p1 = (long long)(blockIdx.x + 1) * P / gridDim.x;
+    for (int k = threadIdx.x; k < nk; k += EB) {
+        const bool w = k < COUT * C;
+        const int o = w ? k / C : k - COUT * C, c = w ? k - o * C : 0;
+        float s = 0.f;
+        for (long long p = p0; p < p1; ++p)
+            s += dpred[p * COUT + o] * (w ? __bfloat162float(h[p * C + c]) : 1.f);
+        part[(size_t)blockIdx.x * nk + k] = s;
+    }
+}
+
+// dst[i] += sum_z part[z][i] for z = 0 .. nz - 1, in that order.
+__global__ void k_sum_splits(const float* __restrict__ part, int nz, long long n, float* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * EB + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int z = 0; z < nz; ++z) s += part[(size_t)z * n + i];
+    dst[i] += s;
 }
 
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
@@ -583,7 +609,7 @@ struct tf_surrogate {
     size_t p_off = 0, g_off = 0, m_off = 0, v_off = 0, wbf_off = 0, act_off = 0, grad_off = 0;
     size_t dz_off = 0, dzT_off = 0, inT_off = 0, pred_off = 0, tgt_off = 0, dpred_off = 0;
     size_t data_off = 0, zeta_off = 0, idx_off = 0, part_off = 0, err_off = 0;
-    size_t raw_off = 0, total = 0;
+    size_t raw_off = 0, wpart_off = 0, hpart_off = 0, total = 0;
     long long max_cp = 0;        // largest pixels x channels of any tensor at max_batch
     std::vector<float> zeta;     // per pair
     Norm norm{};
@@ -709,6 +735,13 @@ size_t plan(tf_surrogate* s) {
     s->zeta_off = take((size_t)(c.max_pairs + B) * 4);
     s->idx_off = take((size_t)B * 4);
     s->part_off = take(1024 * 28 * 8);
+    size_t wpart = 0;                                          // weight-gradient split partials
+    for (const Conv& cv : s->convs) {
+        const size_t mn = (size_t)cv.cout * 9 * cv.cin;
+        wpart = std::max(wpart, (size_t)wgrad_splits(cv.cout, 9 * cv.cin) * mn);
+    }
+    s->wpart_off = take(wpart * 4);
+    s->hpart_off = take((size_t)kHeadBlocks * (COUT * c.base_channels + COUT) * 4);
     s->err_off = take(64);
     s->total = off;
     return off;
@@ -784,9 +817,13 @@ cudaError_t backward_pass(tf_surrogate* s, int B, double* loss) {
     k_loss<<<lb, EB, 0, st>>>(s->at<float>(s->pred_off), s->at<float>(s->tgt_off),
                               s->at<float>(s->dpred_off), n, s->at<double>(s->part_off));
     const Tensor& d0 = s->tensors[s->dec0_t];
-    k_head_bwd<<<152, EB, (COUT * d0.C + COUT) * sizeof(float), st>>>(
-        s->at<bf16>(d0.act), s->at<float>(s->dpred_off), P + s->head_w, s->at<float>(d0.grad),
-        G + s->head_w, G + s->head_b, P0, d0.C);
+    k_head_bwd<<<152, EB, 0, st>>>(s->at<bf16>(d0.act), s->at<float>(s->dpred_off), P + s->head_w,
+                                   s->at<float>(d0.grad), P0, d0.C);
+    const long long nhead = (long long)COUT * d0.C + COUT;     // [dWh | dbh] at G + head_w
+    k_head_wgrad<<<kHeadBlocks, EB, 0, st>>>(s->at<bf16>(d0.act), s->at<float>(s->dpred_off),
+                                            s->at<float>(s->hpart_off), P0, d0.C);
+    k_sum_splits<<<blocks(nhead), EB, 0, st>>>(s->at<float>(s->hpart_off), kHeadBlocks, nhead,
+                                               G + s->head_w);
     for (int k = (int)s->ops.size() - 1; k >= 0; --k) {
         const Op& op = s->ops[k];
         if (op.kind == OP_CONV) {
@@ -808,13 +845,15 @@ cudaError_t backward_pass(tf_surrogate* s, int B, double* loss) {
             gw.err = err;
             gw.dzT = dzT;
             gw.inT = inT;
-            gw.dw = G + cv.w_off;
+            gw.part = s->at<float>(s->wpart_off);
             gw.H = H;
             gw.W = W;
             gw.cin = cv.cin;
-            const int tiles = ((gw.M + 127) / 128) * ((gw.N + 63) / 64);
-            e = gemm(gw, (304 + tiles - 1) / tiles, st);
+            int used = 0;
+            e = gemm(gw, wgrad_splits(gw.M, gw.N), st, &used);
             if (e != cudaSuccess) return e;
+            const long long mn = (long long)gw.M * gw.N;
+            k_sum_splits<<<blocks(mn), EB, 0, st>>>(gw.part, used, mn, G + cv.w_off);
             k_bias_grad<<<cv.cout, EB, 0, st>>>(dzT, Pp, G + cv.b_off);
             if (cv.in_t != s->x_t) {
                 const tcg::ConvRowArgs gd{dz, s->at<bf16>(cv.wt), nullptr, nullptr,
