@@ -115,8 +115,69 @@ def reduce_max(value: float, world: int, device=None) -> float:
 
 
 # -------------------------------------------------------------- clocks
+class NvmlClocks:
+    """SM clock and clock-event reasons read in-process through the driver's
+    NVML library every 2 ms while the timed region runs (read-only queries).
+    Raises OSError when NVML cannot be used; ClockSampler then falls back to
+    nvidia-smi."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, cuda_index: int):
+        import ctypes
+        self.ct = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.lib = lib
+        idx = cuda_index
+        try:
+            import torch
+            idx = torch.cuda._get_nvml_device_index(cuda_index)
+        except Exception:
+            pass
+        self.h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples = []
+        self.stop_flag = threading.Event()
+
+    def _clock(self, fn):
+        v = self.ct.c_uint()
+        return v.value if fn(self.h, self.ct.c_int(1), self.ct.byref(v)) == 0 else None   # 1: SM
+
+    def _loop(self):
+        while not self.stop_flag.is_set():
+            mhz = self._clock(self.lib.nvmlDeviceGetClockInfo)
+            r = self.ct.c_ulonglong()
+            ok = self.get_reasons(self.h, self.ct.byref(r)) == 0
+            if mhz is not None and ok:
+                self.samples.append((mhz, r.value))
+            self.stop_flag.wait(0.002)
+
+    def start(self):
+        self.samples = []
+        self.stop_flag.clear()
+        self.th = threading.Thread(target=self._loop, daemon=True)
+        self.th.start()
+
+    def stop(self):
+        self.stop_flag.set()
+        self.th.join(timeout=2)
+        smax = self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+        if not self.samples:
+            return None
+        reasons = sorted({nm for _, bits in self.samples for b, nm in self.REASONS.items() if bits & b})
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": smax,
+                "reasons": reasons, "when": "during the timed region", "samples": len(self.samples),
+                "source": "NVML every 2 ms"}
+
+
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """Clocks during the timed region: NVML in-process when the driver's
+    library loads (NvmlClocks), else nvidia-smi samples every 50 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -125,23 +186,42 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.lines = []
+        self.mark = 0
+        try:
+            self.nvml = NvmlClocks(gpu_index)
+        except (OSError, AttributeError):
+            self.nvml = None
 
     def start(self):
+        """Start sampling.  The nvidia-smi path returns once its first sample
+        is in (at most ~3 s), so that the timed region that follows is covered
+        from its start; that first sample, taken before the region, is left out."""
+        if self.nvml is not None:
+            self.nvml.start()
+            return
+        self.mark = 0
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 3.0:
+            time.sleep(0.01)
+        self.mark = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            return self.nvml.stop()
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -149,7 +229,9 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.th.join(timeout=2)     # the reader has taken every line nvidia-smi wrote
         self.at_end = False
+        self.lines = self.lines[self.mark:]
         if not self.lines:
             # the timed region was shorter than the sampler's start-up: one query
             # right at its end, while the clocks still reflect the load
