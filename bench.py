@@ -265,6 +265,9 @@ class ClockSampler:
 
 
 # ----------------------------------------------------- roofline inputs
+NOMINAL_HBM_GBS = 7900.0     # GB300 HBM3e nominal bandwidth, for context beside the measured peak
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -473,7 +476,8 @@ def run_ours(args, wl):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "kernel": kernel_name, "bytes_per_site": bps,
-                "launches_per_step": launches / args.steps}
+                "launches_per_step": launches / args.steps,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
 
     # End to end through the host-buffer entry point: raw state in from pinned
     # host memory, one step, raw state out, synchronised; wall clock.
@@ -625,7 +629,8 @@ def run_ensemble(args, wl):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                 "kernel": "k_ens (persistent, all steps in one launch)", "bytes_per_site": bps,
-                "launches_per_step": launches / args.steps}
+                "launches_per_step": launches / args.steps,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         mlups, n, el = oracle_sample(256, 256, 0.005, 0, budget_s=args.cpu_seconds)
