@@ -68,3 +68,29 @@ def field_errors(tf: B.TwoFluid, inst: int, ref: O.State, p: O.Params) -> dict:
         "u1": max(uerr(u1[0], mc["u1"][0]), uerr(u1[1], mc["u1"][1])),
         "u2": max(uerr(u2[0], mc["u2"][0]), uerr(u2[1], mc["u2"][1])),
     }
+
+
+# ------------------------------------------------ oracle on windows of a grid
+def cut(state: O.State, x0: int, y0: int, w: int, h: int, margin: int) -> O.State:
+    """Window [y0 - margin, y0 + h + margin) x [x0 - margin, x0 + w + margin)
+    of a periodic state, indices taken modulo the grid."""
+    ny, nx = state.phi.shape
+    ys = (y0 - margin + np.arange(h + 2 * margin)) % ny
+    xs = (x0 - margin + np.arange(w + 2 * margin)) % nx
+    sel = np.ix_(ys, xs)
+    return O.State(state.f1[:, ys[:, None], xs[None, :]].copy(),
+                   state.f2[:, ys[:, None], xs[None, :]].copy(),
+                   state.phi[sel].copy(), state.Qxx[sel].copy(), state.Qxy[sel].copy())
+
+
+def interior(a: np.ndarray, margin: int, w: int, h: int) -> np.ndarray:
+    return a[..., margin:margin + h, margin:margin + w]
+
+
+def window_step(state: O.State, p: O.Params, x0: int, y0: int, w: int, h: int, margin: int):
+    """One oracle step of a window (margin on each side); returns the stepped
+    window state and its macroscopic fields."""
+    win = cut(state, x0, y0, w, h, margin)
+    pw = p.with_(nx=w + 2 * margin, ny=h + 2 * margin)
+    nxt = O.step(win, pw)
+    return nxt, O.macro(nxt, pw)

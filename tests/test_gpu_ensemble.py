@@ -107,6 +107,63 @@ def test_ensemble_autotune_steps_are_real_steps():
     assert cfg["tile_y"] in (24, 30, 32) and cfg["ctas_per_sm"] in (1, 2)
 
 
+def test_ensemble48_benchmarked_configuration():
+    """The benchmarked ensemble: 48 instances of 128^2, 256^2 and 512^2 over
+    the zeta / lambda / K combinations (instance b takes combination b mod 27
+    of zeta in {0.001, 0.005, 0.01}, lambda in {0.3, 0.7, 1.1}, K in {0.02,
+    0.04, 0.08}; seed b), autotuned, one persistent launch per call.  Every
+    member equals the same instances stepped context by context, bit for bit,
+    and the next step of a 512^2 member matches the FP64 oracle on windows."""
+    from helpers import interior, oracle_params, read_state, window_step
+    zetas, lams, ks = (0.001, 0.005, 0.01), (0.3, 0.7, 1.1), (0.02, 0.04, 0.08)
+    spec = []
+    for gi, n in enumerate((128, 256, 512)):
+        spec.append([B.SolverParams(nx=n, ny=n, zeta=zetas[(b % 27) // 9], lam=lams[(b % 9) // 3],
+                                    K=ks[b % 3]) for b in range(16 * gi, 16 * gi + 16)])
+
+    def make():
+        out = []
+        for gi, plist in enumerate(spec):
+            tf = B.TwoFluid(plist)
+            for k in range(len(plist)):
+                tf.init_fields(seed=16 * gi + k, phi0=0.5, dphi=0.01, S0=0.01, inst=k)
+            out.append(tf)
+        return out
+
+    grp = make()
+    ens = B.Ensemble(grp)
+    ens.autotune(2)                       # first pass + 6 x 2 steps
+    ens.step(5)
+    ens.sync()
+    ref = make()
+    for tf in ref:
+        tf.step(18)
+        tf.sync()
+    for g, (a, b) in enumerate(zip(grp, ref)):
+        for inst in range(a.batch):
+            for f in (B.FIELD_PHI, B.FIELD_QXY, B.FIELD_F1 + 5, B.FIELD_U2X):
+                assert np.array_equal(a.read_field(inst, f), b.read_field(inst, f)), (g, inst, f)
+    # one more ensemble step of a 512^2 member against the oracle on windows
+    member, inst = grp[2], 7
+    before = read_state(member, inst)
+    op = oracle_params(spec[2][inst])
+    ens.step(1)
+    ens.sync()
+    after = read_state(member, inst)
+    H, WIN = 16, 32
+    rng = np.random.default_rng(48)
+    origins = [(0, 0), (512 - WIN // 2, 512 - WIN // 2)] + \
+              [(int(rng.integers(0, 512)), int(rng.integers(0, 512))) for _ in range(3)]
+    for x0, y0 in origins:
+        ys, xs = (y0 + np.arange(WIN)) % 512, (x0 + np.arange(WIN)) % 512
+        nxt, _ = window_step(before, op, x0, y0, WIN, WIN, H)
+        for name in ("phi", "Qxx", "Qxy"):
+            want = interior(getattr(nxt, name), H, WIN, WIN)
+            got = getattr(after, name)[np.ix_(ys, xs)]
+            spread = np.abs(getattr(before, name) - getattr(before, name).mean()).max()
+            assert np.abs(got - want).max() <= 1e-6 * spread, (name, x0, y0)
+
+
 def test_ensemble_member_reads_between_calls():
     """A member read completes that member's pending sub-steps; the next
     ensemble call realigns all members and the trajectory is unchanged."""

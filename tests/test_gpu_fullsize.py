@@ -18,7 +18,7 @@ from oracle import twofluid as O
 from paper_2511_00445_gb300 import _binding as B
 from paper_2511_00445_gb300 import inputs
 
-from helpers import oracle_params, read_state, read_velocities
+from helpers import interior, oracle_params, read_state, read_velocities, window_step
 
 H = 16            # window margin: more than the dependence radius of one step
 WIN = 32          # compared interior of each window
@@ -28,31 +28,6 @@ WIN = 32          # compared interior of each window
 # figure is the same on every run); an indexing or tile-seam mistake is O(1e-2).
 TOL_1STEP = 1e-6
 UNIT_ROUNDOFF = {B.STORE_F16: 2.0**-11, B.STORE_BF16: 2.0**-8}
-
-
-def cut(state: O.State, x0: int, y0: int, w: int, h: int, margin: int) -> O.State:
-    """Window [y0 - margin, y0 + h + margin) x [x0 - margin, x0 + w + margin)
-    of a periodic state, indices taken modulo the grid."""
-    ny, nx = state.phi.shape
-    ys = (y0 - margin + np.arange(h + 2 * margin)) % ny
-    xs = (x0 - margin + np.arange(w + 2 * margin)) % nx
-    sel = np.ix_(ys, xs)
-    return O.State(state.f1[:, ys[:, None], xs[None, :]].copy(),
-                   state.f2[:, ys[:, None], xs[None, :]].copy(),
-                   state.phi[sel].copy(), state.Qxx[sel].copy(), state.Qxy[sel].copy())
-
-
-def interior(a: np.ndarray, margin: int, w: int, h: int) -> np.ndarray:
-    return a[..., margin:margin + h, margin:margin + w]
-
-
-def window_step(state: O.State, p: O.Params, x0: int, y0: int, w: int, h: int, margin: int):
-    """One oracle step of a window; returns the stepped window state, its
-    macroscopic fields and the window parameters."""
-    win = cut(state, x0, y0, w, h, margin)
-    pw = p.with_(nx=w + 2 * margin, ny=h + 2 * margin)
-    nxt = O.step(win, pw)
-    return nxt, O.macro(nxt, pw)
 
 
 # ------------------------------------------------------------------ CPU pin of the method
