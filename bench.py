@@ -758,11 +758,14 @@ def run_surrogate(args, wl):
     t_pred = a.elapsed_time(b_) / 1e3 / args.steps
     one.step(args.warmup * horizon)
     torch.cuda.synchronize(dev)
+    plain_clocks = ClockSampler(torch.cuda.current_device())
+    plain_clocks.start()
     with torch.cuda.stream(stream):
         a.record(stream)
         one.step(args.steps * horizon)
         b_.record(stream)
     torch.cuda.synchronize(dev)
+    clk_plain = plain_clocks.stop()
     t_plain = a.elapsed_time(b_) / 1e3 / args.steps
     one.close()
     # the whole sweep (four instances) predicted as one batch vs the batched plain step
@@ -814,7 +817,7 @@ def run_surrogate(args, wl):
                          "kernel": "whole prediction (tcgen05 convolutions + element-wise)",
                          "flops_per_prediction": flops},
             "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": None,
-            "surrogate": {"plain_value": plain, "speedup_vs_plain": value / plain,
+            "surrogate": {"plain_value": plain, "plain_clocks": clk_plain, "speedup_vs_plain": value / plain,
                           "sweep4": {"value": horizon * 4 * sites / t_pred4 / 1e6,
                                      "plain_value": horizon * 4 * sites / t_plain4 / 1e6,
                                      "speedup_vs_plain": t_plain4 / t_pred4,
