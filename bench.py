@@ -166,12 +166,16 @@ class NvmlClocks:
     def stop(self):
         self.stop_flag.set()
         self.th.join(timeout=2)
-        smax = self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
-        if not self.samples:
+        return self.summarise(self.samples, self._clock(self.lib.nvmlDeviceGetMaxClockInfo))
+
+    @classmethod
+    def summarise(cls, samples, smax):
+        """(SM MHz, clock-event reason bits) samples -> the JSON `clocks` object."""
+        if not samples:
             return None
-        reasons = sorted({nm for _, bits in self.samples for b, nm in self.REASONS.items() if bits & b})
-        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": smax,
-                "reasons": reasons, "when": "during the timed region", "samples": len(self.samples),
+        reasons = sorted({nm for _, bits in samples for b, nm in cls.REASONS.items() if bits & b})
+        return {"sm_mhz": statistics.median(m for m, _ in samples), "sm_max_mhz": smax,
+                "reasons": reasons, "when": "during the timed region", "samples": len(samples),
                 "source": "NVML every 2 ms"}
 
 

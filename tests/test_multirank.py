@@ -53,3 +53,18 @@ def test_aggregate_is_whole_job_over_slowest_rank():
     import bench
     v, t = bench.aggregate([2.0, 4.0], sites_per_rank=1000, steps=10)
     assert t == 4.0 and v == pytest.approx(2 * 1000 * 10 / 4.0 / 1e6)
+
+
+def test_clock_samples_summary():
+    """NVML clock-event reason bits map to the names the benchmark line
+    reports (sw_power_cap 0x4, hw_slowdown 0x8, sw_thermal_slowdown 0x20,
+    hw_thermal_slowdown 0x40); idle (0x1) and other bits are not reasons; the
+    SM clock is the median of the samples."""
+    import bench
+    s = bench.NvmlClocks.summarise([(2070, 0x0), (2070, 0x1), (1980, 0x4), (2070, 0x100)], 2070)
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070 and s["samples"] == 4
+    assert s["reasons"] == ["sw_power_cap"]
+    s = bench.NvmlClocks.summarise([(1500, 0x8 | 0x40), (1600, 0x20)], 2070)
+    assert s["sm_mhz"] == 1550 and s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown",
+                                                     "sw_thermal_slowdown"]
+    assert bench.NvmlClocks.summarise([], 2070) is None
