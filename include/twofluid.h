@@ -253,6 +253,20 @@ int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out);
 int tf_save(tf_ctx* ctx, const char* path);
 int tf_load(tf_ctx* ctx, const char* path);
 
+/* Tile plan of the fused per-context kernel (n_sub = 5); host-side only, no
+ * device call.  For `batch` instances of nx x ny sites and `slots` resident
+ * CTAs (SMs x CTAs per SM; contexts take it from the occupancy of the narrow
+ * kernel, two per SM on GB300) it writes out[0] = 1 for the wide geometry
+ * (tiles of at most 40 x 30 sites, used when the 32 x 32 tiles of all
+ * instances exceed one wave) or 0 for the narrow one (at most 32 x 32),
+ * out[1] = tile columns and out[2] = tile rows per instance.  Tile row r
+ * spans rows [r ny / out[2], (r + 1) ny / out[2]) (integer division); column
+ * tile k spans [col_start[k], col_start[k + 1]).  `col_start` may be NULL;
+ * otherwise it must hold cap >= out[1] + 1 entries.  TF_ERR_ARG on a bad
+ * argument. */
+int tf_plan_tiles(int nx, int ny, int batch, long long slots, int out[3], int* col_start,
+                  int cap);
+
 /* ---- ensembles: several contexts stepped by one persistent launch ----- */
 /* The paper explores its parameters (activity zeta, tumbling lambda, Frank
  * constant K; Sec. IV) through many separate runs; it has no counterpart to

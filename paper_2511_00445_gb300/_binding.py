@@ -45,7 +45,7 @@ EXPORTS = [
     "tf_step_count", "tf_kernel_launches", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
     "tf_length_scale", "tf_energy_spectrum", "tf_phase_difference", "tf_phi_stats",
     "tf_correlation", "tf_snapshot", "tf_time_correlation", "tf_defects", "tf_reynolds",
-    "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load",
+    "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load", "tf_plan_tiles",
     "tf_ensemble_workspace_bytes", "tf_ensemble_create", "tf_ensemble_destroy",
     "tf_ensemble_last_error", "tf_ensemble_step", "tf_ensemble_sync", "tf_ensemble_autotune",
     "tf_ensemble_config", "tf_ensemble_launches",
@@ -165,6 +165,7 @@ def load_library() -> ctypes.CDLL:
         "tf_advance_host": (i, [vp, vp, i64, vp]),
         "tf_save": (i, [vp, ctypes.c_char_p]),
         "tf_load": (i, [vp, ctypes.c_char_p]),
+        "tf_plan_tiles": (i, [i, i, i, ctypes.c_longlong, ctypes.POINTER(i), ctypes.POINTER(i), i]),
         "tf_ensemble_workspace_bytes": (sz, [i]),
         "tf_ensemble_create": (i, [ctypes.POINTER(vp), i, vp, sz, vp, ctypes.POINTER(vp)]),
         "tf_ensemble_destroy": (i, [vp]),

@@ -7,6 +7,11 @@
 #include <vector>
 
 #include "tf_internal.h"
+#include "tf_fused.cuh"   // tile geometry constants and tile_col of the fused kernel
+
+// Tile planning of the fused per-context kernel (defined in tf_fused.cu).
+bool wide_for(int nx, int ny, int batch, long long slots);
+int tile_rows_for(int ntx, int ny, int tym, int batch, long long slots);
 
 namespace {
 
@@ -675,6 +680,22 @@ int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
         if ((rc = copy_state(ctx, h_out, true)) != TF_OK) return rc;
     }
     TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TF_OK;
+}
+
+int tf_plan_tiles(int nx, int ny, int batch, long long slots, int out[3], int* col_start, int cap) {
+    if (nx < 1 || ny < 1 || nx > kMaxDim || ny > kMaxDim || batch < 1 || slots < 1 || !out)
+        return TF_ERR_ARG;
+    const bool wide = wide_for(nx, ny, batch, slots);
+    const int txm = wide ? TX_WIDE : TX, tym = wide ? TY_WIDE : TY_DEFAULT;
+    const int cols = (nx + txm - 1) / txm;
+    out[0] = wide ? 1 : 0;
+    out[1] = cols;
+    out[2] = tile_rows_for(cols, ny, tym, batch, slots);
+    if (col_start) {
+        if (cap < cols + 1) return TF_ERR_ARG;
+        for (int k = 0; k <= cols; ++k) col_start[k] = tile_col(k, cols, nx);
+    }
     return TF_OK;
 }
 
