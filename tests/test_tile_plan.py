@@ -87,3 +87,41 @@ def test_plan_argument_errors(lib):
     # too small a column array: 256 columns narrow need 9 entries
     assert lib.tf_plan_tiles(256, 256, 1, SLOTS, out, cs, 4) == B.TF_ERR_ARG
     assert lib.tf_plan_tiles(256, 256, 1, SLOTS, out, None, 0) == B.TF_OK
+
+
+def _segments(xs, length, nx):
+    """Row segments of a periodic copy of `length` elements from column xs,
+    split at the wrap (the kernel's bulk-copy and prefetch row walk)."""
+    out, off = [], 0
+    while off < length:
+        gx = (xs + off) % nx
+        n = min(length - off, nx - gx)
+        out.append((gx, n))
+        off += n
+    return out
+
+
+@pytest.mark.parametrize("nx,ny,batch", GRIDS)
+def test_bulk_copy_and_prefetch_segments_are_16_byte_units(lib, nx, ny, batch):
+    """The tile loads and the L2 population prefetch move whole 16-byte
+    units from 16-byte boundaries (a bulk copy from anywhere else faults).
+    Restated host arithmetic of the kernel: a tile row of phi, Q or u is
+    loaded from x0 - RH over tw + 2 RH columns (RH = 12 with pending
+    sub-steps, 4 without) when nx is a multiple of 4; populations are
+    prefetched over x0 - 1 .. x0 + tw widened to whole units of PF elements
+    (4 FP32 or 8 16-bit values) when nx is a multiple of PF."""
+    wide, cols, rows, cs = plan(lib, nx, ny, batch)
+    for k in range(cols):
+        x0, tw = cs[k], cs[k + 1] - cs[k]
+        if nx % 4 == 0:
+            for rh in (12, 4):
+                for gx, n in _segments(x0 - rh, tw + 2 * rh, nx):
+                    assert gx % 4 == 0 and n % 4 == 0, (x0, tw, rh, gx, n)
+        for pf in (4, 8):
+            if nx % pf:
+                continue
+            xs = ((x0 - 1 + pf) // pf - 1) * pf
+            xe = (x0 + tw + 1 + pf - 1) // pf * pf
+            assert xs <= x0 - 1 and xe >= x0 + tw + 1
+            for gx, n in _segments(xs, xe - xs, nx):
+                assert gx % pf == 0 and n % pf == 0, (x0, tw, pf, gx, n)
