@@ -31,6 +31,8 @@
  *   - Every function returns TF_OK (0) or a negative TF_ERR_* code; the
  *     message of the last failure is available from tf_last_error().  No
  *     C++ exception crosses this boundary and no kernel traps.
+ *   - A context (and an ensemble, a surrogate) is used by one host thread at
+ *     a time; different contexts may be used from different threads.
  */
 #ifndef TWOFLUID_H
 #define TWOFLUID_H
