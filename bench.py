@@ -1,17 +1,20 @@
 #!/usr/bin/env python3
 """Throughput of the coupled two-fluid lattice step on GB300.
 
-Default workload: the activity sweep zeta in {0, 0.002, 0.005, 0.01} on
-256x256 periodic grids (lambda 0.7, K 0.04, drag 0.01, tau 1), FP32, run as
-one batch of four instances.  One bench step = one coupled lattice step of
-all four instances (two D2Q9 fluids, forces, five Cahn-Hilliard and
-Beris-Edwards sub-steps).  The state (~44 MB) fits in L2, so L2 is flushed
-(256 MiB write) before every timed step and each step is timed alone with
-CUDA events on the solver's stream.
+Default workload: one 2048 x 2048 periodic instance (zeta 0.005, lambda 0.7,
+K 0.04, drag 0.01, tau 1), FP32, the size at which the step's HBM roofline
+is measured (state ~0.9 GB, far larger than the 129 MB L2).  One bench step =
+one coupled lattice step (two D2Q9 fluids, forces, five Cahn-Hilliard and
+Beris-Edwards sub-steps) = one launch of the steady-state kernel.  Steps run
+back to back; each is bracketed by CUDA events on the solver's stream.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sweep256|single1024|single2048|ensemble48]
-                    [--storage f32|f16|bf16]
+                    [--workload single2048|single1024|sweep256|ensemble48|surrogate256]
+                    [--storage f32|f16|bf16] [--kernel auto|tile|strip]
+
+--workload sweep256 is the activity sweep zeta in {0, 0.002, 0.005, 0.01} on
+four 256 x 256 instances; its state (~44 MB) fits in L2, so L2 is flushed
+(256 MiB write) before every timed step there.
 
 --workload ensemble48 steps 48 instances of three sizes (the parameter-sweep
 ensemble) with the persistent ensemble launch after its autotuner ran, and
@@ -24,8 +27,8 @@ arithmetic).  Such a run also times the FP32 storage on the same workload
 spectrum of instance 0).
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own copy of
-the workload with its own seed (independent ensemble members, weak scaling);
-only the timing is reduced across ranks (max).
+the workload with its own seed (independent replicas, weak scaling); only the
+timing is reduced across ranks (max).
 """
 from __future__ import annotations
 
@@ -55,7 +58,7 @@ WORKLOADS = {
                      name="zeta sweep {0,0.002,0.005,0.01} x 256x256, FP32, lambda 0.7, K 0.04"),
     "single1024": dict(nx=1024, ny=1024, zetas=[0.005],
                        name="single 1024x1024, FP32, zeta 0.005, lambda 0.7, K 0.04"),
-    "single2048": dict(nx=2048, ny=2048, zetas=[0.005],
+    "single2048": dict(nx=2048, ny=2048, zetas=[0.005], large=True,
                        name="single 2048x2048, FP32, zeta 0.005, lambda 0.7, K 0.04"),
     # 48 instances: sizes {128, 256, 512}^2 (16 each); parameter combination
     # c = b mod 27 over zeta x lambda x K (lexicographic); seed b.
@@ -283,7 +286,7 @@ def measured_peaks():
 
 
 # Sources the per-context fused kernel is compiled from.
-FUSED_SOURCES = ("tf_device.cuh", "tf_fused.cu", "tf_fused.cuh", "tf_internal.h", "tf_pair.cuh",
+FUSED_SOURCES = ("tf_device.cuh", "tf_fused.cu", "tf_fused.cuh", "tf_strip.cuh", "tf_internal.h", "tf_pair.cuh",
                  "tf_ptx.cuh")
 
 
@@ -335,11 +338,65 @@ def oracle_sample(nx, ny, zeta, seed, budget_s, max_steps=None):
     return nx * ny * n / el / 1e6, n, el
 
 
+def _oracle_worker(job):
+    nx, ny, zeta, seed, budget_s = job
+    return oracle_sample(nx, ny, zeta, seed, budget_s)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_all_cores(nx, ny, zeta, budget_s, procs):
+    """The FP64 oracle on every host core: `procs` spawned processes, each
+    stepping its own instance (different seeds) for budget_s seconds; the
+    sum of their site-update rates.  Each process runs single-threaded
+    numpy (BLAS threads pinned to one)."""
+    import multiprocessing as mp
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                          "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [(nx, ny, zeta, k, budget_s) for k in range(procs)])
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return sum(r[0] for r in res), sum(r[1] for r in res), max(r[2] for r in res)
+
+
+def cpu_baseline(nx, ny, zeta, budget_s):
+    """The oracle as it stands on the machine's host cores: one core, then all
+    cores, each on instances of at most 512 x 512 sites of the workload's
+    parameters (the oracle's cost per site update does not depend on the
+    grid size; a 2048^2 instance would take several seconds per step)."""
+    sx, sy = min(nx, 512), min(ny, 512)
+    one, n1, el1 = oracle_sample(sx, sy, zeta, 0, budget_s=budget_s)
+    procs = host_cores()
+    allc, nall, elall = oracle_all_cores(sx, sy, zeta, budget_s, procs)
+    return {"value": allc, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {procs} processes each stepping its own {sx}x{sy} "
+                      f"instance (zeta {zeta}) for ~{budget_s:.0f} s ({nall} steps in all)",
+            "one_core": {"value": one, "unit": UNIT, "cores": 1,
+                         "sample": f"one {sx}x{sy} instance, {n1} steps ({el1:.1f} s) after one "
+                                   f"warm-up step"}}
+
+
 def run_reference(args, wl):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    nx, ny = wl["nx"], wl["ny"]
+    # each timed step is a bounded sample of the workload: one oracle step of
+    # one instance, cut to 128 x 128 sites for the 2048^2 workload (same
+    # parameters; the oracle's cost per site update does not depend on size)
+    nx, ny = (min(wl["nx"], 128), min(wl["ny"], 128)) if wl.get("large") else (wl["nx"], wl["ny"])
     zeta = wl["zetas"][len(wl["zetas"]) // 2]
     import numpy as np
 
@@ -357,8 +414,8 @@ def run_reference(args, wl):
     el = time.perf_counter() - t0
     sites = nx * ny
     val = sites * args.steps / el / 1e6
-    sample = (f"one instance (zeta={zeta}) of the {len(wl['zetas'])}-instance workload, "
-              f"{nx}x{ny}, {args.steps} steps per run")
+    sample = (f"one {nx}x{ny} instance (zeta={zeta}) with the workload's parameters, "
+              f"{args.steps} oracle steps on one host core")
     out = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
@@ -373,13 +430,16 @@ def run_reference(args, wl):
 
 # -------------------------------------------------------------- our arm
 def time_steps(tf, flush, steps: int, warmup: int, world: int, dev, clocks=None):
-    """W untimed steps, then K steps each timed alone with CUDA events on the
-    solver stream after an L2 flush; barrier + synchronize on both sides."""
+    """W untimed steps, then K steps each bracketed by CUDA events on the
+    solver stream (after an L2 flush when `flush` is a buffer; back to back
+    when it is None, for states far larger than L2); barrier + synchronize on
+    both sides."""
     import torch
     stream = tf.stream
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            flush.zero_()
+            if flush is not None:
+                flush.zero_()
             tf.step(1)
     torch.cuda.synchronize(dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -392,7 +452,8 @@ def time_steps(tf, flush, steps: int, warmup: int, world: int, dev, clocks=None)
     launches0 = tf.kernel_launches()
     with torch.cuda.stream(stream):
         for a, b in evs:
-            flush.zero_()
+            if flush is not None:
+                flush.zero_()
             a.record(stream)
             tf.step(1)
             b.record(stream)
@@ -460,8 +521,11 @@ def run_ours(args, wl):
     sites = wl["nx"] * wl["ny"] * len(params)
     seed = rank_seed(0, rank)
     tf = B.TwoFluid(params, device=dev)
+    tf.set_step_kernel(args.kernel)
     tf.init_fields(seed=seed, phi0=0.5, dphi=0.01, S0=0.01)
-    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    tf_state_gb = tf.state_bytes() / 1e9
+    step_kernel = tf.step_kernel()
+    flush = None if wl.get("large") else torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     clocks = ClockSampler(torch.cuda.current_device() if world == 1 else local)
     ms, launches, clk = time_steps(tf, flush, args.steps, args.warmup, world, dev, clocks)
     sec_local = sum(ms) / 1e3
@@ -473,8 +537,9 @@ def run_ours(args, wl):
 
     peak, peak_kind = measured_peaks()
     bps = BYTES_PER_SITE[args.storage]
-    # With five sub-steps every timed step is one launch of the fused kernel.
-    kernel_name = "k_fused<1,1>" if launches == args.steps else "tf_step (per-stage kernels)"
+    # With five sub-steps every timed step is one launch of the steady-state kernel.
+    kernel_name = ("tf_step (per-stage kernels)" if launches != args.steps else
+                   "k_strip" if step_kernel == B.KERNEL_STRIP else "k_fused<1,1>")
     achieved = bps * sites / (statistics.mean(ms) / 1e3) / 1e9
     traffic = recorded_traffic(kernel_name, args.workload, args.storage)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -510,6 +575,7 @@ def run_ours(args, wl):
     precision = None
     if storage != B.STORE_F32:
         ref = B.TwoFluid([p.with_(storage=B.STORE_F32) for p in params], device=dev)
+        ref.set_step_kernel(args.kernel)
         ref.init_fields(seed=seed, phi0=0.5, dphi=0.01, S0=0.01)
         ms32, _, _ = time_steps(ref, flush, args.steps, args.warmup, world, dev)
         ref.close()
@@ -521,11 +587,7 @@ def run_ours(args, wl):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        mlups, n, el = oracle_sample(wl["nx"], wl["ny"], wl["zetas"][len(wl["zetas"]) // 2], 0,
-                                     budget_s=args.cpu_seconds)
-        cpu = {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle, one {wl['nx']}x{wl['ny']} instance, {n} steps "
-                         f"({el:.1f} s) after one warm-up step"}
+        cpu = cpu_baseline(wl["nx"], wl["ny"], wl["zetas"][len(wl["zetas"]) // 2], args.cpu_seconds)
 
     if rank == 0:
         name = wl["name"] if storage == B.STORE_F32 else wl["name"].replace(
@@ -537,7 +599,9 @@ def run_ours(args, wl):
             "data": "synthetic (seeded SplitMix64 initial condition of Sec. III)",
             "config": {"workload": name, "sites_per_step": sites, "instances": len(params),
                        "storage": args.storage,
-                       "l2": "flushed (256 MiB write) before every timed step",
+                       "l2": ("not flushed: the state (~%.2f GB) is far larger than L2, "
+                              "steps run back to back" % (tf_state_gb,)) if flush is None
+                             else "flushed (256 MiB write) before every timed step",
                        "timing": "CUDA events per step on the solver stream"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches,
@@ -637,10 +701,7 @@ def run_ensemble(args, wl):
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        mlups, n, el = oracle_sample(256, 256, 0.005, 0, budget_s=args.cpu_seconds)
-        cpu = {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle, one 256x256 member of the ensemble, {n} steps "
-                         f"({el:.1f} s) after one warm-up step"}
+        cpu = cpu_baseline(256, 256, 0.005, args.cpu_seconds)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -839,21 +900,26 @@ def run_surrogate(args, wl):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2000 for single2048, 200 otherwise)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sweep256")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single2048")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32",
                     help="population storage (arithmetic is FP32 in every mode)")
+    ap.add_argument("--kernel", choices=["auto", "tile", "strip"], default="auto",
+                    help="steady-state kernel (auto: strip on grids of several tile waves)")
     ap.add_argument("--error-steps", type=int, default=200,
                     help="steps of the FP32-vs-16-bit trajectory comparison")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     wl = WORKLOADS[args.workload]
+    if args.steps is None:
+        args.steps = 2000 if wl.get("large") else 200
     if args.impl == "reference":
         run_reference(args, wl)
     elif wl.get("ensemble"):

@@ -17,7 +17,8 @@
  *   - periodic boundaries in x and y for every field.
  *
  * Conventions for every entry point:
- *   - Lattice units: dx = dt_LBM = 1, c_s^2 = 1/3, dt_fd = 1/n_sub.
+ *   - Lattice units: dx = dt_LBM = 1, c_s^2 = 1/3; the FD sub-steps advance
+ *     by dt_fd = dt / n_sub each (tf_params.dt, 1 for lattice units).
  *   - A context holds `batch` independent instances (e.g. a parameter sweep)
  *     that share nx, ny and n_sub; each instance has its own tf_params.
  *   - Host arrays are row-major (y, x): element (x, y) at index y*nx + x, in
@@ -106,6 +107,19 @@ typedef struct tf_params {
     double kappa;       /* eps^2 of Eq. (2)                                    */
     double phi_ref;     /* reference value phi is stored relative to (use the
                            mean concentration, e.g. 0.5)                        */
+    double dt;          /* duration of one lattice step in the time unit of the
+                           Cahn-Hilliard and Beris-Edwards rates; each of the
+                           n_sub sub-steps advances them by dt / n_sub (Sec.
+                           III: five FD updates per lattice step).  1 reads the
+                           rates in lattice units (the default reading); the
+                           printed dt = 0.02 is the literal one.  > 0, finite */
+    int    check_every; /* 0: off.  k > 0: tf_step scans the latest phi, Q and
+                           velocity planes after every k-th lattice step (counted
+                           by tf_step_count) for NaN / Inf and records
+                           TF_ERR_NONFINITE in the context's device status word,
+                           which the next tf_sync returns; no host
+                           synchronisation, no device trap.  Taken from params[0]
+                           for the whole context.                              */
 } tf_params;
 
 typedef struct tf_ctx tf_ctx;   /* opaque, library-owned host object */
@@ -154,7 +168,30 @@ int tf_read_field(tf_ctx* ctx, int inst, int field, double* host);
  * reported by the next synchronising call. */
 int tf_step(tf_ctx* ctx, int64_t n);
 
-/* Wait for the context stream; returns TF_ERR_CUDA on an execution error. */
+/* Kernel of the steady-state steps (five sub-steps per step).  Both compute
+ * bitwise the same trajectory; they differ in schedule:
+ *   TF_KERNEL_TILE:  one CTA per 2-D tile (up to 40 x 30 sites) with a 12-site
+ *                    halo, the five sub-steps on shrinking neighbourhoods;
+ *   TF_KERNEL_STRIP: one CTA per column strip (up to 96 columns) and row
+ *                    segment, walked down in blocks of 8 rows with the five
+ *                    sub-steps pipelined two rows apart (needs nx % 4 == 0);
+ *   TF_KERNEL_AUTO:  the faster of the two for the context's grid (currently
+ *                    the tile kernel everywhere).
+ * tf_set_step_kernel takes effect from the next step (TF_ERR_ARG for an
+ * unknown kind, or TF_KERNEL_STRIP on a context it cannot step);
+ * tf_step_kernel returns TF_KERNEL_TILE or TF_KERNEL_STRIP, the kernel the
+ * next steady-state step launches (planning it if needed), or a negative
+ * TF_ERR_* code. */
+#define TF_KERNEL_AUTO  0
+#define TF_KERNEL_TILE  1
+#define TF_KERNEL_STRIP 2
+int tf_set_step_kernel(tf_ctx* ctx, int kind);
+int tf_step_kernel(tf_ctx* ctx);
+
+/* Wait for the context stream; returns TF_ERR_CUDA on an execution error,
+ * else the device status word if a kernel set it since the last tf_sync
+ * (TF_ERR_TIMEOUT: a bounded device wait ran out; TF_ERR_NONFINITE: the
+ * check_every scan found NaN or Inf), clearing it. */
 int tf_sync(tf_ctx* ctx);
 
 /* Number of lattice steps taken since the last init / load. */
@@ -337,6 +374,19 @@ int tf_ensemble_config(const tf_ensemble* ens, int* tile_y, int* ctas_per_sm, in
  * one kernel). */
 int64_t tf_ensemble_launches(const tf_ensemble* ens);
 
+/* Failure-detection drill for the persistent launch's grid barrier (no fault
+ * is injected on the device: a CTA just leaves early).  From the next
+ * tf_ensemble_step on, the barrier gives up after `barrier_polls` polls of
+ * ~128 ns each (0 restores the default of about one second) and, when
+ * held_cta >= 0, that CTA of each steady-state launch of two or more steps
+ * returns at the first grid barrier without arriving (it has no bulk copy in
+ * flight there).  The other CTAs' bounded waits then run out: they record
+ * TF_ERR_TIMEOUT in the first member's status word, raise the launch's abort
+ * word and return, so tf_ensemble_sync reports TF_ERR_TIMEOUT and the members'
+ * state is left partly stepped (initialise or load it again).  The drill
+ * stays on until called again with (0, -1).  TF_ERR_ARG for held_cta < -1. */
+int tf_ensemble_fault_drill(tf_ensemble* ens, uint32_t barrier_polls, int held_cta);
+
 /* ---- learned surrogate: a U-Net that advances a state by many steps ---- */
 /* The paper has no learned component; this layer is a convolutional
  * surrogate of the coupled step: from (phi, Q_xx, Q_xy, u1, u2) at time t of
@@ -445,19 +495,23 @@ int tf_sur_judged_predict(tf_surrogate* s, tf_ctx* ctx, tf_ctx* shadow, int inst
  * Input: d_values, a device array of n FP32 values v_i (for example the
  * stored deviations phi - phi_ref of a concentration field).  Output: d_out, a
  * device array of 2 doubles receiving mean = phi_ref + <v> and the standard
- * deviation of v, both summed in FP64.  The call only enqueues work on
- * `stream` (a cudaStream_t passed as void*); synchronise before reading d_out.
+ * deviation sqrt(<(v - <v>)^2>) of v, in FP64: every block of 4096 values
+ * contributes its mean and its sum of squared deviations (two passes), and
+ * these are merged pairwise in a fixed order (Chan, Golub & LeVeque), so v
+ * need not be centred.  The call only enqueues work on `stream` (a
+ * cudaStream_t passed as void*); synchronise before reading d_out.
  *
  * Scratch: the library keeps TF_NOALLOC_MAX_BLOCKS x 2 doubles (16 KiB) of
- * per-block partial sums in one statically allocated device array, held by
- * every GPU that loads the library until the process exits.  Each block sums
- * 4096 values, so n is limited to TF_NOALLOC_MAX_ELEMS (4 194 304, e.g. one
- * 2048 x 2048 field); larger n returns TF_ERR_TOO_LARGE, n <= 0 or a null
- * pointer TF_ERR_ARG.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress with that device current) and caches
- * it; make that first call before any stream capture.  All calls share the
- * array: two calls whose kernels overlap on the GPU (different streams, or
- * different host threads on one device) race and may return wrong values. */
+ * per-block partials in one statically allocated device array, held by every
+ * GPU that loads the library until the process exits.  n is limited to
+ * TF_NOALLOC_MAX_ELEMS (4 194 304, e.g. one 2048 x 2048 field); larger n
+ * returns TF_ERR_TOO_LARGE, n <= 0 or a null pointer TF_ERR_ARG.  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a device
+ * may load the library's device code there, so make it before any stream
+ * capture.  All calls share the array: two calls whose kernels overlap on
+ * the GPU (different streams, or different host threads on one device) race
+ * and may return wrong values. */
 #define TF_NOALLOC_MAX_BLOCKS 1024
 #define TF_NOALLOC_MAX_ELEMS  (4096LL * TF_NOALLOC_MAX_BLOCKS)
 int tf_phi_stats_noalloc(const float* d_values, long long n, double phi_ref,

@@ -77,6 +77,8 @@ class Params:
     A_ch: float = 0.05       # prefactor of the double well f(phi)
     kappa: float = 0.1       # eps^2 in mu = A_ch f'(phi) - eps^2 lap(phi), Eq. (2)
     n_sub: int = 5           # finite-difference sub-steps per lattice step (Sec. III)
+    dt: float = 1.0          # one lattice step in the time unit of the FD rates (Sec. III:
+                             # dt_fd = dt / n_sub; 1 = lattice units, the default reading)
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
@@ -365,9 +367,9 @@ def be_rate(Q, u1, p: Params):
 
 
 def substeps(phi, Qxx, Qxy, u1, u2, p: Params):
-    """n_sub forward-Euler updates of phi and Q with dt_fd = 1/n_sub and the
-    velocities held fixed (Sec. III)."""
-    dt = 1.0 / p.n_sub
+    """n_sub forward-Euler updates of phi and Q with dt_fd = dt / n_sub and the
+    velocities held fixed (Sec. III: five FD updates share one lattice step)."""
+    dt = p.dt / p.n_sub
     for _ in range(p.n_sub):
         Q = q_tensor(Qxx, Qxy)
         dphi = ch_rate(phi, u1, u2, p)

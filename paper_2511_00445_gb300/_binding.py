@@ -36,19 +36,22 @@ STORE_F32 = 0
 STORE_F16 = 1
 STORE_BF16 = 2
 STORAGE_NAMES = {"f32": STORE_F32, "f16": STORE_F16, "bf16": STORE_BF16}
+KERNEL_AUTO, KERNEL_TILE, KERNEL_STRIP = 0, 1, 2
+KERNEL_NAMES = {"auto": KERNEL_AUTO, "tile": KERNEL_TILE, "strip": KERNEL_STRIP}
 NCONS = 8
 
 # Every symbol include/twofluid.h declares, in declaration order.
 EXPORTS = [
     "tf_workspace_bytes", "tf_create", "tf_destroy", "tf_last_error", "tf_init_fields",
-    "tf_write_field", "tf_set_equilibrium", "tf_read_field", "tf_step", "tf_sync",
+    "tf_write_field", "tf_set_equilibrium", "tf_read_field", "tf_step", "tf_set_step_kernel",
+    "tf_step_kernel", "tf_sync",
     "tf_step_count", "tf_kernel_launches", "tf_conserved", "tf_n_shell", "tf_shell_counts", "tf_structure_factor",
     "tf_length_scale", "tf_energy_spectrum", "tf_phase_difference", "tf_phi_stats",
     "tf_correlation", "tf_snapshot", "tf_time_correlation", "tf_defects", "tf_reynolds",
     "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load", "tf_plan_tiles",
     "tf_ensemble_workspace_bytes", "tf_ensemble_create", "tf_ensemble_destroy",
     "tf_ensemble_last_error", "tf_ensemble_step", "tf_ensemble_sync", "tf_ensemble_autotune",
-    "tf_ensemble_config", "tf_ensemble_launches",
+    "tf_ensemble_config", "tf_ensemble_launches", "tf_ensemble_fault_drill",
     "tf_sur_workspace_bytes", "tf_sur_create", "tf_sur_destroy", "tf_sur_last_error",
     "tf_sur_num_params", "tf_sur_init_weights", "tf_sur_set_weights", "tf_sur_get_weights",
     "tf_sur_forward", "tf_sur_gradients", "tf_sur_add_pair", "tf_sur_fit_normalisation",
@@ -75,7 +78,8 @@ class TFParams(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("K", ctypes.c_double),
                 ("Gamma_Q", ctypes.c_double), ("A_Q", ctypes.c_double), ("C_Q", ctypes.c_double),
                 ("M", ctypes.c_double), ("A_ch", ctypes.c_double), ("kappa", ctypes.c_double),
-                ("phi_ref", ctypes.c_double)]
+                ("phi_ref", ctypes.c_double), ("dt", ctypes.c_double),
+                ("check_every", ctypes.c_int)]
 
 
 @dataclass(frozen=True)
@@ -103,6 +107,8 @@ class SolverParams:
     A_ch: float = 0.05
     kappa: float = 0.1
     phi_ref: float = 0.5
+    dt: float = 1.0          # FD sub-step = dt / n_sub (1: lattice units)
+    check_every: int = 0     # non-finite scan every k steps (0: off)
 
     def with_(self, **kw) -> "SolverParams":
         return replace(self, **kw)
@@ -145,6 +151,8 @@ def load_library() -> ctypes.CDLL:
         "tf_set_equilibrium": (i, [vp, i, dp, dp]),
         "tf_read_field": (i, [vp, i, i, dp]),
         "tf_step": (i, [vp, i64]),
+        "tf_set_step_kernel": (i, [vp, i]),
+        "tf_step_kernel": (i, [vp]),
         "tf_sync": (i, [vp]),
         "tf_step_count": (i64, [vp]),
         "tf_kernel_launches": (i64, [vp]),
@@ -176,6 +184,7 @@ def load_library() -> ctypes.CDLL:
         "tf_ensemble_config": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i64), dp, ctypes.POINTER(i)]),
         "tf_ensemble_launches": (i64, [vp]),
+        "tf_ensemble_fault_drill": (i, [vp, ctypes.c_uint32, i]),
         "tf_sur_workspace_bytes": (sz, [ctypes.POINTER(TFSurConfig)]),
         "tf_sur_create": (i, [ctypes.POINTER(TFSurConfig), vp, sz, vp, ctypes.POINTER(vp)]),
         "tf_sur_destroy": (i, [vp]),
@@ -282,6 +291,16 @@ class TwoFluid:
 
     def sync(self):
         self._check(self.lib.tf_sync(self.ctx))
+
+    def set_step_kernel(self, kind):
+        """kind: KERNEL_AUTO / KERNEL_TILE / KERNEL_STRIP or 'auto' / 'tile' / 'strip'."""
+        self._check(self.lib.tf_set_step_kernel(self.ctx, KERNEL_NAMES.get(kind, kind)))
+
+    def step_kernel(self) -> int:
+        rc = self.lib.tf_step_kernel(self.ctx)
+        if rc < 0:
+            self._check(rc)
+        return rc
 
     def step_count(self) -> int:
         return int(self.lib.tf_step_count(self.ctx))
@@ -432,6 +451,9 @@ class Ensemble:
 
     def launches(self) -> int:
         return int(self.lib.tf_ensemble_launches(self.ens))
+
+    def fault_drill(self, barrier_polls: int = 0, held_cta: int = -1):
+        self._check(self.lib.tf_ensemble_fault_drill(self.ens, barrier_polls, held_cta))
 
 
 def _fptr(a: np.ndarray):

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(HERE, LIB_NAME)
 
 SOURCES = ["tf_api.cu", "tf_step.cu", "tf_observe.cu", "tf_fused.cu", "tf_ensemble.cu", "nn_surrogate.cu",
            "tf_noalloc.cu"]
-HEADERS = ["tf_internal.h", "tf_device.cuh", "tf_ptx.cuh", "tf_pair.cuh", "tf_fused.cuh", "nn_tc.cuh"]
+HEADERS = ["tf_internal.h", "tf_device.cuh", "tf_ptx.cuh", "tf_pair.cuh", "tf_fused.cuh", "tf_strip.cuh",
+           "nn_tc.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

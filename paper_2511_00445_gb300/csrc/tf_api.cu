@@ -19,7 +19,7 @@ constexpr size_t kAlign = 256;
 constexpr int kMaxDim = 32768;
 constexpr int kMaxFFT = 8192;
 constexpr uint64_t kMagic = 0x31444C4655464F57ull;  // checkpoint tag
-constexpr int kVersion = 1;
+constexpr int kVersion = 2;   // 2: tf_params gained dt and check_every
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -52,6 +52,8 @@ const char* check_params(const tf_params& p) {
                         p.C_Q,   p.M,    p.A_ch,   p.kappa, p.phi_ref};
     for (double x : v)
         if (!std::isfinite(x)) return "parameters must be finite";
+    if (!(p.dt > 0) || !std::isfinite(p.dt)) return "dt must be positive and finite (1 for lattice units)";
+    if (p.check_every < 0) return "check_every must be >= 0";
     return nullptr;
 }
 
@@ -93,7 +95,7 @@ DevParams tf_make_devparams(const tf_params& p) {
     d.C_Q = (float)p.C_Q;
     d.M = (float)p.M;
     d.kappa = (float)p.kappa;
-    d.dt_fd = (float)(1.0 / p.n_sub);
+    d.dt_fd = (float)(p.dt / p.n_sub);
     d.phi_ref = (float)p.phi_ref;
     d.rho1 = (float)p.rho1;
     d.rho2 = (float)p.rho2;
@@ -290,8 +292,43 @@ int tf_step(tf_ctx* ctx, int64_t n) {
     if (!ctx) return TF_ERR_ARG;
     if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
     if (n == 0) return TF_OK;
-    TF_CK(ctx, tf_launch_steps(ctx, n));
+    const int64_t k = ctx->params[0].check_every;
+    if (k <= 0) {
+        TF_CK(ctx, tf_launch_steps(ctx, n));
+        return TF_OK;
+    }
+    // Steps in chunks that end on multiples of k (of the step count), each
+    // followed by the non-finite scan.
+    while (n > 0) {
+        const int64_t to_next = k - ctx->steps % k;
+        const int64_t m = n < to_next ? n : to_next;
+        TF_CK(ctx, tf_launch_steps(ctx, m));
+        n -= m;
+        if (ctx->steps % k == 0) TF_CK(ctx, tf_launch_nonfinite_scan(ctx));
+    }
     return TF_OK;
+}
+
+int tf_set_step_kernel(tf_ctx* ctx, int kind) {
+    if (!ctx) return TF_ERR_ARG;
+    if (kind != TF_KERNEL_AUTO && kind != TF_KERNEL_TILE && kind != TF_KERNEL_STRIP)
+        return fail(ctx, TF_ERR_ARG, "unknown step kernel");
+    if (kind == TF_KERNEL_STRIP && !tf_strip_supported(ctx))
+        return fail(ctx, TF_ERR_ARG, "the strip kernel needs n_sub = 5 and nx a multiple of 4");
+    ctx->step_kernel = kind;
+    // captured host-buffer pipelines bake in the kernel: drop them
+    TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& g : ctx->host_graphs) cudaGraphExecDestroy(g.exec);
+    ctx->host_graphs.clear();
+    TF_CK(ctx, tf_plan_fused(ctx));
+    return TF_OK;
+}
+
+int tf_step_kernel(tf_ctx* ctx) {
+    if (!ctx) return TF_ERR_ARG;
+    if (!tf_fused_supported(ctx)) return TF_KERNEL_TILE;
+    if (ctx->tile_rows <= 0) TF_CK(ctx, tf_plan_fused(ctx));
+    return ctx->use_strip ? TF_KERNEL_STRIP : TF_KERNEL_TILE;
 }
 
 int tf_sync(tf_ctx* ctx) {
@@ -305,7 +342,10 @@ int tf_sync(tf_ctx* ctx) {
     TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
     if (flag != 0) {
         TF_CK(ctx, cudaMemsetAsync(ctx->d.flags, 0, sizeof(int), ctx->stream));
-        return fail(ctx, flag, "a device-side bounded wait timed out");
+        TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, flag, flag == TF_ERR_NONFINITE
+                                   ? "the check_every scan found NaN or Inf in the state"
+                                   : "a device-side bounded wait timed out");
     }
     return TF_OK;
 }

@@ -55,7 +55,7 @@ constexpr int shape_index() {
 // All CTAs of the launch meet here.  Thread 0 of each CTA arrives on a
 // global counter; the last arrival resets the counter and the finished
 // step's ticket slot, then bumps the generation the others spin on.
-__device__ __forceinline__ bool grid_barrier(EnsCtl* ctl, int k, int* err) {
+__device__ __forceinline__ bool grid_barrier(EnsCtl* ctl, int k, int* err, uint32_t polls) {
     __shared__ int s_ok;
     // Next step reads this step's stores through bulk copies (async proxy).
     tfp::fence_proxy_async_global();
@@ -77,7 +77,7 @@ __device__ __forceinline__ bool grid_barrier(EnsCtl* ctl, int k, int* err) {
                     ok = 0;
                     break;
                 }
-                if (++it > kBarrierPolls) {
+                if (++it > polls) {
                     atomicExch(err, TF_ERR_TIMEOUT);
                     atomicExch(&ctl->abort, 1);
                     ok = 0;
@@ -100,7 +100,7 @@ __device__ __forceinline__ bool grid_barrier(EnsCtl* ctl, int k, int* err) {
 template <bool DO_FD, bool DO_LBM, class S, int TY, int TXW>
 __global__ void __launch_bounds__(NT, 2)
 k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int steps, int fpar,
-      int ppar, int upar, EnsCtl* ctl) {
+      int ppar, int upar, EnsCtl* ctl, uint32_t polls, int held) {
     constexpr int TI = shape_index<TY, TXW>();
     using T = typename S::T;
     __shared__ __align__(8) uint64_t bar;
@@ -146,13 +146,17 @@ k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int st
             if ((G.nx & 3) == 0) ++phase;   // the tile went through the mbarrier
             __syncthreads();
         }
-        if (k + 1 < steps && !grid_barrier(ctl, k, groups[0].err)) return;
+        // Failure drill (tf_ensemble_fault_drill): CTA `held` leaves at the
+        // first barrier without arriving; it has no bulk copy in flight here.
+        if (k == 0 && (int)blockIdx.x == held && k + 1 < steps) return;
+        if (k + 1 < steps && !grid_barrier(ctl, k, groups[0].err, polls)) return;
     }
 }
 
 enum Mode { kPrologue = 0, kSteady = 1 };
 
-typedef void (*EnsKernel)(const EnsGroup*, int, long long, int, int, int, int, EnsCtl*);
+typedef void (*EnsKernel)(const EnsGroup*, int, long long, int, int, int, int, EnsCtl*, uint32_t,
+                          int);
 
 template <class S>
 EnsKernel pick(int mode, int ti) {
@@ -195,7 +199,9 @@ struct tf_ensemble {
     int sm_count = 0;
     double us[kCandidates] = {};
     bool graphs = true;
-    std::map<std::tuple<int, int64_t, int, int, int, int>, cudaGraphExec_t> cache;
+    uint32_t drill_polls = 0;                  // tf_ensemble_fault_drill: barrier poll limit (0: default)
+    int drill_held = -1;                       // ... and the CTA that does not arrive (-1: none)
+    std::map<std::tuple<int, int64_t, int, int, int, int, uint32_t, int>, cudaGraphExec_t> cache;
     int64_t launches = 0;
     std::string last_error;
 };
@@ -250,8 +256,9 @@ cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid, cuda
     const EnsGroup* g = e->d_groups;
     const int ng = (int)e->groups.size();
     const long long total = e->tiles[ti];
+    const uint32_t polls = e->drill_polls ? e->drill_polls : kBarrierPolls;
     return cudaLaunchKernelEx(&lc, kernel_for(e->storage, mode, ti), g, ng, total, steps, e->fpar,
-                              e->ppar, e->upar, e->d_ctl);
+                              e->ppar, e->upar, e->d_ctl, polls, e->drill_held);
 }
 
 // Issue one launch, from the graph cache when this shape was captured before.
@@ -260,7 +267,7 @@ cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid, cuda
 // launched into the caller's stream.
 int issue(tf_ensemble* e, int mode, int steps) {
     const auto key = std::make_tuple(mode, (int64_t)steps, e->fpar, e->ppar, e->upar,
-                                     mode == kPrologue ? 0 : e->cfg);
+                                     mode == kPrologue ? 0 : e->cfg, e->drill_polls, e->drill_held);
     const int grid = grid_for(e, mode, e->cfg);
     auto it = e->cache.find(key);
     if (it != e->cache.end()) {
@@ -550,5 +557,13 @@ int tf_ensemble_config(const tf_ensemble* e, int* tile_y, int* ctas_per_sm, int*
 }
 
 int64_t tf_ensemble_launches(const tf_ensemble* e) { return e ? e->launches : -1; }
+
+int tf_ensemble_fault_drill(tf_ensemble* e, uint32_t barrier_polls, int held_cta) {
+    if (!e) return TF_ERR_ARG;
+    if (held_cta < -1) return efail(e, TF_ERR_ARG, "held_cta must be -1 or a CTA index");
+    e->drill_polls = barrier_polls;
+    e->drill_held = held_cta;
+    return TF_OK;
+}
 
 }  // extern "C"

@@ -3,6 +3,7 @@
 // described in tf_fused.cuh).  Launch sequence per run: LBM-only prologue,
 // steady-state launches, FD-only epilogue before any read.
 #include "tf_fused.cuh"
+#include "tf_strip.cuh"
 
 namespace {
 
@@ -54,6 +55,7 @@ cudaError_t configure() {
     cudaError_t e = configure_one<true, true, S>();
     if (e == cudaSuccess) e = configure_one<false, true, S>();
     if (e == cudaSuccess) e = configure_one<true, false, S>();
+    if (e == cudaSuccess) e = configure_strip<S>();
     return e;
 }
 
@@ -67,18 +69,27 @@ struct Span {
     FusedCursor* cur;
 };
 
+template <class S>
+TileArgs<S> span_args(tf_ctx* ctx, const Span& sp) {
+    using T = typename S::T;
+    DevBuffers& d = ctx->d;
+    const int fc = sp.cur->fcur, pc = sp.cur->pcur, uc = sp.cur->ucur;
+    const long long N = ctx->N, b0 = sp.inst0;
+    return TileArgs<S>{static_cast<const T*>(d.f[fc]) + b0 * 18 * N, static_cast<T*>(d.f[fc ^ 1]) + b0 * 18 * N,
+                       d.phi[pc] + b0 * N, d.phi[pc ^ 1] + b0 * N, d.Q[pc] + b0 * 2 * N,
+                       d.Q[pc ^ 1] + b0 * 2 * N, d.u[uc] + b0 * 4 * N, d.u[uc ^ 1] + b0 * 4 * N,
+                       d.prm + b0, ctx->nx, ctx->ny, d.flags};
+}
+
 template <bool DO_FD, bool DO_LBM, class S, bool WIDE>
 void launch_as(tf_ctx* ctx, const Span& sp) {
     using G = Geo<DO_FD, DO_LBM, CtxGeo<WIDE>::TYM, CtxGeo<WIDE>::TXM>;
-    using T = typename S::T;
-    DevBuffers& d = ctx->d;
+    const TileArgs<S> a = span_args<S>(ctx, sp);
+    if (DO_FD && DO_LBM && ctx->use_strip) {
+        launch_strip<S>(a, dim3(ctx->strip_cols, ctx->strip_segs, sp.count), sp.stream);
+        return;
+    }
     const dim3 grid(ctx->tile_cols, sp.tile_rows, sp.count);
-    const int fc = sp.cur->fcur, pc = sp.cur->pcur, uc = sp.cur->ucur;
-    const long long N = ctx->N, b0 = sp.inst0;
-    const TileArgs<S> a{static_cast<const T*>(d.f[fc]) + b0 * 18 * N, static_cast<T*>(d.f[fc ^ 1]) + b0 * 18 * N,
-                        d.phi[pc] + b0 * N, d.phi[pc ^ 1] + b0 * N, d.Q[pc] + b0 * 2 * N,
-                        d.Q[pc ^ 1] + b0 * 2 * N, d.u[uc] + b0 * 4 * N, d.u[uc ^ 1] + b0 * 4 * N,
-                        d.prm + b0, ctx->nx, ctx->ny, d.flags};
     k_fused<DO_FD, DO_LBM, S, WIDE><<<grid, NT, G::SMEM, sp.stream>>>(a);
 }
 
@@ -129,6 +140,8 @@ void set_cursor(tf_ctx* ctx, const FusedCursor& c) {
 
 bool tf_fused_supported(const tf_ctx* ctx) { return ctx->n_sub == NS_FUSED; }
 
+bool tf_strip_supported(const tf_ctx* ctx) { return ctx->n_sub == NS_FUSED && ctx->nx % 4 == 0; }
+
 cudaError_t tf_configure_fused_kernels() {
     cudaError_t e = configure<PopF32>();
     if (e == cudaSuccess) e = configure<PopF16>();
@@ -159,20 +172,48 @@ int tile_rows_for(int ntx, int ny, int tym, int batch, long long slots) {
     return (int)(fit < most ? fit : most);
 }
 
+// Strip kernel plan: strips of at most ts::TWMAX columns (cut at multiples
+// of 4 by tile_col), and as many row segments as fill one wave of resident
+// CTAs, with segments of at least kMinSegRows rows (each segment recomputes
+// up to 12 rows of sub-step halo above and below it).
+constexpr int kMinSegRows = 32;
+// Whether TF_KERNEL_AUTO picks the strip kernel on multi-wave grids (it does
+// once it steps them faster than the tile kernel).
+constexpr bool kAutoStrip = false;
+
+int strip_segs_for(int ncols, int ny, int batch, long long slots) {
+    const long long per = (long long)ncols * batch;
+    long long segs = slots / per;
+    const long long most = ny / kMinSegRows;
+    if (segs > most) segs = most;
+    return segs < 1 ? 1 : (int)segs;
+}
+
 cudaError_t plan_tile_rows(tf_ctx* ctx) {
     if (ctx->tile_rows > 0) return cudaSuccess;
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm = 0, per_sm_strip = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, k_fused<true, true, PopF32, false>, NT, Geo<true, true, TY_DEFAULT, TX>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_strip, k_strip<PopF32>, NT,
+                                                          ts::SMEM);
     if (e != cudaSuccess) return e;
     const long long slots = (long long)sms * per_sm;
     ctx->wide_tiles = wide_for(ctx->nx, ctx->ny, ctx->batch, slots);
     const int txm = ctx->wide_tiles ? TX_WIDE : TX, tym = ctx->wide_tiles ? TY_WIDE : TY_DEFAULT;
     ctx->tile_cols = (ctx->nx + txm - 1) / txm;
     ctx->tile_rows = tile_rows_for(ctx->tile_cols, ctx->ny, tym, ctx->batch, slots);
+    // Steady-state kernel: AUTO takes the strip kernel on grids of several
+    // waves of tiles only where it is the faster one (kAutoStrip).
+    const bool can = tf_strip_supported(ctx) && per_sm_strip > 0;
+    ctx->use_strip = can && (ctx->step_kernel == TF_KERNEL_STRIP ||
+                             (ctx->step_kernel == TF_KERNEL_AUTO && kAutoStrip && ctx->wide_tiles));
+    ctx->strip_cols = (ctx->nx + ts::TWMAX - 1) / ts::TWMAX;
+    ctx->strip_segs = strip_segs_for(ctx->strip_cols, ctx->ny, ctx->batch,
+                                     (long long)sms * (per_sm_strip > 0 ? per_sm_strip : 1));
     return cudaSuccess;
 }
 
@@ -204,4 +245,9 @@ cudaError_t tf_fused_span(tf_ctx* ctx, int inst0, int count, int64_t n, bool flu
     // different streams, then share the resident CTA slots as one batched
     // launch would.
     return run(ctx, Span{inst0, count, ctx->tile_rows, stream, cur}, n, flush);
+}
+
+cudaError_t tf_plan_fused(tf_ctx* ctx) {
+    ctx->tile_rows = 0;
+    return plan_tile_rows(ctx);
 }

@@ -133,6 +133,10 @@ struct tf_ctx {
     int tile_rows = 0;               // fused path: tile rows per instance (0: not planned yet)
     int tile_cols = 0;               // fused path: tile columns per instance
     bool wide_tiles = false;         // fused path: the wide tile geometry
+    int step_kernel = TF_KERNEL_AUTO;// requested steady-state kernel (tf_set_step_kernel)
+    bool use_strip = false;          // fused path: steady-state steps run the strip kernel
+    int strip_cols = 0;              // strip kernel: strips per instance
+    int strip_segs = 0;              // strip kernel: row segments per strip
     int64_t steps = 0;
     int64_t launches = 0;            // kernels launched by this context
     int n_shell = 0;
@@ -181,6 +185,11 @@ bool tf_fused_supported(const tf_ctx* ctx);
 cudaError_t tf_fused_steps(tf_ctx* ctx, int64_t n);
 cudaError_t tf_fused_flush(tf_ctx* ctx);
 cudaError_t tf_configure_fused_kernels();
+// Plan (once per context, again after tf_set_step_kernel) the tile rows and
+// columns of the tile kernel and the strips and segments of the strip kernel.
+cudaError_t tf_plan_fused(tf_ctx* ctx);
+// Whether the strip kernel can step this context (nx a multiple of 4, n_sub = 5).
+bool tf_strip_supported(const tf_ctx* ctx);
 // Buffer cursors of the fused path (the fields of tf_ctx of the same names).
 struct FusedCursor {
     int fcur, pcur, ucur;
@@ -208,6 +217,9 @@ cudaError_t tf_launch_read_field(tf_ctx* ctx, int inst, int field, double* ddst)
 cudaError_t tf_launch_conserved(tf_ctx* ctx, int inst, double* dout8);
 cudaError_t tf_launch_phase_difference(tf_ctx* ctx, int inst, double* dout6);
 cudaError_t tf_launch_phi_stats(tf_ctx* ctx, int inst, double* dout2);
+// Scan the latest phi, Q and velocity planes of every instance for NaN / Inf;
+// a hit records TF_ERR_NONFINITE in d.flags[0] (kept until tf_sync reads it).
+cudaError_t tf_launch_nonfinite_scan(tf_ctx* ctx);
 // which: 0 = structure factor of phi - <phi>, 1 = kinetic-energy spectrum of u_c.
 // Writes n_shell shell sums to d.shell_out[0..n_shell-1] and the all-mode
 // total to d.shell_out[n_shell].

@@ -62,6 +62,21 @@ __global__ void __launch_bounds__(RB) k_finish(const double* __restrict__ part, 
         for (int k = 0; k < NV; ++k) out[k] = v[k];
 }
 
+// Non-finite scan of three FP32 arrays: any NaN or Inf sets *flag to
+// TF_ERR_NONFINITE unless another code is already recorded there.
+__global__ void __launch_bounds__(RB)
+k_scan_nonfinite(const float* __restrict__ a, long long na, const float* __restrict__ b,
+                 long long nb, const float* __restrict__ c, long long nc, int* __restrict__ flag) {
+    const long long total = na + nb + nc;
+    const long long stride = (long long)gridDim.x * RB;
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * RB + threadIdx.x; i < total; i += stride) {
+        const float v = i < na ? a[i] : (i < na + nb ? b[i - na] : c[i - na - nb]);
+        bad |= !isfinite(v);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(flag, 0, TF_ERR_NONFINITE);
+}
+
 // ---------------------------------------------------------------- init
 __global__ void __launch_bounds__(RB)
 k_init(void* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q, long long N, int b0,
@@ -703,6 +718,18 @@ cudaError_t tf_launch_phase_difference(tf_ctx* ctx, int inst, double* dout6) {
     k_phase<<<ctx->red_blocks, RB, 0, ctx->stream>>>(d.phi[ctx->pcur], d.macro, ctx->nx, ctx->ny,
                                                     inst, d.prm, d.red_part);
     k_finish<6><<<1, RB, 0, ctx->stream>>>(d.red_part, ctx->red_blocks, dout6);
+    return cudaGetLastError();
+}
+
+cudaError_t tf_launch_nonfinite_scan(tf_ctx* ctx) {
+    const DevBuffers& d = ctx->d;
+    const long long n = (long long)ctx->batch * ctx->N;
+    long long blocks = (7 * n + RB * 8 - 1) / (RB * 8);
+    if (blocks > 1216) blocks = 1216;
+    if (blocks < 1) blocks = 1;
+    k_scan_nonfinite<<<(int)blocks, RB, 0, ctx->stream>>>(d.phi[ctx->pcur], n, d.Q[ctx->pcur],
+                                                         2 * n, d.u[ctx->ucur], 4 * n, d.flags);
+    ctx->launches += 1;
     return cudaGetLastError();
 }
 

@@ -1,0 +1,451 @@
+// Steady-state coupled step on large grids: the strip-streaming kernel.
+//
+// Same step as k_fused<1, 1> (tf_fused.cuh): the pending five Cahn-Hilliard /
+// Beris-Edwards sub-steps FD(k) (Sec. III; Eq. 1, 11-12) with the stored
+// velocities u^k, then LBM(k+1) (forces, pull streaming, implicit-drag Guo
+// velocities, BGK + Guo collision of both D2Q9 fluids) from phi^{k+1},
+// Q^{k+1}.  Every value is computed with the same correctly rounded scalar
+// operations in the same order as k_fused (tfq helpers), so the two kernels
+// give bitwise the same state; only the schedule differs.
+//
+// Schedule.  One CTA owns a strip of tw <= 96 columns and a segment of S rows
+// of one instance.  Its window is the strip plus 12 columns on each side (120
+// columns: 30 lanes x 4 columns), and it walks down the segment in blocks of
+// R = 8 rows.  Per block every stage advances by R rows, each stage lagging
+// two rows behind the one it reads:
+//   input rows of phi^(0), Q^(0), u  : [L - R, L)            (bulk copies, one block ahead)
+//   sub-step s = 1..5 (phi^(s), Q^(s)): [L - 2s - R, L - 2s)  (mu^(s) on R + 2 rows first)
+//   stress and mu of phi^(5), Q^(5)   : [L - 11 - R, L - 11)
+//   LBM, stores of the new state      : [L - 12 - R, L - 12)
+// Sub-step s overwrites phi^(s-1), Q^(s-1) in place in one ring of rows; the
+// rows just above its block that the next block still needs as neighbours
+// (two of phi, one of Q) are saved first into per-stage shadow rows.  The
+// halo shrinks with the stage (phi^(s) is exact on rows and columns within
+// 12 - 2s of the segment / strip, Q^(s) within 7 - s), so nothing outside the
+// window or the segment is ever needed; rows outside a stage's exact range
+// are skipped, columns outside it are computed and never read.
+//
+// Population rows of the next block's LBM are bulk-prefetched into L2 one
+// block ahead, so the pulls of the LBM phase hit L2 while the sub-steps of
+// the following block run on the SM's other CTA.
+#pragma once
+
+#include "tf_fused.cuh"
+
+namespace {
+
+namespace ts {
+constexpr int R = 8;                    // rows per block: one per warp in the FD phases
+constexpr int NW = NT / 32;
+static_assert(NW == R, "one row per warp");
+constexpr int HALO = 12;                // window columns on each side of the strip
+constexpr int TWMAX = 96;               // widest strip
+constexpr int WW = TWMAX + 2 * HALO;    // window row (floats)
+constexpr int LANES = WW / 4;           // lanes holding window columns (4 each)
+static_assert(WW % 4 == 0 && LANES <= 32, "window row within one warp");
+constexpr int DP = 2 * R + 13;          // phi / Q ring rows
+constexpr int DU = R + 11;              // u ring rows
+constexpr int DS = R + 2;               // stress ring rows
+constexpr int SC0 = 8;                  // first window column kept in the stress ring
+constexpr int SW = 104;                 // stress ring columns [SC0, SC0 + SW)
+static_assert(SC0 + SW >= HALO + TWMAX + 1 + 1 && SC0 <= HALO - 1 - 3, "stress columns cover the LBM's");
+constexpr int NSUB = NS_FUSED;
+constexpr int OFF_PHI = 0;
+constexpr int OFF_QA = OFF_PHI + DP * WW;
+constexpr int OFF_QB = OFF_QA + DP * WW;
+constexpr int OFF_U = OFF_QB + DP * WW;              // u1x, u1y, u2x, u2y: DU rows each
+constexpr int OFF_SH = OFF_U + 4 * DU * WW;          // per stage: phi, phi, Q_xx, Q_xy rows
+constexpr int OFF_MU = OFF_SH + NSUB * 4 * WW;       // mu of the current sub-step: R + 2 rows
+constexpr int OFF_ST = OFF_MU + (R + 2) * WW;        // mu, sxx, sxy, syx, syy: DS rows x SW
+constexpr int NFLOAT = OFF_ST + 5 * DS * SW;
+constexpr size_t SMEM = (size_t)NFLOAT * sizeof(float);
+constexpr int ROWB = WW * 4;                         // bytes of one window row
+}  // namespace ts
+
+// Four adjacent columns of a lane as two pairs (columns 0,1 and 2,3).
+struct V4 {
+    tfq::f2 lo, hi;
+};
+
+__device__ __forceinline__ V4 ld4(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
+__device__ __forceinline__ void st4(float* p, const V4& v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.lo.x, v.lo.y, v.hi.x, v.hi.y);
+}
+
+// x-neighbours of each of a lane's four columns, as pairs (the outer ones
+// from the adjacent lanes): l = values at column - 1, r = at column + 1.
+__device__ __forceinline__ void nbr4(const V4& v, V4& l, V4& r) {
+    const float up = __shfl_up_sync(0xffffffffu, v.hi.y, 1);
+    const float dn = __shfl_down_sync(0xffffffffu, v.lo.x, 1);
+    l.lo = make_float2(up, v.lo.x);
+    l.hi = make_float2(v.lo.y, v.hi.x);
+    r.lo = make_float2(v.lo.y, v.hi.x);
+    r.hi = make_float2(v.hi.y, dn);
+}
+
+// Ring slots (rows t >= -HALO of the segment, or >= -1 for the stress ring).
+__device__ __forceinline__ int pslot(int t) { return (t + ts::HALO) % ts::DP; }
+__device__ __forceinline__ int uslot(int t) { return (t + ts::HALO) % ts::DU; }
+__device__ __forceinline__ int sslot(int t) { return (t + 1) % ts::DS; }
+
+template <class S>
+__global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
+    using namespace tfq;
+    using ts::R;
+    using ts::WW;
+    __shared__ __align__(8) uint64_t bars[2];   // [0] phi / Q blocks, [1] u blocks
+    float* const sm = tf_smem;
+    const int b = blockIdx.z;
+    const int nx = a.nx, ny = a.ny;
+    const long long N = (long long)nx * ny;
+    const int x0 = tile_col(blockIdx.x, gridDim.x, nx);
+    const int tw = tile_col(blockIdx.x + 1, gridDim.x, nx) - x0;
+    const int y0 = (int)((long long)blockIdx.y * ny / gridDim.y);
+    const int SG = (int)((long long)(blockIdx.y + 1) * ny / gridDim.y) - y0;
+    const DevParams P = a.prm[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = 4 * min(lane, ts::LANES - 1);   // this lane's first window column
+    const bool own = lane < ts::LANES;
+    const int nblk = (SG + 2 * ts::HALO + R - 1) / R;   // blocks (= iterations)
+
+    if (threadIdx.x == 0) {
+        tfp::mbar_init(&bars[0], 1);
+        tfp::mbar_init(&bars[1], 1);
+        tfp::fence_mbar_init();
+    }
+    __syncthreads();
+
+    // input plane pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y
+    auto gsrc = [&](int pl) -> const float* {
+        return pl == 0 ? a.phi_in + b * N
+                       : (pl < 3 ? a.Q_in + (2 * b + pl - 1) * N : a.u_in + (4 * b + pl - 3) * N);
+    };
+
+    // Bulk copies of input block `blk` (rows [-HALO + blk R, ...) up to
+    // S + HALO, S the segment rows): planes [p0, p1) of (phi, Q_xx, Q_xy, u1x, u1y, u2x, u2y) on
+    // barrier `bar`.  Warp 0 only; lane 0 posts the byte count first.
+    auto issue_block = [&](int blk, int p0, int p1, uint64_t* bar) {
+        const int t0 = -ts::HALO + blk * R;
+        const int t1 = min(t0 + R, SG + ts::HALO);
+        const int rows = t1 - t0;
+        if (lane == 0) tfp::mbar_arrive_expect_tx(bar, (uint32_t)(rows * (p1 - p0) * ts::ROWB));
+        __syncwarp();
+        for (int k = lane; k < rows * (p1 - p0); k += 32) {
+            const int pl = p0 + k / rows, t = t0 + k % rows;
+            float* dst = pl < 3 ? sm + (pl == 0 ? ts::OFF_PHI : (pl == 1 ? ts::OFF_QA : ts::OFF_QB)) +
+                                      pslot(t) * WW
+                                : sm + ts::OFF_U + (pl - 3) * ts::DU * WW + uslot(t) * WW;
+            bulk_row(dst, gsrc(pl), wrapc(y0 + t, ny), x0 - ts::HALO, WW, nx, bar);
+        }
+    };
+    // L2 prefetch of the population rows the LBM of block `blk` pulls.
+    constexpr int PF = 16 / (int)sizeof(typename S::T);
+    auto prefetch_pops = [&](int blk) {
+        const int eL = -ts::HALO + (blk + 1) * R - 12;        // LBM rows [eL - R, eL)
+        const int r0 = max(eL - R - 1, -1), r1 = min(eL + 1, SG + 1);
+        const int nr = r1 - r0;
+        if (nr <= 0 || nx % PF != 0) return;
+        const int xs = ((x0 - 1 + PF) / PF - 1) * PF;
+        const int xe = (x0 + tw + 1 + PF - 1) / PF * PF;
+        const typename S::T* F = a.fsrc + 18 * b * N;
+        for (int k = threadIdx.x; k < 18 * nr; k += NT) {
+            const int i = k / nr, t = r0 + k % nr;
+            prefetch_row(F + (long long)i * N, wrapc(y0 + t, ny), xs, xe - xs, nx);
+        }
+    };
+    // Give up after a bounded wait: report, let copies in flight land, leave.
+    auto bail = [&](int issued_pq, int issued_u) {
+        if (threadIdx.x == 0) atomicExch(a.err, TF_ERR_TIMEOUT);
+        if (issued_pq >= 0) tfp::wait_bounded(&bars[0], issued_pq & 1u, kWaitPolls);
+        if (issued_u >= 0) tfp::wait_bounded(&bars[1], issued_u & 1u, kWaitPolls);
+    };
+
+    if (warp == 0) {
+        issue_block(0, 0, 3, &bars[0]);
+        issue_block(0, 3, 7, &bars[1]);
+    }
+    prefetch_pops(0);
+
+    const float m4f = -4.f;
+    const f2 m4 = S2(m4f), half = S2(0.5f);
+    const f2 mu0 = S2(P.mu0), mu1 = S2(P.mu1), mu2 = S2(P.mu2), mu3 = S2(P.mu3);
+    const f2 kap = S2(-P.kappa), cref = S2(P.phi_ref);
+    // sub-step coefficients, exactly as fd_substep forms them
+    const float dt = P.dt_fd, dG = __fmul_rn(dt, P.GammaQ), hdt = 0.5f * dt;
+    const f2 M2x = S2(2.f * P.M), nhdt = S2(-hdt), hdt2 = S2(hdt);
+    const f2 cGA = S2(-__fmul_rn(dG, P.A_Q)), cGC = S2(-__fmul_rn(dG, P.C_Q));
+    const f2 cGK = S2(__fmul_rn(dG, P.K)), lamd = S2(__fmul_rn(dt, P.lam));
+    const f2 lamq = S2(0.25f * __fmul_rn(dt, P.lam));
+    auto flux = [&](f2 pv, f2 v1, f2 v2) { return M2(pv, F2(pv, B2(v1, v2), v2)); };
+
+#pragma unroll 1
+    for (int j = 0; j < nblk; ++j) {
+        const int L = -ts::HALO + (j + 1) * R;     // input rows < L are resident after the wait
+        {
+            const bool ok0 = tfp::wait_bounded(&bars[0], (uint32_t)j & 1u, kWaitPolls);
+            const bool ok1 = tfp::wait_bounded(&bars[1], (uint32_t)j & 1u, kWaitPolls);
+            if (__syncthreads_or(!(ok0 && ok1))) {
+                bail(j, j);
+                return;
+            }
+        }
+        // the next block's phi / Q rows (their ring slots were last read by
+        // the previous block's LBM) and its population rows
+        if (warp == 0 && j + 1 < nblk) issue_block(j + 1, 0, 3, &bars[0]);
+        if (j + 1 < nblk) prefetch_pops(j + 1);
+
+        // ---- the five sub-steps
+#pragma unroll 1
+        for (int s = 1; s <= ts::NSUB; ++s) {
+            const int E = L - 2 * s;                       // block rows [E - R, E)
+            const int lo = -(12 - 2 * s), hi = SG + 12 - 2 * s;     // exact rows of phi^(s)
+            const int qlo = -(7 - s), qhi = SG + 7 - s;             // exact rows of Q^(s)
+            float* const shp = sm + ts::OFF_SH + (s - 1) * 4 * WW;   // phi, phi, Q_xx, Q_xy
+            // row t of phi^(s-1): rows below the block come from the shadow
+            auto phi_row = [&](int t) -> const float* {
+                return t < E - R ? shp + (t - (E - R - 2)) * WW : sm + ts::OFF_PHI + pslot(t) * WW;
+            };
+            auto qa_row = [&](int t) -> const float* {
+                return t < E - R ? shp + 2 * WW : sm + ts::OFF_QA + pslot(t) * WW;
+            };
+            auto qb_row = [&](int t) -> const float* {
+                return t < E - R ? shp + 3 * WW : sm + ts::OFF_QB + pslot(t) * WW;
+            };
+            // (a) mu^(s) on rows [E - R - 1, E + 1)
+            for (int k = warp; k < R + 2; k += ts::NW) {
+                const int m = E - R - 1 + k;
+                if (m < lo - 1 || m >= hi + 1) continue;
+                const V4 pp = ld4(phi_row(m - 1) + col), pc = ld4(phi_row(m) + col),
+                         pn = ld4(phi_row(m + 1) + col);
+                V4 l, r, mu;
+                nbr4(pc, l, r);
+                {
+                    const f2 lap = F2(m4, pc.lo, A2(A2(l.lo, r.lo), A2(pp.lo, pn.lo)));
+                    const f2 poly = F2(pc.lo, F2(pc.lo, F2(pc.lo, mu3, mu2), mu1), mu0);
+                    mu.lo = F2(kap, lap, poly);
+                }
+                {
+                    const f2 lap = F2(m4, pc.hi, A2(A2(l.hi, r.hi), A2(pp.hi, pn.hi)));
+                    const f2 poly = F2(pc.hi, F2(pc.hi, F2(pc.hi, mu3, mu2), mu1), mu0);
+                    mu.hi = F2(kap, lap, poly);
+                }
+                if (own) st4(sm + ts::OFF_MU + k * WW + col, mu);
+            }
+            __syncthreads();
+            // (b) phi^(s), Q^(s) of this warp's row into registers
+            const int y = E - R + warp;
+            const bool vp = y >= lo && y < hi, vq = y >= qlo && y < qhi;
+            V4 nph, nqa, nqb;
+            if (vp) {
+                const float* mrow = sm + ts::OFF_MU + warp * WW + col;     // mu rows y-1, y, y+1
+                const float* u1x = sm + ts::OFF_U + 0 * ts::DU * WW + col;
+                const float* u1y = sm + ts::OFF_U + 1 * ts::DU * WW + col;
+                const float* u2x = sm + ts::OFF_U + 2 * ts::DU * WW + col;
+                const float* u2y = sm + ts::OFF_U + 3 * ts::DU * WW + col;
+                const int us = uslot(y - 1) * WW, uc = uslot(y) * WW, un = uslot(y + 1) * WW;
+                const V4 phs = ld4(phi_row(y - 1) + col), phc = ld4(phi_row(y) + col),
+                         phn = ld4(phi_row(y + 1) + col);
+                const V4 mus = ld4(mrow), muc = ld4(mrow + WW), mun = ld4(mrow + 2 * WW);
+                const V4 axc = ld4(u1x + uc), ays = ld4(u1y + us), ayn = ld4(u1y + un);
+                const V4 bxc = ld4(u2x + uc), bys = ld4(u2y + us), byn = ld4(u2y + un);
+                // fluxes J_x at row y, J_y at rows y -/+ 1
+                V4 jx, jys, jyn;
+                jx.lo = flux(A2(cref, phc.lo), axc.lo, bxc.lo);
+                jx.hi = flux(A2(cref, phc.hi), axc.hi, bxc.hi);
+                jys.lo = flux(A2(cref, phs.lo), ays.lo, bys.lo);
+                jys.hi = flux(A2(cref, phs.hi), ays.hi, bys.hi);
+                jyn.lo = flux(A2(cref, phn.lo), ayn.lo, byn.lo);
+                jyn.hi = flux(A2(cref, phn.hi), ayn.hi, byn.hi);
+                V4 jl, jr, ml, mr;
+                nbr4(jx, jl, jr);
+                nbr4(muc, ml, mr);
+                {
+                    const f2 dJ = A2(B2(jr.lo, jl.lo), B2(jyn.lo, jys.lo));
+                    const f2 lapmu = F2(m4, muc.lo, A2(A2(ml.lo, mr.lo), A2(mun.lo, mus.lo)));
+                    nph.lo = F2(hdt2, F2(M2x, lapmu, N2(dJ)), phc.lo);
+                }
+                {
+                    const f2 dJ = A2(B2(jr.hi, jl.hi), B2(jyn.hi, jys.hi));
+                    const f2 lapmu = F2(m4, muc.hi, A2(A2(ml.hi, mr.hi), A2(mun.hi, mus.hi)));
+                    nph.hi = F2(hdt2, F2(M2x, lapmu, N2(dJ)), phc.hi);
+                }
+                if (vq) {
+                    const V4 as = ld4(qa_row(y - 1) + col), ac = ld4(qa_row(y) + col),
+                             an = ld4(qa_row(y + 1) + col);
+                    const V4 bs = ld4(qb_row(y - 1) + col), bc = ld4(qb_row(y) + col),
+                             bn = ld4(qb_row(y + 1) + col);
+                    const V4 axs = ld4(u1x + us), axn = ld4(u1x + un), ayc = ld4(u1y + uc);
+                    V4 al, ar, bl, br, uxl, uxr, uyl, uyr;
+                    nbr4(ac, al, ar);
+                    nbr4(bc, bl, br);
+                    nbr4(axc, uxl, uxr);
+                    nbr4(ayc, uyl, uyr);
+                    auto qpair = [&](f2 a, f2 bq, f2 al_, f2 ar_, f2 an_, f2 as_, f2 bl_, f2 br_, f2 bn_,
+                                     f2 bs_, f2 uxl_, f2 uxr_, f2 uyl_, f2 uyr_, f2 axn_, f2 axs_,
+                                     f2 ayn_, f2 ays_, f2 axc_, f2 ayc_, f2& oa, f2& ob) {
+                        const f2 lapa = F2(m4, a, A2(A2(al_, ar_), A2(an_, as_)));
+                        const f2 lapb = F2(m4, bq, A2(A2(bl_, br_), A2(bn_, bs_)));
+                        const f2 cg = F2(cGC, F2(a, a, M2(bq, bq)), cGA);
+                        const f2 Dxx = B2(uxr_, uxl_), Dyy = B2(ayn_, ays_);
+                        const f2 Dxy = B2(axn_, axs_), Dyx = B2(uyr_, uyl_);
+                        const f2 E1 = B2(Dxx, Dyy), EX = A2(Dxy, Dyx);
+                        const f2 t1 = F2(half, A2(Dxx, Dyy), N2(F2(a, E1, M2(bq, EX))));
+                        const f2 cc = F2(lamd, t1, cg);
+                        const f2 hO = M2(hdt2, B2(Dxy, Dyx));
+                        const f2 nux = M2(nhdt, axc_), nuy = M2(nhdt, ayc_);
+                        oa = A2(a, F2(cc, a, F2(cGK, lapa, F2(lamq, E1, F2(hO, bq,
+                                F2(nux, B2(ar_, al_), M2(nuy, B2(an_, as_))))))));
+                        ob = A2(bq, F2(cc, bq, F2(cGK, lapb, F2(lamq, EX, F2(N2(hO), a,
+                                F2(nux, B2(br_, bl_), M2(nuy, B2(bn_, bs_))))))));
+                    };
+                    qpair(ac.lo, bc.lo, al.lo, ar.lo, an.lo, as.lo, bl.lo, br.lo, bn.lo, bs.lo,
+                          uxl.lo, uxr.lo, uyl.lo, uyr.lo, axn.lo, axs.lo, ayn.lo, ays.lo, axc.lo,
+                          ayc.lo, nqa.lo, nqb.lo);
+                    qpair(ac.hi, bc.hi, al.hi, ar.hi, an.hi, as.hi, bl.hi, br.hi, bn.hi, bs.hi,
+                          uxl.hi, uxr.hi, uyl.hi, uyr.hi, axn.hi, axs.hi, ayn.hi, ays.hi, axc.hi,
+                          ayc.hi, nqa.hi, nqb.hi);
+                }
+            }
+            __syncthreads();
+            // (c) save the rows the next block reads below its own (phi^(s-1)
+            // of rows E - 2, E - 1 and Q^(s-1) of row E - 1), then write in place
+            if (own) {
+                if (warp >= R - 2 && y >= lo - 2) {
+                    float* dst = shp + (warp - (R - 2)) * WW + col;
+                    st4(dst, ld4(sm + ts::OFF_PHI + pslot(y) * WW + col));
+                    if (warp == R - 1) {
+                        st4(shp + 2 * WW + col, ld4(sm + ts::OFF_QA + pslot(y) * WW + col));
+                        st4(shp + 3 * WW + col, ld4(sm + ts::OFF_QB + pslot(y) * WW + col));
+                    }
+                }
+                if (vp) st4(sm + ts::OFF_PHI + pslot(y) * WW + col, nph);
+                if (vq) {
+                    st4(sm + ts::OFF_QA + pslot(y) * WW + col, nqa);
+                    st4(sm + ts::OFF_QB + pslot(y) * WW + col, nqb);
+                }
+            }
+            if (s == ts::NSUB) tfp::fence_proxy_async_smem();   // u slots of the next copy
+            __syncthreads();
+            if (s == ts::NSUB && warp == 0 && j + 1 < nblk) issue_block(j + 1, 3, 7, &bars[1]);
+        }
+
+        // ---- mu and the fluid-1 stress of phi^(5), Q^(5) on rows [L - 11 - R, L - 11)
+        {
+            const int y = L - 11 - R + warp;
+            if (y >= -1 && y < SG + 1) {
+                const float* ps = sm + ts::OFF_PHI + pslot(y - 1) * WW + col;
+                const float* pc = sm + ts::OFF_PHI + pslot(y) * WW + col;
+                const float* pn = sm + ts::OFF_PHI + pslot(y + 1) * WW + col;
+                const int dqa = ts::OFF_QA - ts::OFF_PHI, dqb = ts::OFF_QB - ts::OFF_PHI;
+                const V4 dp = ld4(ps), dc = ld4(pc), dn = ld4(pn);
+                const V4 ap = ld4(ps + dqa), ac = ld4(pc + dqa), an = ld4(pn + dqa);
+                const V4 bp = ld4(ps + dqb), bc = ld4(pc + dqb), bn = ld4(pn + dqb);
+                V4 dl, dr, al, ar, bl, br;
+                nbr4(dc, dl, dr);
+                nbr4(ac, al, ar);
+                nbr4(bc, bl, br);
+                const PairStress r0 = stress2(P, dc.lo, dl.lo, dr.lo, dn.lo, dp.lo, ac.lo, al.lo,
+                                              ar.lo, an.lo, ap.lo, bc.lo, bl.lo, br.lo, bn.lo, bp.lo);
+                const PairStress r1 = stress2(P, dc.hi, dl.hi, dr.hi, dn.hi, dp.hi, ac.hi, al.hi,
+                                              ar.hi, an.hi, ap.hi, bc.hi, bl.hi, br.hi, bn.hi, bp.hi);
+                if (lane >= ts::SC0 / 4 && lane < (ts::SC0 + ts::SW) / 4) {
+                    float* st = sm + ts::OFF_ST + sslot(y) * ts::SW + (col - ts::SC0);
+                    constexpr int PL = ts::DS * ts::SW;
+                    st4(st, {r0.mu, r1.mu});
+                    st4(st + PL, {r0.sxx, r1.sxx});
+                    st4(st + 2 * PL, {r0.sxy, r1.sxy});
+                    st4(st + 3 * PL, {r0.syx, r1.syx});
+                    st4(st + 4 * PL, {r0.syy, r1.syy});
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- LBM of rows [L - 12 - R, L - 12) and stores of the new state
+        {
+            const int eL = L - 12;
+            const int r0 = max(eL - R, 0) - (eL - R), r1 = min(eL, SG) - (eL - R);   // block rows
+            const typename S::T* __restrict__ F1 = a.fsrc + 18 * b * N;
+            const typename S::T* __restrict__ F2p = F1 + 9 * N;
+            typename S::T* __restrict__ D1 = a.fdst + 18 * b * N;
+            typename S::T* __restrict__ D2 = D1 + 9 * N;
+            float* __restrict__ uo = a.u_out + 4 * b * N;
+            float* __restrict__ po = a.phi_out + b * N;
+            float* __restrict__ qo = a.Q_out + 2 * b * N;
+            const float* stb = sm + ts::OFF_ST - ts::SC0;   // stress ring, window columns
+            constexpr int PL = ts::DS * ts::SW;
+            if (r0 < r1) {
+                const int nsite = (r1 - r0) * tw;
+                int r = r0 + threadIdx.x / tw, cx = threadIdx.x % tw;
+                const int dr = NT / tw, dc = NT - dr * tw;
+#pragma unroll 1
+                for (int site = threadIdx.x; site < nsite; site += NT) {
+                    const int t = eL - R + r;             // segment row
+                    const int x = x0 + cx, gy = y0 + t;
+                    const int c = ts::HALO + cx;          // window column
+                    const float* ph = sm + ts::OFF_PHI + pslot(t) * WW;
+                    const float* phs = sm + ts::OFF_PHI + pslot(t - 1) * WW;
+                    const float* phn = sm + ts::OFF_PHI + pslot(t + 1) * WW;
+                    const float* sc = stb + sslot(t) * ts::SW;
+                    const float* ss = stb + sslot(t - 1) * ts::SW;
+                    const float* sn = stb + sslot(t + 1) * ts::SW;
+                    const int xp = x + 1 < nx ? x + 1 : 0, xm = x > 0 ? x - 1 : nx - 1;
+                    const int yp = gy + 1 < ny ? gy + 1 : 0, ym = gy > 0 ? gy - 1 : ny - 1;
+                    f2 f[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
+                        const int sy = d2q9_cy(i) == 0 ? gy : (d2q9_cy(i) > 0 ? ym : yp);
+                        const long long src = (long long)sy * nx + sx;
+                        f[i] = P2(S::load(F1 + i * N + src), S::load(F2p + i * N + src));
+                    }
+                    f2 u1, u2;
+                    lbm_site2(P, ph[c], P2(ph[c - 1], ph[c + 1]), P2(phs[c], phn[c]), sc[c],
+                              P2(sc[c - 1], sc[c + 1]), P2(ss[c], sn[c]),
+                              P2(sc[PL + c - 1], sc[PL + c + 1]), P2(ss[2 * PL + c], sn[2 * PL + c]),
+                              P2(sc[3 * PL + c - 1], sc[3 * PL + c + 1]),
+                              P2(ss[4 * PL + c], sn[4 * PL + c]), f, u1, u2);
+                    const long long g = (long long)gy * nx + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        S::store(D1 + i * N + g, f[i].x);
+                        S::store(D2 + i * N + g, f[i].y);
+                    }
+                    uo[g] = u1.x;
+                    uo[N + g] = u1.y;
+                    uo[2 * N + g] = u2.x;
+                    uo[3 * N + g] = u2.y;
+                    po[g] = ph[c];
+                    qo[g] = sm[ts::OFF_QA + pslot(t) * WW + c];
+                    qo[N + g] = sm[ts::OFF_QB + pslot(t) * WW + c];
+                    cx += dc;
+                    r += dr;
+                    if (cx >= tw) {
+                        cx -= tw;
+                        ++r;
+                    }
+                }
+            }
+        }
+        // the next block's copies overwrite ring rows this block read
+        tfp::fence_proxy_async_smem();
+        __syncthreads();
+    }
+}
+
+template <class S>
+cudaError_t configure_strip() {
+    return cudaFuncSetAttribute(k_strip<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ts::SMEM);
+}
+
+template <class S>
+void launch_strip(const TileArgs<S>& a, dim3 grid, cudaStream_t stream) {
+    k_strip<S><<<grid, NT, ts::SMEM, stream>>>(a);
+}
+
+}  // namespace

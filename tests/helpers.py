@@ -6,19 +6,23 @@ from paper_2511_00445_gb300 import _binding as B
 
 # Parity bar after 200 steps in FP32: max |X_gpu - X_oracle| normalised by the
 # oracle field's own spread max |X - <X>| (pointwise relative error of fields
-# that sit near a constant, phi ~ 1/2, u ~ 0, is ill-posed).  The two fluid
-# velocities are one flow and share one scale: the larger spread of u1, u2.
-# (On grids a few sites wide u2 can be ~100x smaller than u1; there a float32
-# restatement of the same arithmetic, independent of the GPU, already departs
-# from the FP64 oracle by ~2e-5 of u2's own spread, so u2's own spread is not
-# a meaningful yardstick for an FP32 method.)
+# that sit near a constant, phi ~ 1/2, u ~ 0, is ill-posed).  Velocities are
+# reported both against their own spread ("u1_own", "u2_own") and against the
+# shared scale of the flow, the larger spread of u1 and u2 ("u1", "u2").  On
+# grids below 32 x 32 u2 can be ~100x smaller than u1, and a float32
+# restatement of the step (tests/fp32_restatement.py, checked in
+# tests/test_fp32_floor.py) already departs from the FP64 oracle by more than
+# 1e-5 of u2's own spread there; from 32 x 32 up every field, u2 included, is
+# held to its own spread.
 TOL_200 = 1e-5
+OWN_SPREAD_MIN = 32     # grids with nx, ny >= this use the own-spread bars
 
 
 def oracle_params(sp: B.SolverParams) -> O.Params:
     return O.Params(nx=sp.nx, ny=sp.ny, tau1=sp.tau1, tau2=sp.tau2, rho1=sp.rho1, rho2=sp.rho2,
                     gamma=sp.gamma, zeta=sp.zeta, lam=sp.lam, K=sp.K, Gamma_Q=sp.Gamma_Q,
-                    A_Q=sp.A_Q, C_Q=sp.C_Q, M=sp.M, A_ch=sp.A_ch, kappa=sp.kappa, n_sub=sp.n_sub)
+                    A_Q=sp.A_Q, C_Q=sp.C_Q, M=sp.M, A_ch=sp.A_ch, kappa=sp.kappa, n_sub=sp.n_sub,
+                    dt=getattr(sp, "dt", 1.0))
 
 
 def read_state(tf: B.TwoFluid, inst: int) -> O.State:
@@ -67,7 +71,19 @@ def field_errors(tf: B.TwoFluid, inst: int, ref: O.State, p: O.Params) -> dict:
         "Qxy": rel_err(tf.read_field(inst, B.FIELD_QXY), ref.Qxy),
         "u1": max(uerr(u1[0], mc["u1"][0]), uerr(u1[1], mc["u1"][1])),
         "u2": max(uerr(u2[0], mc["u2"][0]), uerr(u2[1], mc["u2"][1])),
+        "u1_own": max(rel_err(u1[0], mc["u1"][0]), rel_err(u1[1], mc["u1"][1])),
+        "u2_own": max(rel_err(u2[0], mc["u2"][0]), rel_err(u2[1], mc["u2"][1])),
     }
+
+
+def assert_parity(err: dict, nx: int, ny: int, tol: float = TOL_200):
+    """The 200-step bar: phi, Q and the shared-scale velocities always; the
+    velocities' own spreads as well on grids of at least OWN_SPREAD_MIN."""
+    keys = ["phi", "Qxx", "Qxy", "u1", "u2"]
+    if nx >= OWN_SPREAD_MIN and ny >= OWN_SPREAD_MIN:
+        keys += ["u1_own", "u2_own"]
+    for k in keys:
+        assert err[k] < tol, (k, err)
 
 
 # ------------------------------------------------ oracle on windows of a grid

@@ -210,3 +210,29 @@ def test_ensemble_rejects_bad_members():
         B.Ensemble([a, B.TwoFluid(base.with_(storage=B.STORE_F16))])
     with pytest.raises(B.TwoFluidError):
         B.Ensemble([a, a])
+
+
+def test_grid_barrier_timeout_is_reported_and_recoverable():
+    """Failure detection of the persistent launch without a device fault: with
+    a short barrier poll limit and CTA 0 leaving at the first grid barrier
+    without arriving, every other CTA's bounded wait runs out, the launch ends
+    (tf_ensemble_sync returns, no hang) with TF_ERR_TIMEOUT, and afterwards the
+    same ensemble steps freshly initialised members bitwise like per-context
+    stepping."""
+    spec = groups_spec()
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.fault_drill(barrier_polls=1 << 12, held_cta=0)
+    ens.step(4)                                  # LBM-only pass, then one launch of 3 steps
+    with pytest.raises(B.TwoFluidError) as ei:
+        ens.sync()
+    assert ei.value.code == B.TF_ERR_TIMEOUT
+    ens.sync()                                   # reported once, then clear
+    ens.fault_drill(0, -1)
+    for g, tf in enumerate(grp):
+        for b in range(tf.batch):
+            tf.init_fields(seed=100 * g + b, phi0=0.5, dphi=0.01, S0=0.01)
+    ens.step(6)
+    ens.sync()
+    ens.close()
+    assert_same(grp, alone(spec, 6))

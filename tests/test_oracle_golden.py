@@ -126,3 +126,52 @@ def test_initial_concentration_has_printed_amplitude():
     theta = np.pi * u_theta
     assert theta.min() >= 0 and theta.max() < np.pi
     assert abs(theta.mean() - np.pi / 2) < 4 * (np.pi / math.sqrt(12)) / math.sqrt(n)
+
+
+def test_printed_time_step_gives_the_substep():
+    """Sec. III prints dt = 0.02 and five FD updates per lattice step,
+    dt_fd = dt / 5 = 0.004.  The oracle takes dt as a parameter (default 1,
+    the lattice-unit reading): run with the printed value, one lattice step of
+    uniform-Q relaxation (no flow) applies exactly five Euler updates of size
+    0.004, i.e. q <- q (1 - 0.004 Gamma_Q (A_Q + C_Q q^2)) five times."""
+    p = O.Params(nx=2, ny=2, dt=P["dt"], n_sub=int(P["n_sub"]), Gamma_Q=P["Gamma_Q"])
+    dt_fd = P["dt"] / P["n_sub"]
+    assert dt_fd == pytest.approx(0.004, abs=1e-18)
+    q0 = 0.05
+    zero = np.zeros((2, 2, 2))
+    _, a, b = O.substeps(np.full((2, 2), 0.5), np.full((2, 2), q0), np.zeros((2, 2)),
+                         zero, zero, p)
+    q = q0
+    for _ in range(int(P["n_sub"])):
+        q = q * (1 - dt_fd * p.Gamma_Q * (p.A_Q + p.C_Q * q * q))
+    assert np.allclose(a, q, rtol=1e-14) and np.allclose(b, 0.0)
+
+
+def _printed_run(dt, steps, n=32):
+    """The printed Sec. III set (eta = 0.5 as tau = 2, gamma = 0.1, K = 0.1,
+    Gamma_Q = 0.2, M = 0.2, A = 0.05, kappa = 0.1) at zeta = 0.01 from the
+    seeded initial condition; returns the first step whose state is not
+    finite, or None."""
+    p = O.Params(nx=n, ny=n, tau1=2.0, tau2=2.0, gamma=P["gamma"], K=P["K"], zeta=0.01,
+                 Gamma_Q=P["Gamma_Q"], M=P["M_phi"], A_ch=P["A"], kappa=P["kappa"], dt=dt)
+    up, ut = inputs.initial_draws(0, n, n)
+    Q = O.q_from_director(P["dQ"], np.pi * ut)
+    s = O.state_from_fields(P["phi0"] + P["dphi0"] * (2 * up - 1), Q[0, 0], Q[0, 1], p)
+    with np.errstate(all="ignore"):
+        for k in range(steps):
+            s = O.step(s, p)
+            if not (np.isfinite(s.phi).all() and np.abs(s.phi).max() < 10):
+                return k + 1
+    return None
+
+
+def test_printed_parameter_set_stability():
+    """Which reading of the printed time step the printed parameters survive
+    (2000 steps, 32 x 32): with dt = 1 (the rates in lattice units) the set goes
+    unstable within ~1100 steps; with the literal dt = 0.02 (dt_fd = 0.004) it
+    stays finite.  The blow-up at dt = 1 needs the flow-alignment coupling and
+    K = 0.1 (lambda = 0 or K <= 0.07 stay finite) and a five times smaller FD
+    step does not remove it: it is not the explicit FD step's limit."""
+    assert _printed_run(P["dt"], 2000) is None
+    blew = _printed_run(1.0, 2000)
+    assert blew is not None and blew < 2000

@@ -368,6 +368,59 @@ def test_ldg_bulk_relaxation():
     assert abs(q - math.sqrt(qe2)) < 1e-10
 
 
+@pytest.mark.parametrize("nx,ny,mx,my,comp", [(16, 4, 3, 0, 0), (12, 10, 2, 3, 1),
+                                             (8, 8, 4, 1, 0)])
+def test_frank_term_single_mode_decay(nx, ny, mx, my, comp):
+    """Frank part of the molecular field (Eq. 7-8): with A_Q = C_Q = 0 and no
+    flow, H = K lap(Q), so the Beris-Edwards sub-step (Eq. 11) is the explicit
+    heat equation Q <- Q + dt_fd Gamma_Q K lap(Q).  A Fourier mode of the
+    periodic grid is an eigenvector of the five-point Laplacian with
+    eigenvalue -k2, k2 = 4 sin^2(pi m_x / nx) + 4 sin^2(pi m_y / ny), so every
+    sub-step multiplies it by exactly 1 - dt_fd Gamma_Q K k2.  A wrong sign or
+    factor on K lap(Q), or a Laplacian missing from one component, fails."""
+    p = P0.with_(nx=nx, ny=ny, A_Q=0.0, C_Q=0.0, K=0.37, Gamma_Q=0.45, lam=0.8)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    mode = np.cos(2 * np.pi * (mx * x / nx + my * y / ny) + 0.3)
+    Qxx = 0.02 * mode if comp == 0 else np.zeros_like(mode)
+    Qxy = 0.02 * mode if comp == 1 else np.zeros_like(mode)
+    k2 = 4 * math.sin(math.pi * mx / nx) ** 2 + 4 * math.sin(math.pi * my / ny) ** 2
+    dt_fd = p.dt / p.n_sub
+    g = 1 - dt_fd * p.Gamma_Q * p.K * k2
+    zero = np.zeros((2, ny, nx))
+    phi = np.full((ny, nx), 0.5)
+    # H itself: -k2 K times the mode in the excited component, zero in the other
+    H = O.molecular_field(O.q_tensor(Qxx, Qxy), p)
+    exc, other = (H[0, 0], H[0, 1]) if comp == 0 else (H[0, 1], H[0, 0])
+    assert np.allclose(exc, -p.K * k2 * 0.02 * mode, rtol=0, atol=1e-15)
+    assert np.allclose(other, 0, atol=1e-17)
+    assert np.allclose(H[1, 1], -H[0, 0], atol=1e-17) and np.allclose(H[1, 0], H[0, 1], atol=1e-17)
+    # every sub-step scales the mode by g (no flow: phi stays put)
+    ph, a, b = phi, Qxx, Qxy
+    for s in range(1, 4 * p.n_sub + 1):
+        ph, a, b = O.substeps(ph, a, b, zero, zero, p.with_(n_sub=1, dt=dt_fd))
+        exc = a if comp == 0 else b
+        assert np.allclose(exc, 0.02 * mode * g ** s, rtol=0, atol=1e-12 * 0.02)
+        assert np.allclose(b if comp == 0 else a, 0, atol=1e-17)
+    assert np.allclose(ph, 0.5, atol=1e-16)
+
+
+def test_fd_time_step_scales_the_substeps():
+    """dt_fd = dt / n_sub (Sec. III): with the relaxation alone (uniform Q, no
+    flow) one lattice step of n_sub sub-steps follows the scalar Euler map with
+    that step, for the lattice-unit reading dt = 1 and the printed dt = 0.02."""
+    for dt in (1.0, 0.02):
+        p = P0.with_(nx=2, ny=2, dt=dt)
+        q0 = 0.05
+        Qxx = np.full((2, 2), q0)
+        Qxy = np.zeros((2, 2))
+        zero = np.zeros((2, 2, 2))
+        _, a, _ = O.substeps(np.full((2, 2), 0.5), Qxx, Qxy, zero, zero, p)
+        q = q0
+        for _ in range(p.n_sub):
+            q = q * (1 - (dt / p.n_sub) * p.Gamma_Q * (p.A_Q + p.C_Q * q * q))
+        assert np.allclose(a, q, rtol=1e-14)
+
+
 def test_velocity_gradient_index_order():
     """W_ij = d_j u_i: a shear u_x(y) has only W_xy."""
     N = 16

@@ -63,3 +63,37 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert _call(lib, dev, 0, 0.0, out, stream) == B.TF_ERR_ARG
     assert lib.tf_phi_stats_noalloc(None, 8, 0.0, ctypes.c_void_p(out.data_ptr()),
                                     ctypes.c_void_p(stream.cuda_stream)) == B.TF_ERR_ARG
+
+
+def _host_stats(v32):
+    v = v32.astype(np.float64)
+    m = v.mean()
+    return m, float(np.sqrt(np.mean((v - m) ** 2)))
+
+
+def test_noalloc_at_its_size_limit_and_after_larger_calls():
+    """n = TF_NOALLOC_MAX_ELEMS (every partial slot) and MAX - 1 (a ragged last
+    block), each preceded and followed by small calls: every result matches an
+    FP64 two-pass host computation of the same FP32 values, so no partial left
+    by an earlier, larger call leaks into a later one.  The large inputs are
+    not centred (mean 300, spread ~1e-2)."""
+    import torch
+
+    from paper_2511_00445_gb300 import build
+    build.build()
+    lib = B.load_library()
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(7)
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    small = (0.01 * rng.standard_normal(5000)).astype(np.float32)
+    big = (300.0 + 0.01 * rng.standard_normal(B.NOALLOC_MAX_ELEMS)).astype(np.float32)
+    cases = [small, big, small[:4097], big[:-1], small[:1], small]
+    for v in cases:
+        dev = torch.tensor(v, device="cuda")
+        out.fill_(float("nan"))
+        assert _call(lib, dev, dev.numel(), 0.25, out, stream) == B.TF_OK
+        stream.synchronize()
+        m, s = out.tolist()
+        hm, hs = _host_stats(v)
+        assert abs(m - (0.25 + hm)) <= 1e-12 * max(1.0, abs(hm)), (v.size, m, hm)
+        assert abs(s - hs) <= 1e-9 * hs + 1e-300, (v.size, s, hs)
