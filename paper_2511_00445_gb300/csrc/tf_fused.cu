@@ -140,7 +140,11 @@ void set_cursor(tf_ctx* ctx, const FusedCursor& c) {
 
 bool tf_fused_supported(const tf_ctx* ctx) { return ctx->n_sub == NS_FUSED; }
 
-bool tf_strip_supported(const tf_ctx* ctx) { return ctx->n_sub == NS_FUSED && ctx->nx % 4 == 0; }
+// The strip kernel indexes one fluid's nine population planes with 32-bit
+// element offsets: 9 nx ny must stay below 2^31.
+bool tf_strip_supported(const tf_ctx* ctx) {
+    return ctx->n_sub == NS_FUSED && ctx->nx % 4 == 0 && 9LL * ctx->N < (1LL << 31);
+}
 
 cudaError_t tf_configure_fused_kernels() {
     cudaError_t e = configure<PopF32>();

@@ -1,15 +1,23 @@
 // Paired FP32 arithmetic for the fused step: each lane carries two adjacent
-// columns, and every operation is applied to both with its own correctly
-// rounded scalar instruction (__fadd_rn, __fsub_rn, __fmul_rn, __fmaf_rn).
-// These are never contracted or reassociated, so the prologue, epilogue and
-// steady-state kernels produce bitwise the same values for the same inputs,
-// and every value equals the IEEE result of the written operation order.
+// columns (or the two fluids of a site), and every operation returns, for
+// each of the two elements, the correctly rounded IEEE result of the written
+// operation.  Nothing is contracted or reassociated, so the prologue,
+// epilogue, tile, strip and ensemble kernels produce bitwise the same values
+// for the same inputs.
 //
-// The packed FP32x2 forms (the __f*2_rn intrinsics, or add/sub/mul/fma.rn.f32x2
-// in inline PTX) were tried here and rejected: in this kernel a few sites per
-// sub-step came out one ulp away from the written order, consistently with an
-// unrounded product feeding a subtraction, and where that happened moved with
-// code layout, so two kernels running the same sub-step disagreed.
+// Every pair operation is one packed fused multiply-add (fma.rn.f32x2, two
+// FP32 lanes per instruction), which halves the FP32 instructions of a pair:
+//   a * b = fma(a, b, -0),  a + b = fma(a, 1, b),  a - b = fma(b, -1, a),
+//   -a = fma(a, -1, -0).
+// Each is exact to the scalar operation: the product or sum is formed exactly
+// and rounded once, and the signed zero added or the factor +-1 changes neither
+// the value nor the sign of a zero result.  Because every operation is already
+// a single FMA, the compiler has no separate multiply and add left to fuse: an
+// earlier version that wrote the packed forms as separate add/sub/mul (the
+// __f*2_rn intrinsics and add/sub/mul.rn.f32x2) saw a product fed unrounded into
+// a following subtraction at a few sites, in places that moved with code layout.
+// Compiling with -DTF_SCALAR_FP32 selects per-element scalar intrinsics
+// (__fadd_rn, __fsub_rn, __fmul_rn, __fmaf_rn) with identical results.
 #pragma once
 
 #include "tf_internal.h"
@@ -19,6 +27,7 @@ namespace tfq {
 typedef float2 f2;
 __device__ __forceinline__ f2 S2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ f2 P2(float a, float b) { return make_float2(a, b); }
+#ifdef TF_SCALAR_FP32
 __device__ __forceinline__ f2 A2(f2 a, f2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
 __device__ __forceinline__ f2 B2(f2 a, f2 b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
 __device__ __forceinline__ f2 M2(f2 a, f2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
@@ -27,6 +36,28 @@ __device__ __forceinline__ f2 F2(f2 a, f2 b, f2 c) {
     return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
 }
 __device__ __forceinline__ f2 N2(f2 a) { return make_float2(-a.x, -a.y); }
+#else
+__device__ __forceinline__ unsigned long long pk(f2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ f2 upk(unsigned long long r) {
+    f2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+// a * b + c with a single rounding per element
+__device__ __forceinline__ f2 F2(f2 a, f2 b, f2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+__device__ __forceinline__ f2 M2(f2 a, f2 b) { return F2(a, b, make_float2(-0.f, -0.f)); }
+__device__ __forceinline__ f2 A2(f2 a, f2 b) { return F2(a, make_float2(1.f, 1.f), b); }
+__device__ __forceinline__ f2 B2(f2 a, f2 b) { return F2(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ f2 N2(f2 a) { return F2(a, make_float2(-1.f, -1.f), make_float2(-0.f, -0.f)); }
+#endif
 __device__ __forceinline__ f2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 
 // Left / right x-neighbours of a lane's column pair (2P, 2P+1): the outer

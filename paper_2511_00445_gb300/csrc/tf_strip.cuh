@@ -14,7 +14,8 @@
 // R = 8 rows.  Per block every stage advances by R rows, each stage lagging
 // two rows behind the one it reads:
 //   input rows of phi^(0), Q^(0), u  : [L - R, L)            (bulk copies, one block ahead)
-//   sub-step s = 1..5 (phi^(s), Q^(s)): [L - 2s - R, L - 2s)  (mu^(s) on R + 2 rows first)
+//   sub-step s = 1..5 (phi^(s), Q^(s)): [L - 2s - R, L - 2s)  (each warp one row; it
+//                                       evaluates mu^(s) on its row and the two beside it)
 //   stress and mu of phi^(5), Q^(5)   : [L - 11 - R, L - 11)
 //   LBM, stores of the new state      : [L - 12 - R, L - 12)
 // Sub-step s overwrites phi^(s-1), Q^(s-1) in place in one ring of rows; the
@@ -25,9 +26,10 @@
 // window or the segment is ever needed; rows outside a stage's exact range
 // are skipped, columns outside it are computed and never read.
 //
-// Population rows of the next block's LBM are bulk-prefetched into L2 one
-// block ahead, so the pulls of the LBM phase hit L2 while the sub-steps of
-// the following block run on the SM's other CTA.
+// The LBM pulls its populations straight from global memory; each thread
+// issues the next site's pulls before computing the current one.  (Bulk L2
+// prefetches of the next block's population and velocity rows were measured
+// and removed: at 2048^2 they cost 83 us per step, 525 -> 442 us.)
 #pragma once
 
 #include "tf_fused.cuh"
@@ -50,13 +52,16 @@ constexpr int SC0 = 8;                  // first window column kept in the stres
 constexpr int SW = 104;                 // stress ring columns [SC0, SC0 + SW)
 static_assert(SC0 + SW >= HALO + TWMAX + 1 + 1 && SC0 <= HALO - 1 - 3, "stress columns cover the LBM's");
 constexpr int NSUB = NS_FUSED;
+// phi, Q_xx and Q_xy each have DP ring rows followed by two shadow rows per
+// sub-step, at one common field stride, so a row index addresses all three.
+constexpr int SH0 = DP;                              // first shadow row index
+constexpr int FROWS = DP + 2 * NSUB;
+constexpr int FS = FROWS * WW;                       // field stride
 constexpr int OFF_PHI = 0;
-constexpr int OFF_QA = OFF_PHI + DP * WW;
-constexpr int OFF_QB = OFF_QA + DP * WW;
-constexpr int OFF_U = OFF_QB + DP * WW;              // u1x, u1y, u2x, u2y: DU rows each
-constexpr int OFF_SH = OFF_U + 4 * DU * WW;          // per stage: phi, phi, Q_xx, Q_xy rows
-constexpr int OFF_MU = OFF_SH + NSUB * 4 * WW;       // mu of the current sub-step: R + 2 rows
-constexpr int OFF_ST = OFF_MU + (R + 2) * WW;        // mu, sxx, sxy, syx, syy: DS rows x SW
+constexpr int OFF_QA = OFF_PHI + FS;
+constexpr int OFF_QB = OFF_QA + FS;
+constexpr int OFF_U = OFF_QB + FS;                   // u1x, u1y, u2x, u2y: DU rows each
+constexpr int OFF_ST = OFF_U + 4 * DU * WW;          // mu, sxx, sxy, syx, syy: DS rows x SW
 constexpr int NFLOAT = OFF_ST + 5 * DS * SW;
 constexpr size_t SMEM = (size_t)NFLOAT * sizeof(float);
 constexpr int ROWB = WW * 4;                         // bytes of one window row
@@ -87,10 +92,17 @@ __device__ __forceinline__ void nbr4(const V4& v, V4& l, V4& r) {
     r.hi = make_float2(v.hi.y, dn);
 }
 
-// Ring slots (rows t >= -HALO of the segment, or >= -1 for the stress ring).
-__device__ __forceinline__ int pslot(int t) { return (t + ts::HALO) % ts::DP; }
-__device__ __forceinline__ int uslot(int t) { return (t + ts::HALO) % ts::DU; }
-__device__ __forceinline__ int sslot(int t) { return (t + 1) % ts::DS; }
+// Ring slots of segment row t (any t >= -3 DP; rows below -HALO, or -1 for
+// the stress ring, are only touched by rows that are skipped).  One modulo
+// per phase; neighbouring rows step from it with a conditional wrap.
+__device__ __forceinline__ int pslot(int t) { return (t + ts::HALO + 3 * ts::DP) % ts::DP; }
+__device__ __forceinline__ int uslot(int t) { return (t + ts::HALO + 3 * ts::DU) % ts::DU; }
+__device__ __forceinline__ int sslot(int t) { return (t + 1 + 3 * ts::DS) % ts::DS; }
+template <int D>
+__device__ __forceinline__ int step_slot(int base, int k) {   // (base + k) mod D, 0 <= k < D
+    const int v = base + k;
+    return v >= D ? v - D : v;
+}
 
 template <class S>
 __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
@@ -142,21 +154,6 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             bulk_row(dst, gsrc(pl), wrapc(y0 + t, ny), x0 - ts::HALO, WW, nx, bar);
         }
     };
-    // L2 prefetch of the population rows the LBM of block `blk` pulls.
-    constexpr int PF = 16 / (int)sizeof(typename S::T);
-    auto prefetch_pops = [&](int blk) {
-        const int eL = -ts::HALO + (blk + 1) * R - 12;        // LBM rows [eL - R, eL)
-        const int r0 = max(eL - R - 1, -1), r1 = min(eL + 1, SG + 1);
-        const int nr = r1 - r0;
-        if (nr <= 0 || nx % PF != 0) return;
-        const int xs = ((x0 - 1 + PF) / PF - 1) * PF;
-        const int xe = (x0 + tw + 1 + PF - 1) / PF * PF;
-        const typename S::T* F = a.fsrc + 18 * b * N;
-        for (int k = threadIdx.x; k < 18 * nr; k += NT) {
-            const int i = k / nr, t = r0 + k % nr;
-            prefetch_row(F + (long long)i * N, wrapc(y0 + t, ny), xs, xe - xs, nx);
-        }
-    };
     // Give up after a bounded wait: report, let copies in flight land, leave.
     auto bail = [&](int issued_pq, int issued_u) {
         if (threadIdx.x == 0) atomicExch(a.err, TF_ERR_TIMEOUT);
@@ -168,7 +165,6 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         issue_block(0, 0, 3, &bars[0]);
         issue_block(0, 3, 7, &bars[1]);
     }
-    prefetch_pops(0);
 
     const float m4f = -4.f;
     const f2 m4 = S2(m4f), half = S2(0.5f);
@@ -194,9 +190,8 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             }
         }
         // the next block's phi / Q rows (their ring slots were last read by
-        // the previous block's LBM) and its population rows
+        // the previous block's LBM)
         if (warp == 0 && j + 1 < nblk) issue_block(j + 1, 0, 3, &bars[0]);
-        if (j + 1 < nblk) prefetch_pops(j + 1);
 
         // ---- the five sub-steps
 #pragma unroll 1
@@ -204,52 +199,51 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             const int E = L - 2 * s;                       // block rows [E - R, E)
             const int lo = -(12 - 2 * s), hi = SG + 12 - 2 * s;     // exact rows of phi^(s)
             const int qlo = -(7 - s), qhi = SG + 7 - s;             // exact rows of Q^(s)
-            float* const shp = sm + ts::OFF_SH + (s - 1) * 4 * WW;   // phi, phi, Q_xx, Q_xy
-            // row t of phi^(s-1): rows below the block come from the shadow
-            auto phi_row = [&](int t) -> const float* {
-                return t < E - R ? shp + (t - (E - R - 2)) * WW : sm + ts::OFF_PHI + pslot(t) * WW;
+            // the stage touches rows [E - R - 2, E + 2) of phi / Q and [E - R - 1,
+            // E + 1) of u; the two rows below the block are this stage's shadows
+            const int tb = E - R - 2, pb = pslot(tb), ub = uslot(tb + 1);
+            const int shr = ts::SH0 + 2 * (s - 1);
+            // row index (ring slot or shadow) of row t of phi^(s-1), Q^(s-1)
+            auto ridx = [&](int t) {
+                const int k = t - tb;
+                return k < 2 ? shr + k : step_slot<ts::DP>(pb, k);
             };
-            auto qa_row = [&](int t) -> const float* {
-                return t < E - R ? shp + 2 * WW : sm + ts::OFF_QA + pslot(t) * WW;
-            };
-            auto qb_row = [&](int t) -> const float* {
-                return t < E - R ? shp + 3 * WW : sm + ts::OFF_QB + pslot(t) * WW;
-            };
-            // (a) mu^(s) on rows [E - R - 1, E + 1)
-            for (int k = warp; k < R + 2; k += ts::NW) {
-                const int m = E - R - 1 + k;
-                if (m < lo - 1 || m >= hi + 1) continue;
-                const V4 pp = ld4(phi_row(m - 1) + col), pc = ld4(phi_row(m) + col),
-                         pn = ld4(phi_row(m + 1) + col);
-                V4 l, r, mu;
-                nbr4(pc, l, r);
-                {
-                    const f2 lap = F2(m4, pc.lo, A2(A2(l.lo, r.lo), A2(pp.lo, pn.lo)));
-                    const f2 poly = F2(pc.lo, F2(pc.lo, F2(pc.lo, mu3, mu2), mu1), mu0);
-                    mu.lo = F2(kap, lap, poly);
-                }
-                {
-                    const f2 lap = F2(m4, pc.hi, A2(A2(l.hi, r.hi), A2(pp.hi, pn.hi)));
-                    const f2 poly = F2(pc.hi, F2(pc.hi, F2(pc.hi, mu3, mu2), mu1), mu0);
-                    mu.hi = F2(kap, lap, poly);
-                }
-                if (own) st4(sm + ts::OFF_MU + k * WW + col, mu);
-            }
-            __syncthreads();
-            // (b) phi^(s), Q^(s) of this warp's row into registers
+            auto urow = [&](int t) { return step_slot<ts::DU>(ub, t - tb - 1) * WW; };
+            auto phi_row = [&](int t) -> const float* { return sm + ts::OFF_PHI + ridx(t) * WW; };
+            auto qa_row = [&](int t) -> const float* { return sm + ts::OFF_QA + ridx(t) * WW; };
+            auto qb_row = [&](int t) -> const float* { return sm + ts::OFF_QB + ridx(t) * WW; };
+            // (a) phi^(s), Q^(s) of this warp's row into registers, with mu^(s)
+            // of rows y-1, y, y+1 evaluated here from phi^(s-1) rows y-2 .. y+2
             const int y = E - R + warp;
             const bool vp = y >= lo && y < hi, vq = y >= qlo && y < qhi;
             V4 nph, nqa, nqb;
             if (vp) {
-                const float* mrow = sm + ts::OFF_MU + warp * WW + col;     // mu rows y-1, y, y+1
                 const float* u1x = sm + ts::OFF_U + 0 * ts::DU * WW + col;
                 const float* u1y = sm + ts::OFF_U + 1 * ts::DU * WW + col;
                 const float* u2x = sm + ts::OFF_U + 2 * ts::DU * WW + col;
                 const float* u2y = sm + ts::OFF_U + 3 * ts::DU * WW + col;
-                const int us = uslot(y - 1) * WW, uc = uslot(y) * WW, un = uslot(y + 1) * WW;
-                const V4 phs = ld4(phi_row(y - 1) + col), phc = ld4(phi_row(y) + col),
-                         phn = ld4(phi_row(y + 1) + col);
-                const V4 mus = ld4(mrow), muc = ld4(mrow + WW), mun = ld4(mrow + 2 * WW);
+                const int us = urow(y - 1), uc = urow(y), un = urow(y + 1);
+                const V4 phss = ld4(phi_row(y - 2) + col), phs = ld4(phi_row(y - 1) + col),
+                         phc = ld4(phi_row(y) + col), phn = ld4(phi_row(y + 1) + col),
+                         phnn = ld4(phi_row(y + 2) + col);
+                // mu = -kappa lap(phi) + A_ch f'(phi) (Eq. 2) of the middle row
+                auto mu_row = [&](const V4& pp, const V4& pc, const V4& pn) {
+                    V4 l, r, mu;
+                    nbr4(pc, l, r);
+                    {
+                        const f2 lap = F2(m4, pc.lo, A2(A2(l.lo, r.lo), A2(pp.lo, pn.lo)));
+                        const f2 poly = F2(pc.lo, F2(pc.lo, F2(pc.lo, mu3, mu2), mu1), mu0);
+                        mu.lo = F2(kap, lap, poly);
+                    }
+                    {
+                        const f2 lap = F2(m4, pc.hi, A2(A2(l.hi, r.hi), A2(pp.hi, pn.hi)));
+                        const f2 poly = F2(pc.hi, F2(pc.hi, F2(pc.hi, mu3, mu2), mu1), mu0);
+                        mu.hi = F2(kap, lap, poly);
+                    }
+                    return mu;
+                };
+                const V4 mus = mu_row(phss, phs, phc), muc = mu_row(phs, phc, phn),
+                         mun = mu_row(phc, phn, phnn);
                 const V4 axc = ld4(u1x + uc), ays = ld4(u1y + us), ayn = ld4(u1y + un);
                 const V4 bxc = ld4(u2x + uc), bys = ld4(u2y + us), byn = ld4(u2y + un);
                 // fluxes J_x at row y, J_y at rows y -/+ 1
@@ -311,21 +305,20 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 }
             }
             __syncthreads();
-            // (c) save the rows the next block reads below its own (phi^(s-1)
+            // (b) save the rows the next block reads below its own (phi^(s-1)
             // of rows E - 2, E - 1 and Q^(s-1) of row E - 1), then write in place
             if (own) {
+                const int py = step_slot<ts::DP>(pb, y - tb) * WW + col;
                 if (warp >= R - 2 && y >= lo - 2) {
-                    float* dst = shp + (warp - (R - 2)) * WW + col;
-                    st4(dst, ld4(sm + ts::OFF_PHI + pslot(y) * WW + col));
-                    if (warp == R - 1) {
-                        st4(shp + 2 * WW + col, ld4(sm + ts::OFF_QA + pslot(y) * WW + col));
-                        st4(shp + 3 * WW + col, ld4(sm + ts::OFF_QB + pslot(y) * WW + col));
-                    }
+                    const int sh = (shr + warp - (R - 2)) * WW + col;
+                    st4(sm + ts::OFF_PHI + sh, ld4(sm + ts::OFF_PHI + py));
+                    st4(sm + ts::OFF_QA + sh, ld4(sm + ts::OFF_QA + py));
+                    st4(sm + ts::OFF_QB + sh, ld4(sm + ts::OFF_QB + py));
                 }
-                if (vp) st4(sm + ts::OFF_PHI + pslot(y) * WW + col, nph);
+                if (vp) st4(sm + ts::OFF_PHI + py, nph);
                 if (vq) {
-                    st4(sm + ts::OFF_QA + pslot(y) * WW + col, nqa);
-                    st4(sm + ts::OFF_QB + pslot(y) * WW + col, nqb);
+                    st4(sm + ts::OFF_QA + py, nqa);
+                    st4(sm + ts::OFF_QB + py, nqb);
                 }
             }
             if (s == ts::NSUB) tfp::fence_proxy_async_smem();   // u slots of the next copy
@@ -337,9 +330,10 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         {
             const int y = L - 11 - R + warp;
             if (y >= -1 && y < SG + 1) {
-                const float* ps = sm + ts::OFF_PHI + pslot(y - 1) * WW + col;
-                const float* pc = sm + ts::OFF_PHI + pslot(y) * WW + col;
-                const float* pn = sm + ts::OFF_PHI + pslot(y + 1) * WW + col;
+                const int sb = pslot(y - 1);
+                const float* ps = sm + ts::OFF_PHI + sb * WW + col;
+                const float* pc = sm + ts::OFF_PHI + step_slot<ts::DP>(sb, 1) * WW + col;
+                const float* pn = sm + ts::OFF_PHI + step_slot<ts::DP>(sb, 2) * WW + col;
                 const int dqa = ts::OFF_QA - ts::OFF_PHI, dqb = ts::OFF_QB - ts::OFF_PHI;
                 const V4 dp = ld4(ps), dc = ld4(pc), dn = ld4(pn);
                 const V4 ap = ld4(ps + dqa), ac = ld4(pc + dqa), an = ld4(pn + dqa);
@@ -369,6 +363,9 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         {
             const int eL = L - 12;
             const int r0 = max(eL - R, 0) - (eL - R), r1 = min(eL, SG) - (eL - R);   // block rows
+            // 32-bit element indices within one fluid's nine planes (9 N < 2^31,
+            // checked by the host); the instance offset is in the 64-bit bases
+            const int Ni = (int)N;
             const typename S::T* __restrict__ F1 = a.fsrc + 18 * b * N;
             const typename S::T* __restrict__ F2p = F1 + 9 * N;
             typename S::T* __restrict__ D1 = a.fdst + 18 * b * N;
@@ -378,56 +375,72 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             float* __restrict__ qo = a.Q_out + 2 * b * N;
             const float* stb = sm + ts::OFF_ST - ts::SC0;   // stress ring, window columns
             constexpr int PL = ts::DS * ts::SW;
+            // pulled populations of site (block row r, column cx): f_i(x - c_i)
+            auto pull = [&](f2 (&f)[9], int r, int cx) {
+                const int x = x0 + cx, gy = y0 + eL - R + r;
+                const int xp = x + 1 < nx ? x + 1 : 0, xm = x > 0 ? x - 1 : nx - 1;
+                const int ry = gy * nx;
+                const int ryp = (gy + 1 < ny ? gy + 1 : 0) * nx, rym = (gy > 0 ? gy - 1 : ny - 1) * nx;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
+                    const int sy = d2q9_cy(i) == 0 ? ry : (d2q9_cy(i) > 0 ? rym : ryp);
+                    const int idx = i * Ni + sy + sx;
+                    f[i] = P2(S::load(F1 + idx), S::load(F2p + idx));
+                }
+            };
             if (r0 < r1) {
+                // ring slots of the rows the block reads, from the row below its first
+                const int tb = eL - R + r0 - 1;
+                const int pb = pslot(tb), sb = sslot(tb);
                 const int nsite = (r1 - r0) * tw;
                 int r = r0 + threadIdx.x / tw, cx = threadIdx.x % tw;
                 const int dr = NT / tw, dc = NT - dr * tw;
+                // one site ahead: the next site's pulls are in flight while this
+                // site is computed
+                f2 f[9], fn[9];
+                if (threadIdx.x < nsite) pull(f, r, cx);
 #pragma unroll 1
                 for (int site = threadIdx.x; site < nsite; site += NT) {
-                    const int t = eL - R + r;             // segment row
-                    const int x = x0 + cx, gy = y0 + t;
-                    const int c = ts::HALO + cx;          // window column
-                    const float* ph = sm + ts::OFF_PHI + pslot(t) * WW;
-                    const float* phs = sm + ts::OFF_PHI + pslot(t - 1) * WW;
-                    const float* phn = sm + ts::OFF_PHI + pslot(t + 1) * WW;
-                    const float* sc = stb + sslot(t) * ts::SW;
-                    const float* ss = stb + sslot(t - 1) * ts::SW;
-                    const float* sn = stb + sslot(t + 1) * ts::SW;
-                    const int xp = x + 1 < nx ? x + 1 : 0, xm = x > 0 ? x - 1 : nx - 1;
-                    const int yp = gy + 1 < ny ? gy + 1 : 0, ym = gy > 0 ? gy - 1 : ny - 1;
-                    f2 f[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
-                        const int sy = d2q9_cy(i) == 0 ? gy : (d2q9_cy(i) > 0 ? ym : yp);
-                        const long long src = (long long)sy * nx + sx;
-                        f[i] = P2(S::load(F1 + i * N + src), S::load(F2p + i * N + src));
+                    int rn = r + dr, cxn = cx + dc;
+                    if (cxn >= tw) {
+                        cxn -= tw;
+                        ++rn;
                     }
+                    if (site + NT < nsite) pull(fn, rn, cxn);
+                    const int t = eL - R + r;             // segment row
+                    const int c = ts::HALO + cx;          // window column
+                    const int k = t - tb;                 // 1 .. R
+                    const int pc = step_slot<ts::DP>(pb, k) * WW;
+                    const float* ph = sm + ts::OFF_PHI + pc;
+                    const float* phs = sm + ts::OFF_PHI + step_slot<ts::DP>(pb, k - 1) * WW;
+                    const float* phn = sm + ts::OFF_PHI + step_slot<ts::DP>(pb, k + 1) * WW;
+                    const float* sc = stb + step_slot<ts::DS>(sb, k) * ts::SW;
+                    const float* ss = stb + step_slot<ts::DS>(sb, k - 1) * ts::SW;
+                    const float* sn = stb + step_slot<ts::DS>(sb, k + 1) * ts::SW;
                     f2 u1, u2;
                     lbm_site2(P, ph[c], P2(ph[c - 1], ph[c + 1]), P2(phs[c], phn[c]), sc[c],
                               P2(sc[c - 1], sc[c + 1]), P2(ss[c], sn[c]),
                               P2(sc[PL + c - 1], sc[PL + c + 1]), P2(ss[2 * PL + c], sn[2 * PL + c]),
                               P2(sc[3 * PL + c - 1], sc[3 * PL + c + 1]),
                               P2(ss[4 * PL + c], sn[4 * PL + c]), f, u1, u2);
-                    const long long g = (long long)gy * nx + x;
+                    const int g = (y0 + t) * nx + x0 + cx;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        S::store(D1 + i * N + g, f[i].x);
-                        S::store(D2 + i * N + g, f[i].y);
+                        S::store(D1 + (i * Ni + g), f[i].x);
+                        S::store(D2 + (i * Ni + g), f[i].y);
                     }
                     uo[g] = u1.x;
                     uo[N + g] = u1.y;
                     uo[2 * N + g] = u2.x;
                     uo[3 * N + g] = u2.y;
                     po[g] = ph[c];
-                    qo[g] = sm[ts::OFF_QA + pslot(t) * WW + c];
-                    qo[N + g] = sm[ts::OFF_QB + pslot(t) * WW + c];
-                    cx += dc;
-                    r += dr;
-                    if (cx >= tw) {
-                        cx -= tw;
-                        ++r;
-                    }
+                    qo[g] = sm[ts::OFF_QA + pc + c];
+                    qo[N + g] = sm[ts::OFF_QB + pc + c];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = fn[i];
+                    r = rn;
+                    cx = cxn;
                 }
             }
         }
