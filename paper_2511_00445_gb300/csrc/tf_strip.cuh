@@ -13,7 +13,9 @@
 // columns: 30 lanes x 4 columns), and it walks down the segment in blocks of
 // R = 8 rows.  Per block every stage advances by R rows, each stage lagging
 // two rows behind the one it reads:
-//   input rows of phi^(0), Q^(0), u  : [L - R, L)            (bulk copies, one block ahead)
+//   input rows of phi^(0), Q^(0), u  : [L - R, L)            (asynchronous copies issued
+//                                       one block ahead: phi / Q at the block's start,
+//                                       u once the fifth sub-step has read its rows)
 //   sub-step s = 1..5 (phi^(s), Q^(s)): [L - 2s - R, L - 2s)  (each warp one row; it
 //                                       evaluates mu^(s) on its row and the two beside it)
 //   stress and mu of phi^(5), Q^(5)   : [L - 11 - R, L - 11)
@@ -27,9 +29,11 @@
 // are skipped, columns outside it are computed and never read.
 //
 // The LBM pulls its populations straight from global memory; each thread
-// issues the next site's pulls before computing the current one.  (Bulk L2
-// prefetches of the next block's population and velocity rows were measured
-// and removed: at 2048^2 they cost 83 us per step, 525 -> 442 us.)
+// issues the next site's pulls before computing the current one.  Measured
+// and removed (2048^2, per step): bulk L2 prefetches of the next block's
+// population and velocity rows (525 -> 442 us), and loading the window rows
+// with one bulk copy per row (the copy engine handles small copies slowly;
+// per-thread 16-byte asynchronous copies took 399 -> 381 us for the u rows).
 #pragma once
 
 #include "tf_fused.cuh"
@@ -64,7 +68,6 @@ constexpr int OFF_U = OFF_QB + FS;                   // u1x, u1y, u2x, u2y: DU r
 constexpr int OFF_ST = OFF_U + 4 * DU * WW;          // mu, sxx, sxy, syx, syy: DS rows x SW
 constexpr int NFLOAT = OFF_ST + 5 * DS * SW;
 constexpr size_t SMEM = (size_t)NFLOAT * sizeof(float);
-constexpr int ROWB = WW * 4;                         // bytes of one window row
 }  // namespace ts
 
 // Four adjacent columns of a lane as two pairs (columns 0,1 and 2,3).
@@ -109,7 +112,6 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
     using namespace tfq;
     using ts::R;
     using ts::WW;
-    __shared__ __align__(8) uint64_t bars[2];   // [0] phi / Q blocks, [1] u blocks
     float* const sm = tf_smem;
     const int b = blockIdx.z;
     const int nx = a.nx, ny = a.ny;
@@ -124,12 +126,6 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
     const bool own = lane < ts::LANES;
     const int nblk = (SG + 2 * ts::HALO + R - 1) / R;   // blocks (= iterations)
 
-    if (threadIdx.x == 0) {
-        tfp::mbar_init(&bars[0], 1);
-        tfp::mbar_init(&bars[1], 1);
-        tfp::fence_mbar_init();
-    }
-    __syncthreads();
 
     // input plane pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y
     auto gsrc = [&](int pl) -> const float* {
@@ -137,34 +133,44 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                        : (pl < 3 ? a.Q_in + (2 * b + pl - 1) * N : a.u_in + (4 * b + pl - 3) * N);
     };
 
-    // Bulk copies of input block `blk` (rows [-HALO + blk R, ...) up to
-    // S + HALO, S the segment rows): planes [p0, p1) of (phi, Q_xx, Q_xy, u1x, u1y, u2x, u2y) on
-    // barrier `bar`.  Warp 0 only; lane 0 posts the byte count first.
-    auto issue_block = [&](int blk, int p0, int p1, uint64_t* bar) {
+    // The phi, Q_xx, Q_xy rows of input block `blk` into their ring slots:
+    // 16-byte per-thread asynchronous copies (one warp per plane row, lanes
+    // 0..29 one 4-column chunk each; with nx and x0 multiples of 4 no chunk
+    // straddles the periodic wrap).
+    auto issue_pq = [&](int blk) {
         const int t0 = -ts::HALO + blk * R;
-        const int t1 = min(t0 + R, SG + ts::HALO);
-        const int rows = t1 - t0;
-        if (lane == 0) tfp::mbar_arrive_expect_tx(bar, (uint32_t)(rows * (p1 - p0) * ts::ROWB));
-        __syncwarp();
-        for (int k = lane; k < rows * (p1 - p0); k += 32) {
-            const int pl = p0 + k / rows, t = t0 + k % rows;
-            float* dst = pl < 3 ? sm + (pl == 0 ? ts::OFF_PHI : (pl == 1 ? ts::OFF_QA : ts::OFF_QB)) +
-                                      pslot(t) * WW
-                                : sm + ts::OFF_U + (pl - 3) * ts::DU * WW + uslot(t) * WW;
-            bulk_row(dst, gsrc(pl), wrapc(y0 + t, ny), x0 - ts::HALO, WW, nx, bar);
+        const int rows = min(t0 + R, SG + ts::HALO) - t0;
+        if (own) {
+            const int gx = wrapc(x0 - ts::HALO + col, nx);
+            for (int pr = warp; pr < 3 * rows; pr += ts::NW) {
+                const int pl = pr / rows, t = t0 + pr - pl * rows;
+                const float* plane = pl == 0 ? a.phi_in + b * N : a.Q_in + (2 * b + pl - 1) * N;
+                tfp::cp_async16(sm + pl * ts::FS + pslot(t) * WW + col,
+                                plane + (long long)wrapc(y0 + t, ny) * nx + gx);
+            }
         }
+        tfp::cp_async_commit();
     };
-    // Give up after a bounded wait: report, let copies in flight land, leave.
-    auto bail = [&](int issued_pq, int issued_u) {
-        if (threadIdx.x == 0) atomicExch(a.err, TF_ERR_TIMEOUT);
-        if (issued_pq >= 0) tfp::wait_bounded(&bars[0], issued_pq & 1u, kWaitPolls);
-        if (issued_u >= 0) tfp::wait_bounded(&bars[1], issued_u & 1u, kWaitPolls);
+    // The u rows of input block `blk`: 16-byte per-thread asynchronous copies
+    // (all threads; one warp per plane row, lanes 0..29 one 4-column chunk
+    // each; with nx and x0 multiples of 4 no chunk straddles the periodic
+    // wrap).  Many small bulk copies are slow on the copy engine: issued as
+    // row-sized bulk copies these cost 28 us per 2048^2 step.
+    auto issue_u = [&](int blk) {
+        const int t0 = -ts::HALO + blk * R;
+        const int rows = min(t0 + R, SG + ts::HALO) - t0;
+        if (own) {
+            const int gx = wrapc(x0 - ts::HALO + col, nx);
+            for (int pr = warp; pr < 4 * rows; pr += ts::NW) {
+                const int pl = pr / rows, t = t0 + pr - pl * rows;
+                const float* src = a.u_in + (4 * b + pl) * N + (long long)wrapc(y0 + t, ny) * nx + gx;
+                tfp::cp_async16(sm + ts::OFF_U + pl * ts::DU * WW + uslot(t) * WW + col, src);
+            }
+        }
+        tfp::cp_async_commit();
     };
-
-    if (warp == 0) {
-        issue_block(0, 0, 3, &bars[0]);
-        issue_block(0, 3, 7, &bars[1]);
-    }
+    issue_pq(0);
+    issue_u(0);
 
     const float m4f = -4.f;
     const f2 m4 = S2(m4f), half = S2(0.5f);
@@ -181,17 +187,11 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
 #pragma unroll 1
     for (int j = 0; j < nblk; ++j) {
         const int L = -ts::HALO + (j + 1) * R;     // input rows < L are resident after the wait
-        {
-            const bool ok0 = tfp::wait_bounded(&bars[0], (uint32_t)j & 1u, kWaitPolls);
-            const bool ok1 = tfp::wait_bounded(&bars[1], (uint32_t)j & 1u, kWaitPolls);
-            if (__syncthreads_or(!(ok0 && ok1))) {
-                bail(j, j);
-                return;
-            }
-        }
+        tfp::cp_async_wait_all();      // this block's input rows (this thread's copies)
+        __syncthreads();               // ... and every other thread's
         // the next block's phi / Q rows (their ring slots were last read by
         // the previous block's LBM)
-        if (warp == 0 && j + 1 < nblk) issue_block(j + 1, 0, 3, &bars[0]);
+        if (j + 1 < nblk) issue_pq(j + 1);
 
         // ---- the five sub-steps
 #pragma unroll 1
@@ -305,6 +305,9 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 }
             }
             __syncthreads();
+            // the last sub-step has read this block's u rows: the next block's
+            // u rows go into their slots
+            if (s == ts::NSUB && j + 1 < nblk) issue_u(j + 1);
             // (b) save the rows the next block reads below its own (phi^(s-1)
             // of rows E - 2, E - 1 and Q^(s-1) of row E - 1), then write in place
             if (own) {
@@ -321,9 +324,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                     st4(sm + ts::OFF_QB + py, nqb);
                 }
             }
-            if (s == ts::NSUB) tfp::fence_proxy_async_smem();   // u slots of the next copy
             __syncthreads();
-            if (s == ts::NSUB && warp == 0 && j + 1 < nblk) issue_block(j + 1, 3, 7, &bars[1]);
         }
 
         // ---- mu and the fluid-1 stress of phi^(5), Q^(5) on rows [L - 11 - R, L - 11)
@@ -444,9 +445,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 }
             }
         }
-        // the next block's copies overwrite ring rows this block read
-        tfp::fence_proxy_async_smem();
-        __syncthreads();
+        __syncthreads();               // the next block's copies overwrite rows this block read
     }
 }
 
