@@ -54,6 +54,8 @@ extern "C" {
 #define TF_ERR_IO        (-5)  /* checkpoint file could not be read or written   */
 #define TF_ERR_WORKSPACE (-6)  /* workspace missing, too small or misaligned     */
 #define TF_ERR_TOO_LARGE (-7)  /* input larger than a fixed-footprint entry point accepts */
+#define TF_ERR_BOUNDS    (-8)  /* an index check of the bounds-check build failed
+                                  (libtwofluid_bc.so only; see tf_sync)          */
 
 /* ---- field ids for tf_read_field / tf_write_field -------------------- */
 #define TF_FIELD_PHI   0   /* concentration phi of the active fluid (r/w)        */
@@ -175,8 +177,10 @@ int tf_step(tf_ctx* ctx, int64_t n);
  *   TF_KERNEL_STRIP: one CTA per column strip (up to 96 columns) and row
  *                    segment, walked down in blocks of 8 rows with the five
  *                    sub-steps pipelined two rows apart (needs nx % 4 == 0);
- *   TF_KERNEL_AUTO:  the faster of the two for the context's grid (currently
- *                    the tile kernel everywhere).
+ *   TF_KERNEL_AUTO:  the strip kernel when the context's 32 x 32 tiles exceed
+ *                    one wave of resident CTAs, nx % 4 == 0 and its row
+ *                    segments are at least 128 rows long (e.g. 2048^2), else
+ *                    the tile kernel.
  * tf_set_step_kernel takes effect from the next step (TF_ERR_ARG for an
  * unknown kind, or TF_KERNEL_STRIP on a context it cannot step);
  * tf_step_kernel returns TF_KERNEL_TILE or TF_KERNEL_STRIP, the kernel the

@@ -14,7 +14,9 @@ from typing import Sequence
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtwofluid.so")
+# TF_LIBRARY selects another build of the library (the bounds-check build
+# libtwofluid_bc.so); by default the library next to this file.
+LIB_PATH = os.environ.get("TF_LIBRARY") or os.path.join(HERE, "libtwofluid.so")
 
 TF_OK = 0
 TF_ERR_ARG = -1
@@ -24,6 +26,7 @@ TF_ERR_TIMEOUT = -4
 TF_ERR_IO = -5
 TF_ERR_WORKSPACE = -6
 TF_ERR_TOO_LARGE = -7
+TF_ERR_BOUNDS = -8
 NOALLOC_MAX_ELEMS = 4096 * 1024
 
 FIELD_PHI, FIELD_QXX, FIELD_QXY = 0, 1, 2

@@ -345,7 +345,9 @@ int tf_sync(tf_ctx* ctx) {
         TF_CK(ctx, cudaStreamSynchronize(ctx->stream));
         return fail(ctx, flag, flag == TF_ERR_NONFINITE
                                    ? "the check_every scan found NaN or Inf in the state"
-                                   : "a device-side bounded wait timed out");
+                                   : flag == TF_ERR_BOUNDS
+                                         ? "an index check of the bounds-check build failed"
+                                         : "a device-side bounded wait timed out");
     }
     return TF_OK;
 }

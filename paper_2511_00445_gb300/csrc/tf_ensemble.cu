@@ -111,6 +111,7 @@ k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int st
     }
     __syncthreads();
     uint32_t phase = 0;
+    TF_BC_BEGIN();
     for (int k = 0; k < steps; ++k) {
         const int fp = fpar ^ (DO_LBM ? (k & 1) : 0);
         const int pp = ppar ^ (DO_FD ? (k & 1) : 0);
@@ -151,6 +152,7 @@ k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int st
         if (k == 0 && (int)blockIdx.x == held && k + 1 < steps) return;
         if (k + 1 < steps && !grid_barrier(ctl, k, groups[0].err, polls)) return;
     }
+    TF_BC_END(groups[0].err);
 }
 
 enum Mode { kPrologue = 0, kSteady = 1 };

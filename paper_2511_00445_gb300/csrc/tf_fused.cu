@@ -36,7 +36,9 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
     const int y0 = (int)((long long)blockIdx.y * a.ny / gridDim.y);
     const int y1 = (int)((long long)(blockIdx.y + 1) * a.ny / gridDim.y);
     const int x0 = tile_col(blockIdx.x, gridDim.x, a.nx), x1 = tile_col(blockIdx.x + 1, gridDim.x, a.nx);
+    TF_BC_BEGIN();
     fused_tile<DO_FD, DO_LBM, S, C::TYM, false, C::TXM>(a, blockIdx.z, x0, y0, x1 - x0, y1 - y0, &bar, 0);
+    TF_BC_END(a.err);
 }
 
 template <bool DO_FD, bool DO_LBM, class S>
@@ -181,9 +183,12 @@ int tile_rows_for(int ntx, int ny, int tym, int batch, long long slots) {
 // CTAs, with segments of at least kMinSegRows rows (each segment recomputes
 // up to 12 rows of sub-step halo above and below it).
 constexpr int kMinSegRows = 32;
-// Whether TF_KERNEL_AUTO picks the strip kernel on multi-wave grids (it does
-// once it steps them faster than the tile kernel).
-constexpr bool kAutoStrip = false;
+// TF_KERNEL_AUTO picks the strip kernel on grids of several waves of tiles
+// whose strip segments are at least this long: each segment recomputes up to
+// 12 rows of sub-step halo above and below it, so short segments lose to the
+// tiles (measured: 2048^2, 158-row segments, strip 376 vs tile 381 us per
+// step; 1024^2, 38-row segments, 112 vs 109 us).
+constexpr int kAutoStripMinRows = 128;
 
 int strip_segs_for(int ncols, int ny, int batch, long long slots) {
     const long long per = (long long)ncols * batch;
@@ -210,14 +215,14 @@ cudaError_t plan_tile_rows(tf_ctx* ctx) {
     const int txm = ctx->wide_tiles ? TX_WIDE : TX, tym = ctx->wide_tiles ? TY_WIDE : TY_DEFAULT;
     ctx->tile_cols = (ctx->nx + txm - 1) / txm;
     ctx->tile_rows = tile_rows_for(ctx->tile_cols, ctx->ny, tym, ctx->batch, slots);
-    // Steady-state kernel: AUTO takes the strip kernel on grids of several
-    // waves of tiles only where it is the faster one (kAutoStrip).
-    const bool can = tf_strip_supported(ctx) && per_sm_strip > 0;
-    ctx->use_strip = can && (ctx->step_kernel == TF_KERNEL_STRIP ||
-                             (ctx->step_kernel == TF_KERNEL_AUTO && kAutoStrip && ctx->wide_tiles));
     ctx->strip_cols = (ctx->nx + ts::TWMAX - 1) / ts::TWMAX;
     ctx->strip_segs = strip_segs_for(ctx->strip_cols, ctx->ny, ctx->batch,
                                      (long long)sms * (per_sm_strip > 0 ? per_sm_strip : 1));
+    // Steady-state kernel (tf_set_step_kernel; AUTO: see kAutoStripMinRows).
+    const bool can = tf_strip_supported(ctx) && per_sm_strip > 0;
+    const bool long_segs = ctx->ny / ctx->strip_segs >= kAutoStripMinRows;
+    ctx->use_strip = can && (ctx->step_kernel == TF_KERNEL_STRIP ||
+                             (ctx->step_kernel == TF_KERNEL_AUTO && ctx->wide_tiles && long_segs));
     return cudaSuccess;
 }
 

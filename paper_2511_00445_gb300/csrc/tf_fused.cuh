@@ -25,6 +25,7 @@
 //     forces, pulled populations, drag solve, collision and stores.
 #pragma once
 
+#include "tf_check.cuh"
 #include "tf_device.cuh"
 #include "tf_internal.h"
 #include "tf_pair.cuh"
@@ -117,15 +118,16 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
         const PairCols pc(o, w, lane);
         const int bh = (h + NW - 1) / NW, y0 = warp * bh, y1 = min(h, y0 + bh);
         if (y0 < y1) {
-            const float* col = phi + pc.c0;
-            f2 pp = ld2(col + (o + y0 - 1) * W), pcur = ld2(col + (o + y0) * W);
+            constexpr int H = A / W;
+            const float* col = phi + TF_BC(pc.c0, W - 1);
+            f2 pp = ld2(col + TF_BC(o + y0 - 1, H) * W), pcur = ld2(col + TF_BC(o + y0, H) * W);
             for (int y = y0; y < y1; ++y) {
-                const f2 pn = ld2(col + (o + y + 1) * W);
+                const f2 pn = ld2(col + TF_BC(o + y + 1, H) * W);
                 f2 l, r;
                 nbr2(pcur, l, r);
                 const f2 lap = F2(m4, pcur, A2(A2(l, r), A2(pp, pn)));
                 const f2 poly = F2(pcur, F2(pcur, F2(pcur, mu3, mu2), mu1), mu0);
-                st_pair(mu + (o + y) * W + pc.c0, F2(kap, lap, poly), pc.st);
+                st_pair(mu + TF_BC((o + y) * W + pc.c0, A - 1), F2(kap, lap, poly), pc.st);
                 pp = pcur;
                 pcur = pn;
             }
@@ -165,7 +167,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
     Row r0, r1, r2;                               // three rows: roles rotate by renaming
     f2 e_ph, e_qa, e_qb;                          // row y1 (below the band), captured early
     auto load_row = [&](Row& R, int y, bool edge) {
-        const int c = (o + y) * W + pc.c0;
+        const int c = TF_BC((o + y) * W + pc.c0, A - 1);
         R.mu = ld2(mu + c);
         R.ax = ld2(u1x + c);
         R.ay = ld2(u1y + c);
@@ -194,7 +196,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
         const bool qrow = row >= oq && row < oq + th + 2 * rq;
         // A lane reads and writes only its own columns (x-neighbours come by
         // shuffle), so row y is overwritten in place without a warp barrier.
-        const int c = row * W + pc.c0;
+        const int c = TF_BC(row * W + pc.c0, A - 1);
         st_pair(phi + c, nph, pc.st);
         if (qrow) {
             f2 al, ar, bl, br, uxl, uxr, uyl, uyr;
@@ -224,7 +226,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
     if (y0 < y1) {
         load_row(r0, y0 - 1, false);
         load_row(r1, y0, false);
-        const int ce = (o + y1) * W + pc.c0;
+        const int ce = TF_BC((o + y1) * W + pc.c0, A - 1);
         e_ph = ld2(phi + ce);
         e_qa = ld2(qa + ce);
         e_qb = ld2(qb + ce);
@@ -257,7 +259,7 @@ __device__ __forceinline__ void bulk_row(float* dst, const float* plane, int gy,
                                          int nx, uint64_t* bar) {
     int off = 0;
     while (off < len) {
-        const int gx = wrapc(xs + off, nx);
+        const int gx = TF_BC(wrapc(xs + off, nx), nx);
         const int n = min(len - off, nx - gx);
         tfp::bulk_g2s(dst + off, plane + (long long)gy * nx + gx, (uint32_t)n * 4u, bar);
         off += n;
@@ -407,7 +409,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
                 f2 ap = ld2(qa + (o + y0 - 1) * W + col), ac = ld2(qa + (o + y0) * W + col);
                 f2 bp = ld2(qb + (o + y0 - 1) * W + col), bc = ld2(qb + (o + y0) * W + col);
                 for (int y = y0; y < y1; ++y) {
-                    const int cn = (o + y + 1) * W + col, cc = (o + y) * W + col;
+                    const int cn = TF_BC((o + y + 1) * W + col, A - 1), cc = TF_BC((o + y) * W + col, A - 1);
                     const f2 dn = ld2(phi + cn), an = ld2(qa + cn), bn = ld2(qb + cn);
                     f2 dl, dr, al, ar, bl, br;
                     nbr2(dc, dl, dr);
@@ -446,7 +448,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         auto lbm_site = [&](int r, int cx) {
             const int x = x0 + cx, y = y0 + r;
             if (x >= nx || y >= ny) return;
-            const int c = (RH + r) * W + RH + cx;
+            const int c = TF_BC((RH + r) * W + RH + cx - W - 1, A - 2 * W - 2) + W + 1;
             const int xp = x + 1 < nx ? x + 1 : 0, xm = x > 0 ? x - 1 : nx - 1;
             const int yp = y + 1 < ny ? y + 1 : 0, ym = y > 0 ? y - 1 : ny - 1;
             f2 f[9];
@@ -454,7 +456,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             for (int i = 0; i < 9; ++i) {
                 const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
                 const int sy = d2q9_cy(i) == 0 ? y : (d2q9_cy(i) > 0 ? ym : yp);
-                const long long src = (long long)sy * nx + sx;
+                const long long src = TF_BC64((long long)sy * nx + sx, N);
                 if constexpr (MULTI)
                     f[i] = P2(S::load_cg(F1 + i * N + src), S::load_cg(F2p + i * N + src));
                 else
@@ -465,7 +467,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
                       P2(mu[c - 1], mu[c + 1]), P2(mu[c - W], mu[c + W]), P2(sxx[c - 1], sxx[c + 1]),
                       P2(sxy[c - W], sxy[c + W]), P2(syx[c - 1], syx[c + 1]),
                       P2(syy[c - W], syy[c + W]), f, u1, u2);
-            const long long g = (long long)y * nx + x;
+            const long long g = TF_BC64((long long)y * nx + x, N);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 S::store(D1 + i * N + g, f[i].x);
@@ -505,8 +507,8 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             const int r = site / tw, cx = site - r * tw;
             const int x = x0 + cx, y = y0 + r;
             if (x >= nx || y >= ny) continue;
-            const int c = (RH + r) * W + RH + cx;
-            const long long g = (long long)y * nx + x;
+            const int c = TF_BC((RH + r) * W + RH + cx, A);
+            const long long g = TF_BC64((long long)y * nx + x, N);
             po[g] = tf_smem[P_PHI * A + c];
             qo[g] = tf_smem[P_QA * A + c];
             qo[N + g] = tf_smem[P_QB * A + c];

@@ -36,6 +36,7 @@
 // per-thread 16-byte asynchronous copies took 399 -> 381 us for the u rows).
 #pragma once
 
+#include "tf_check.cuh"
 #include "tf_fused.cuh"
 
 namespace {
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
     const int col = 4 * min(lane, ts::LANES - 1);   // this lane's first window column
     const bool own = lane < ts::LANES;
     const int nblk = (SG + 2 * ts::HALO + R - 1) / R;   // blocks (= iterations)
+    TF_BC_BEGIN();
 
 
     // input plane pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y
@@ -141,12 +143,12 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         const int t0 = -ts::HALO + blk * R;
         const int rows = min(t0 + R, SG + ts::HALO) - t0;
         if (own) {
-            const int gx = wrapc(x0 - ts::HALO + col, nx);
+            const int gx = TF_BC(wrapc(x0 - ts::HALO + col, nx), nx - 3);
             for (int pr = warp; pr < 3 * rows; pr += ts::NW) {
                 const int pl = pr / rows, t = t0 + pr - pl * rows;
                 const float* plane = pl == 0 ? a.phi_in + b * N : a.Q_in + (2 * b + pl - 1) * N;
-                tfp::cp_async16(sm + pl * ts::FS + pslot(t) * WW + col,
-                                plane + (long long)wrapc(y0 + t, ny) * nx + gx);
+                tfp::cp_async16(sm + pl * ts::FS + TF_BC(pslot(t), ts::DP) * WW + col,
+                                plane + (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx + gx);
             }
         }
         tfp::cp_async_commit();
@@ -160,11 +162,13 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         const int t0 = -ts::HALO + blk * R;
         const int rows = min(t0 + R, SG + ts::HALO) - t0;
         if (own) {
-            const int gx = wrapc(x0 - ts::HALO + col, nx);
+            const int gx = TF_BC(wrapc(x0 - ts::HALO + col, nx), nx - 3);
             for (int pr = warp; pr < 4 * rows; pr += ts::NW) {
                 const int pl = pr / rows, t = t0 + pr - pl * rows;
-                const float* src = a.u_in + (4 * b + pl) * N + (long long)wrapc(y0 + t, ny) * nx + gx;
-                tfp::cp_async16(sm + ts::OFF_U + pl * ts::DU * WW + uslot(t) * WW + col, src);
+                const float* src = a.u_in + (4 * b + pl) * N +
+                                   (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx + gx;
+                tfp::cp_async16(sm + ts::OFF_U + pl * ts::DU * WW + TF_BC(uslot(t), ts::DU) * WW + col,
+                                src);
             }
         }
         tfp::cp_async_commit();
@@ -206,9 +210,9 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             // row index (ring slot or shadow) of row t of phi^(s-1), Q^(s-1)
             auto ridx = [&](int t) {
                 const int k = t - tb;
-                return k < 2 ? shr + k : step_slot<ts::DP>(pb, k);
+                return TF_BC(k < 2 ? shr + k : step_slot<ts::DP>(pb, k), ts::FROWS);
             };
-            auto urow = [&](int t) { return step_slot<ts::DU>(ub, t - tb - 1) * WW; };
+            auto urow = [&](int t) { return TF_BC(step_slot<ts::DU>(ub, t - tb - 1), ts::DU) * WW; };
             auto phi_row = [&](int t) -> const float* { return sm + ts::OFF_PHI + ridx(t) * WW; };
             auto qa_row = [&](int t) -> const float* { return sm + ts::OFF_QA + ridx(t) * WW; };
             auto qb_row = [&](int t) -> const float* { return sm + ts::OFF_QB + ridx(t) * WW; };
@@ -311,9 +315,9 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             // (b) save the rows the next block reads below its own (phi^(s-1)
             // of rows E - 2, E - 1 and Q^(s-1) of row E - 1), then write in place
             if (own) {
-                const int py = step_slot<ts::DP>(pb, y - tb) * WW + col;
+                const int py = TF_BC(step_slot<ts::DP>(pb, y - tb), ts::DP) * WW + col;
                 if (warp >= R - 2 && y >= lo - 2) {
-                    const int sh = (shr + warp - (R - 2)) * WW + col;
+                    const int sh = TF_BC(shr + warp - (R - 2), ts::FROWS) * WW + col;
                     st4(sm + ts::OFF_PHI + sh, ld4(sm + ts::OFF_PHI + py));
                     st4(sm + ts::OFF_QA + sh, ld4(sm + ts::OFF_QA + py));
                     st4(sm + ts::OFF_QB + sh, ld4(sm + ts::OFF_QB + py));
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         {
             const int y = L - 11 - R + warp;
             if (y >= -1 && y < SG + 1) {
-                const int sb = pslot(y - 1);
+                const int sb = TF_BC(pslot(y - 1), ts::DP);
                 const float* ps = sm + ts::OFF_PHI + sb * WW + col;
                 const float* pc = sm + ts::OFF_PHI + step_slot<ts::DP>(sb, 1) * WW + col;
                 const float* pn = sm + ts::OFF_PHI + step_slot<ts::DP>(sb, 2) * WW + col;
@@ -348,7 +352,8 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 const PairStress r1 = stress2(P, dc.hi, dl.hi, dr.hi, dn.hi, dp.hi, ac.hi, al.hi,
                                               ar.hi, an.hi, ap.hi, bc.hi, bl.hi, br.hi, bn.hi, bp.hi);
                 if (lane >= ts::SC0 / 4 && lane < (ts::SC0 + ts::SW) / 4) {
-                    float* st = sm + ts::OFF_ST + sslot(y) * ts::SW + (col - ts::SC0);
+                    float* st = sm + ts::OFF_ST + TF_BC(sslot(y), ts::DS) * ts::SW +
+                                TF_BC(col - ts::SC0, ts::SW - 3);
                     constexpr int PL = ts::DS * ts::SW;
                     st4(st, {r0.mu, r1.mu});
                     st4(st + PL, {r0.sxx, r1.sxx});
@@ -386,7 +391,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 for (int i = 0; i < 9; ++i) {
                     const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
                     const int sy = d2q9_cy(i) == 0 ? ry : (d2q9_cy(i) > 0 ? rym : ryp);
-                    const int idx = i * Ni + sy + sx;
+                    const int idx = TF_BC(i * Ni + sy + sx, 9 * Ni);
                     f[i] = P2(S::load(F1 + idx), S::load(F2p + idx));
                 }
             };
@@ -410,8 +415,8 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                     }
                     if (site + NT < nsite) pull(fn, rn, cxn);
                     const int t = eL - R + r;             // segment row
-                    const int c = ts::HALO + cx;          // window column
-                    const int k = t - tb;                 // 1 .. R
+                    const int c = TF_BC(ts::HALO + cx, ts::SC0 + ts::SW - 1);   // window column
+                    const int k = TF_BC(t - tb, ts::DS - 1);   // 1 .. R
                     const int pc = step_slot<ts::DP>(pb, k) * WW;
                     const float* ph = sm + ts::OFF_PHI + pc;
                     const float* phs = sm + ts::OFF_PHI + step_slot<ts::DP>(pb, k - 1) * WW;
@@ -425,7 +430,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                               P2(sc[PL + c - 1], sc[PL + c + 1]), P2(ss[2 * PL + c], sn[2 * PL + c]),
                               P2(sc[3 * PL + c - 1], sc[3 * PL + c + 1]),
                               P2(ss[4 * PL + c], sn[4 * PL + c]), f, u1, u2);
-                    const int g = (y0 + t) * nx + x0 + cx;
+                    const int g = TF_BC((y0 + t) * nx + x0 + cx, Ni);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         S::store(D1 + (i * Ni + g), f[i].x);
@@ -447,6 +452,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         }
         __syncthreads();               // the next block's copies overwrite rows this block read
     }
+    TF_BC_END(a.err);
 }
 
 template <class S>

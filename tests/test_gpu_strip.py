@@ -95,8 +95,11 @@ def test_strip_parity_against_oracle(nx, ny):
 
 
 def test_kernel_selection():
-    big = B.TwoFluid(CFG0.with_(nx=1024, ny=1024))
-    assert big.step_kernel() in (B.KERNEL_TILE, B.KERNEL_STRIP)
+    huge = B.TwoFluid(CFG0.with_(nx=2048, ny=2048))     # long strip segments: strip
+    assert huge.step_kernel() == B.KERNEL_STRIP
+    huge.close()
+    big = B.TwoFluid(CFG0.with_(nx=1024, ny=1024))      # short segments: tiles
+    assert big.step_kernel() == B.KERNEL_TILE
     big.set_step_kernel("strip")
     assert big.step_kernel() == B.KERNEL_STRIP
     big.set_step_kernel("tile")
