@@ -16,7 +16,7 @@
 //  1. the phi, Q and u planes of the tile plus a halo are brought into shared
 //     memory by bulk copies (one per row segment, periodic wrap handled by
 //     splitting segments), and the population rows the tile will pull are
-//     bulk-prefetched into L2 so that they stream from HBM during step 2;
+//     prefetched into L2 so that they stream from HBM during step 2;
 //  2. FD(k) runs in shared memory on shrinking neighbourhoods of the tile
 //     (phi loses two sites of halo per sub-step through lap(mu), Q one site);
 //     each sub-step computes mu, then the new phi and Q into registers, then
@@ -266,15 +266,16 @@ __device__ __forceinline__ void bulk_row(float* dst, const float* plane, int gy,
     }
 }
 
+// L2 prefetch hint for elements [c0, c1] (c0 <= c1) of one row: one
+// per-thread prefetch per 128-byte line, every address inside the range.
+// (Bulk prefetches through the copy engine were slower: it handles many
+// small requests slowly.)
 template <typename T>
-__device__ __forceinline__ void prefetch_row(const T* plane, int gy, int xs, int len, int nx) {
-    int off = 0;
-    while (off < len) {
-        const int gx = wrapc(xs + off, nx);
-        const int n = min(len - off, nx - gx);
-        tfp::prefetch_l2(plane + (long long)gy * nx + gx, (uint32_t)(n * sizeof(T)));
-        off += n;
-    }
+__device__ __forceinline__ void prefetch_span(const T* row, int c0, int c1) {
+    const char* const p0 = reinterpret_cast<const char*>(row + c0);
+    const char* const p1 = reinterpret_cast<const char*>(row + c1);
+    for (const char* q = p0; q < p1; q += 128) tfp::prefetch_l2_line(q);
+    tfp::prefetch_l2_line(p1);
 }
 
 // Device pointers and sizes of one stepping launch (one group of instances
@@ -322,9 +323,6 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
     const DevParams P = a.prm[b];
     // 16-byte bulk copies need every row start on a 16-byte boundary.
     const bool bulk = (nx & 3) == 0;
-    // Population prefetch: rows of PF elements (16 bytes) at 16-byte boundaries.
-    constexpr int PF = 16 / (int)sizeof(typename S::T);
-    const bool pref = nx % PF == 0;
 
     // ---- stage 1: tile loads (and population prefetch)
     // Load task pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y.
@@ -346,17 +344,15 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             const int gy = wrapc(y0 - RH + ly, ny);
             bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, wr, nx, bar);
         }
-        if (DO_LBM && pref) {
-            // columns x0 - 1 .. x0 + tw widened to whole 16-byte units (PF
-            // elements): tiles start on multiples of 4 only, and the bulk
-            // prefetch needs 16-byte aligned starts and sizes
-            const int xs = ((x0 - 1 + PF) / PF - 1) * PF;             // floor to PF (x0 - 1 >= -1)
-            const int xe = (x0 + tw + 1 + PF - 1) / PF * PF;           // ceil to PF
+        if (DO_LBM) {
+            // the population rows the tile pulls (columns x0 - 1 .. x0 + tw)
+            // into L2, so that they stream from HBM during the sub-steps
             const typename S::T* F = fsrc + 18 * b * N;
             for (int t = threadIdx.x; t < 18 * (TY + 2); t += NT) {
                 const int i = t / (TY + 2), r = t - i * (TY + 2);
                 if (r >= th + 2) continue;
-                prefetch_row(F + (long long)i * N, wrapc(y0 - 1 + r, ny), xs, xe - xs, nx);
+                prefetch_span(F + (long long)i * N + (long long)wrapc(y0 - 1 + r, ny) * nx,
+                              max(x0 - 1, 0), min(x0 + tw, nx - 1));
             }
         }
         const bool ok = tfp::wait_bounded(bar, phase & 1u, kWaitPolls);

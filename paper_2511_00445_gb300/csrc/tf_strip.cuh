@@ -28,12 +28,17 @@
 // window or the segment is ever needed; rows outside a stage's exact range
 // are skipped, columns outside it are computed and never read.
 //
-// The LBM pulls its populations straight from global memory; each thread
-// issues the next site's pulls before computing the current one.  Measured
-// and removed (2048^2, per step): bulk L2 prefetches of the next block's
-// population and velocity rows (525 -> 442 us), and loading the window rows
-// with one bulk copy per row (the copy engine handles small copies slowly;
-// per-thread 16-byte asynchronous copies took 399 -> 381 us for the u rows).
+// The LBM pulls its populations straight from global memory.  At the start
+// of a block every CTA asks L2 for the population rows its LBM phase will pull
+// (per-thread prefetch instructions, ~3 per thread; 343 -> 325 us per 2048^2
+// step), each thread issues its first site's pulls before the barrier that
+// publishes the stress rows and the next site's pulls before computing the
+// current one.  Measured and removed (2048^2, per step): bulk L2 prefetches
+// through the copy engine (525 -> 442 us without them), prefetching one block
+// further ahead (340 us), and loading the window rows with one bulk copy per
+// row (the copy engine handles small copies slowly; per-thread 16-byte
+// asynchronous copies took 399 -> 381 us for the u rows, and issuing them
+// without per-row index divisions 374 -> 348 us).
 #pragma once
 
 #include "tf_check.cuh"
@@ -129,47 +134,36 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
     TF_BC_BEGIN();
 
 
-    // input plane pl: 0 phi, 1 Q_xx, 2 Q_xy, 3..6 u1x u1y u2x u2y
-    auto gsrc = [&](int pl) -> const float* {
-        return pl == 0 ? a.phi_in + b * N
-                       : (pl < 3 ? a.Q_in + (2 * b + pl - 1) * N : a.u_in + (4 * b + pl - 3) * N);
-    };
-
-    // The phi, Q_xx, Q_xy rows of input block `blk` into their ring slots:
-    // 16-byte per-thread asynchronous copies (one warp per plane row, lanes
-    // 0..29 one 4-column chunk each; with nx and x0 multiples of 4 no chunk
-    // straddles the periodic wrap).
+    // Window copies: 16-byte per-thread asynchronous copies.  Warp w copies
+    // row t0 + w of an input block (all its planes), lanes 0..29 one 4-column
+    // chunk each; with nx and x0 multiples of 4 no chunk straddles the
+    // periodic wrap.  The rows past the segment's lower halo are not copied.
+    // (Many small bulk copies are slow on the copy engine: issued as row-sized
+    // bulk copies the u rows alone cost 28 us per 2048^2 step.)
+    const int gx = TF_BC(wrapc(x0 - ts::HALO + col, nx), nx - 3);
+    const float* const phi_src = a.phi_in + b * N + gx;
+    const float* const qa_src = a.Q_in + 2 * b * N + gx;
+    const float* const u_src = a.u_in + 4 * b * N + gx;
+    // the phi, Q_xx, Q_xy rows of input block `blk` into their ring slots
     auto issue_pq = [&](int blk) {
-        const int t0 = -ts::HALO + blk * R;
-        const int rows = min(t0 + R, SG + ts::HALO) - t0;
-        if (own) {
-            const int gx = TF_BC(wrapc(x0 - ts::HALO + col, nx), nx - 3);
-            for (int pr = warp; pr < 3 * rows; pr += ts::NW) {
-                const int pl = pr / rows, t = t0 + pr - pl * rows;
-                const float* plane = pl == 0 ? a.phi_in + b * N : a.Q_in + (2 * b + pl - 1) * N;
-                tfp::cp_async16(sm + pl * ts::FS + TF_BC(pslot(t), ts::DP) * WW + col,
-                                plane + (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx + gx);
-            }
+        const int t = -ts::HALO + blk * R + warp;
+        if (own && t < SG + ts::HALO) {
+            const long long ro = (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx;
+            float* const d = sm + TF_BC(pslot(t), ts::DP) * WW + col;
+            tfp::cp_async16(d, phi_src + ro);
+            tfp::cp_async16(d + ts::FS, qa_src + ro);
+            tfp::cp_async16(d + 2 * ts::FS, qa_src + N + ro);
         }
         tfp::cp_async_commit();
     };
-    // The u rows of input block `blk`: 16-byte per-thread asynchronous copies
-    // (all threads; one warp per plane row, lanes 0..29 one 4-column chunk
-    // each; with nx and x0 multiples of 4 no chunk straddles the periodic
-    // wrap).  Many small bulk copies are slow on the copy engine: issued as
-    // row-sized bulk copies these cost 28 us per 2048^2 step.
+    // the u rows of input block `blk`
     auto issue_u = [&](int blk) {
-        const int t0 = -ts::HALO + blk * R;
-        const int rows = min(t0 + R, SG + ts::HALO) - t0;
-        if (own) {
-            const int gx = TF_BC(wrapc(x0 - ts::HALO + col, nx), nx - 3);
-            for (int pr = warp; pr < 4 * rows; pr += ts::NW) {
-                const int pl = pr / rows, t = t0 + pr - pl * rows;
-                const float* src = a.u_in + (4 * b + pl) * N +
-                                   (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx + gx;
-                tfp::cp_async16(sm + ts::OFF_U + pl * ts::DU * WW + TF_BC(uslot(t), ts::DU) * WW + col,
-                                src);
-            }
+        const int t = -ts::HALO + blk * R + warp;
+        if (own && t < SG + ts::HALO) {
+            const float* const src = u_src + (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx;
+            float* const d = sm + ts::OFF_U + TF_BC(uslot(t), ts::DU) * WW + col;
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) tfp::cp_async16(d + pl * ts::DU * WW, src + pl * N);
         }
         tfp::cp_async_commit();
     };
@@ -196,6 +190,17 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         // the next block's phi / Q rows (their ring slots were last read by
         // the previous block's LBM)
         if (j + 1 < nblk) issue_pq(j + 1);
+        // L2 prefetch of the population rows [L - 19, L - 11) that this block's
+        // LBM phase pulls (rows L - 21, L - 20 came with the previous block):
+        // thread (plane, row) touches every 128-byte line of columns
+        // [x0 - 1, x0 + tw] of its row; each address lies inside the row.
+        if (threadIdx.x < 18 * R) {
+            const int pl = threadIdx.x / R, t = L - 19 + threadIdx.x % R;
+            if (t >= -1 && t < SG + 1) {
+                prefetch_span(a.fsrc + (18 * b + pl) * N + (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx,
+                              max(x0 - 1, 0), min(x0 + tw, nx - 1));
+            }
+        }
 
         // ---- the five sub-steps
 #pragma unroll 1
@@ -363,8 +368,6 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 }
             }
         }
-        __syncthreads();
-
         // ---- LBM of rows [L - 12 - R, L - 12) and stores of the new state
         {
             const int eL = L - 12;
@@ -395,62 +398,62 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                     f[i] = P2(S::load(F1 + idx), S::load(F2p + idx));
                 }
             };
-            if (r0 < r1) {
-                // ring slots of the rows the block reads, from the row below its first
-                const int tb = eL - R + r0 - 1;
-                const int pb = pslot(tb), sb = sslot(tb);
-                const int nsite = (r1 - r0) * tw;
-                int r = r0 + threadIdx.x / tw, cx = threadIdx.x % tw;
-                const int dr = NT / tw, dc = NT - dr * tw;
-                // one site ahead: the next site's pulls are in flight while this
-                // site is computed
-                f2 f[9], fn[9];
-                if (threadIdx.x < nsite) pull(f, r, cx);
+            // ring slots of the rows the block reads, from the row below its first
+            const int tb = eL - R + r0 - 1;
+            const int pb = pslot(tb), sb = sslot(tb);
+            const int nsite = r0 < r1 ? (r1 - r0) * tw : 0;
+            int r = r0 + threadIdx.x / tw, cx = threadIdx.x % tw;
+            const int dr = NT / tw, dc = NT - dr * tw;
+            // one site ahead: the next site's pulls are in flight while this
+            // site is computed (the first site's before the barrier)
+            f2 f[9], fn[9];
+            if (threadIdx.x < nsite) pull(f, r, cx);
+            __syncthreads();   // the stress rows of this block
 #pragma unroll 1
-                for (int site = threadIdx.x; site < nsite; site += NT) {
-                    int rn = r + dr, cxn = cx + dc;
-                    if (cxn >= tw) {
-                        cxn -= tw;
-                        ++rn;
-                    }
-                    if (site + NT < nsite) pull(fn, rn, cxn);
-                    const int t = eL - R + r;             // segment row
-                    const int c = TF_BC(ts::HALO + cx, ts::SC0 + ts::SW - 1);   // window column
-                    const int k = TF_BC(t - tb, ts::DS - 1);   // 1 .. R
-                    const int pc = step_slot<ts::DP>(pb, k) * WW;
-                    const float* ph = sm + ts::OFF_PHI + pc;
-                    const float* phs = sm + ts::OFF_PHI + step_slot<ts::DP>(pb, k - 1) * WW;
-                    const float* phn = sm + ts::OFF_PHI + step_slot<ts::DP>(pb, k + 1) * WW;
-                    const float* sc = stb + step_slot<ts::DS>(sb, k) * ts::SW;
-                    const float* ss = stb + step_slot<ts::DS>(sb, k - 1) * ts::SW;
-                    const float* sn = stb + step_slot<ts::DS>(sb, k + 1) * ts::SW;
-                    f2 u1, u2;
-                    lbm_site2(P, ph[c], P2(ph[c - 1], ph[c + 1]), P2(phs[c], phn[c]), sc[c],
-                              P2(sc[c - 1], sc[c + 1]), P2(ss[c], sn[c]),
-                              P2(sc[PL + c - 1], sc[PL + c + 1]), P2(ss[2 * PL + c], sn[2 * PL + c]),
-                              P2(sc[3 * PL + c - 1], sc[3 * PL + c + 1]),
-                              P2(ss[4 * PL + c], sn[4 * PL + c]), f, u1, u2);
-                    const int g = TF_BC((y0 + t) * nx + x0 + cx, Ni);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        S::store(D1 + (i * Ni + g), f[i].x);
-                        S::store(D2 + (i * Ni + g), f[i].y);
-                    }
-                    uo[g] = u1.x;
-                    uo[N + g] = u1.y;
-                    uo[2 * N + g] = u2.x;
-                    uo[3 * N + g] = u2.y;
-                    po[g] = ph[c];
-                    qo[g] = sm[ts::OFF_QA + pc + c];
-                    qo[N + g] = sm[ts::OFF_QB + pc + c];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) f[i] = fn[i];
-                    r = rn;
-                    cx = cxn;
+            for (int site = threadIdx.x; site < nsite; site += NT) {
+                int rn = r + dr, cxn = cx + dc;
+                if (cxn >= tw) {
+                    cxn -= tw;
+                    ++rn;
                 }
+                if (site + NT < nsite) pull(fn, rn, cxn);
+                const int t = eL - R + r;             // segment row
+                const int c = TF_BC(ts::HALO + cx, ts::SC0 + ts::SW - 1);   // window column
+                const int k = TF_BC(t - tb, ts::DS - 1);   // 1 .. R
+                const int pc = step_slot<ts::DP>(pb, k) * WW;
+                const float* ph = sm + ts::OFF_PHI + pc;
+                const float* phs = sm + ts::OFF_PHI + step_slot<ts::DP>(pb, k - 1) * WW;
+                const float* phn = sm + ts::OFF_PHI + step_slot<ts::DP>(pb, k + 1) * WW;
+                const float* sc = stb + step_slot<ts::DS>(sb, k) * ts::SW;
+                const float* ss = stb + step_slot<ts::DS>(sb, k - 1) * ts::SW;
+                const float* sn = stb + step_slot<ts::DS>(sb, k + 1) * ts::SW;
+                f2 u1, u2;
+                lbm_site2(P, ph[c], P2(ph[c - 1], ph[c + 1]), P2(phs[c], phn[c]), sc[c],
+                          P2(sc[c - 1], sc[c + 1]), P2(ss[c], sn[c]),
+                          P2(sc[PL + c - 1], sc[PL + c + 1]), P2(ss[2 * PL + c], sn[2 * PL + c]),
+                          P2(sc[3 * PL + c - 1], sc[3 * PL + c + 1]),
+                          P2(ss[4 * PL + c], sn[4 * PL + c]), f, u1, u2);
+                const int g = TF_BC((y0 + t) * nx + x0 + cx, Ni);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    S::store(D1 + (i * Ni + g), f[i].x);
+                    S::store(D2 + (i * Ni + g), f[i].y);
+                }
+                uo[g] = u1.x;
+                uo[N + g] = u1.y;
+                uo[2 * N + g] = u2.x;
+                uo[3 * N + g] = u2.y;
+                po[g] = ph[c];
+                qo[g] = sm[ts::OFF_QA + pc + c];
+                qo[N + g] = sm[ts::OFF_QB + pc + c];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = fn[i];
+                r = rn;
+                cx = cxn;
             }
         }
-        __syncthreads();               // the next block's copies overwrite rows this block read
+        // No barrier at the end of a block: the next block writes shared
+        // memory first through its copies, issued after its first barrier.
     }
     TF_BC_END(a.err);
 }
