@@ -198,7 +198,10 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
         // shuffle), so row y is overwritten in place without a warp barrier.
         const int c = TF_BC(row * W + pc.c0, A - 1);
         st_pair(phi + c, nph, pc.st);
-        if (qrow) {
+        // Q on every row, stored only inside its neighbourhood (the rows read
+        // lie inside phi's): the row stays one basic block, so the phi and Q
+        // chains of consecutive rows interleave.
+        {
             f2 al, ar, bl, br, uxl, uxr, uyl, uyr;
             nbr2(Cr.qa, al, ar);
             nbr2(Cr.qb, bl, br);
@@ -219,8 +222,8 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
                                   F2(nux, B2(ar, al), M2(nuy, B2(Nr.qa, Pr.qa))))))));
             const f2 nqb = A2(bq, F2(cc, bq, F2(cGK, lapb, F2(lamq, EX, F2(N2(hO), a,
                                   F2(nux, B2(br, bl), M2(nuy, B2(Nr.qb, Pr.qb))))))));
-            st_pair(qa + c, nqa, qs);
-            st_pair(qb + c, nqb, qs);
+            st_pair(qa + c, nqa, qs && qrow);
+            st_pair(qb + c, nqb, qs && qrow);
         }
     };
     if (y0 < y1) {

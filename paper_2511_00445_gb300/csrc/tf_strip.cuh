@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             // of rows y-1, y, y+1 evaluated here from phi^(s-1) rows y-2 .. y+2
             const int y = E - R + warp;
             const bool vp = y >= lo && y < hi, vq = y >= qlo && y < qhi;
-            V4 nph, nqa, nqb;
+            V4 nph, nqa, nqb, oph, oqa, oqb;   // new and old (phi, Q) of row y
             if (vp) {
                 const float* u1x = sm + ts::OFF_U + 0 * ts::DU * WW + col;
                 const float* u1y = sm + ts::OFF_U + 1 * ts::DU * WW + col;
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 const V4 phss = ld4(phi_row(y - 2) + col), phs = ld4(phi_row(y - 1) + col),
                          phc = ld4(phi_row(y) + col), phn = ld4(phi_row(y + 1) + col),
                          phnn = ld4(phi_row(y + 2) + col);
+                oph = phc;
                 // mu = -kappa lap(phi) + A_ch f'(phi) (Eq. 2) of the middle row
                 auto mu_row = [&](const V4& pp, const V4& pc, const V4& pn) {
                     V4 l, r, mu;
@@ -276,11 +277,16 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                     const f2 lapmu = F2(m4, muc.hi, A2(A2(ml.hi, mr.hi), A2(mun.hi, mus.hi)));
                     nph.hi = F2(hdt2, F2(M2x, lapmu, N2(dJ)), phc.hi);
                 }
-                if (vq) {
+                // Q^(s) of the row, also where only phi^(s) is exact (vp && !vq:
+                // computed from in-range rows, not stored): one basic block with
+                // the phi update, so the two chains interleave (2048^2: 326 -> 318 us)
+                {
                     const V4 as = ld4(qa_row(y - 1) + col), ac = ld4(qa_row(y) + col),
                              an = ld4(qa_row(y + 1) + col);
                     const V4 bs = ld4(qb_row(y - 1) + col), bc = ld4(qb_row(y) + col),
                              bn = ld4(qb_row(y + 1) + col);
+                    oqa = ac;
+                    oqb = bc;
                     const V4 axs = ld4(u1x + us), axn = ld4(u1x + un), ayc = ld4(u1y + uc);
                     V4 al, ar, bl, br, uxl, uxr, uyl, uyr;
                     nbr4(ac, al, ar);
@@ -323,9 +329,14 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 const int py = TF_BC(step_slot<ts::DP>(pb, y - tb), ts::DP) * WW + col;
                 if (warp >= R - 2 && y >= lo - 2) {
                     const int sh = TF_BC(shr + warp - (R - 2), ts::FROWS) * WW + col;
-                    st4(sm + ts::OFF_PHI + sh, ld4(sm + ts::OFF_PHI + py));
-                    st4(sm + ts::OFF_QA + sh, ld4(sm + ts::OFF_QA + py));
-                    st4(sm + ts::OFF_QB + sh, ld4(sm + ts::OFF_QB + py));
+                    if (!vp) {   // row not computed: its old values are not in registers
+                        oph = ld4(sm + ts::OFF_PHI + py);
+                        oqa = ld4(sm + ts::OFF_QA + py);
+                        oqb = ld4(sm + ts::OFF_QB + py);
+                    }
+                    st4(sm + ts::OFF_PHI + sh, oph);
+                    st4(sm + ts::OFF_QA + sh, oqa);
+                    st4(sm + ts::OFF_QB + sh, oqb);
                 }
                 if (vp) st4(sm + ts::OFF_PHI + py, nph);
                 if (vq) {
