@@ -287,7 +287,7 @@ def measured_peaks():
 
 # Sources the per-context fused kernel is compiled from.
 FUSED_SOURCES = ("tf_device.cuh", "tf_fused.cu", "tf_fused.cuh", "tf_strip.cuh", "tf_internal.h", "tf_pair.cuh",
-                 "tf_ptx.cuh")
+                 "tf_ptx.cuh", "tf_check.cuh")
 
 
 def kernel_source_sha() -> str:
