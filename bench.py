@@ -17,8 +17,9 @@ four 256 x 256 instances; its state (~44 MB) fits in L2, so L2 is flushed
 (256 MiB write) before every timed step there.
 
 --workload ensemble48 steps 48 instances of three sizes (the parameter-sweep
-ensemble) with the persistent ensemble launch after its autotuner ran, and
-also times the same instances stepped context by context.
+ensemble) through the ensemble API with the launch shape its autotuner chose
+(one persistent launch for all steps, or one launch per step over every tile
+of every group), and also times the same instances stepped context by context.
 
 --storage f16|bf16 stores the populations as 16-bit deviations (FP32
 arithmetic).  Such a run also times the FP32 storage on the same workload
@@ -615,8 +616,9 @@ def run_ours(args, wl):
 
 
 def run_ensemble(args, wl):
-    """48 instances of three sizes in one persistent launch per K steps
-    (after the autotuner picked the tile shape), against the same instances
+    """48 instances of three sizes stepped through the ensemble API with the
+    launch shape its autotuner picked (one persistent launch per K steps or
+    one launch per step over all groups' tiles), against the same instances
     stepped context by context with one launch per group and step."""
     import torch
 
@@ -696,7 +698,9 @@ def run_ensemble(args, wl):
     achieved = bps * sites / (sec / args.steps) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "k_ens (persistent, all steps in one launch)", "bytes_per_site": bps,
+                "kernel": ("k_ens (persistent, all steps in one launch)" if cfg["persistent"] else
+                           "k_ens_step (one launch per step over every tile of every group)"),
+                "bytes_per_site": bps,
                 "launches_per_step": launches / args.steps,
                 "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     cpu = None
@@ -711,7 +715,7 @@ def run_ensemble(args, wl):
             "config": {"workload": wl["name"], "sites_per_step": sites, "instances": 48,
                        "storage": args.storage,
                        "l2": "not flushed: the state (~1.2 GB) is far larger than L2",
-                       "timing": "CUDA events around the one persistent launch of all K steps",
+                       "timing": "CUDA events around the ensemble's launches of all K steps",
                        "autotuned": cfg},
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": None, "clocks": clk, "gpu_launches": launches,

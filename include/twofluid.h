@@ -330,7 +330,7 @@ int tf_plan_tiles(int nx, int ny, int batch, long long slots, int out[3], int* c
  * destroyed, while the ensemble exists. */
 typedef struct tf_ensemble tf_ensemble;
 #define TF_ENS_MAX_GROUPS 64
-#define TF_ENS_CANDIDATES 6    /* autotuner candidates, see tf_ensemble_config */
+#define TF_ENS_CANDIDATES 8    /* autotuner candidates, see tf_ensemble_autotune */
 
 /* Device workspace bytes for an ensemble of n_groups (1..64) groups; 0 when
  * n_groups is out of range. */
@@ -348,37 +348,55 @@ int tf_ensemble_destroy(tf_ensemble* ens);
 const char* tf_ensemble_last_error(const tf_ensemble* ens);
 
 /* Advance every member instance by n >= 0 steps: an LBM-only first pass
- * when the members hold a completed state, then ONE persistent launch for
- * the remaining steps.  Asynchronous on the ensemble's stream. */
+ * when the members hold a completed state, then the remaining steps as one
+ * persistent launch (candidates 0..5 of tf_ensemble_autotune) or as one
+ * launch per step covering every tile of every group (candidates 6, 7), up
+ * to 1024 steps per launch or per recorded graph.  Asynchronous on the
+ * ensemble's stream. */
 int tf_ensemble_step(tf_ensemble* ens, int64_t n);
 
 /* Wait for the ensemble's work and report the members' device status
  * (TF_ERR_TIMEOUT after a bounded wait ran out). */
 int tf_ensemble_sync(tf_ensemble* ens);
 
-/* Tile-shape autotuner: candidate k = 0..5 is tile shape (columns x rows)
- * {32 x 32, 32 x 24, 40 x 30}[k/2] with {2, 1}[k%2] resident CTAs per SM
- * (40-column tiles: columns cut at multiples of 4, up to 40 wide).  Each candidate runs one launch of
- * `steps_per_candidate` (>= 1) real steps timed with CUDA events; the fastest
- * becomes the configuration.  Every candidate computes bitwise the same
- * trajectory, so the tuning steps are ordinary steps: the ensemble advances
- * by 6 * steps_per_candidate steps (plus the first pass if one is due).
+/* Launch-shape autotuner over TF_ENS_CANDIDATES candidates.  Candidate
+ * k = 0..5: one persistent cooperative launch for all steps (a grid barrier
+ * between steps, populations read through L2), tile shape (columns x rows)
+ * {32 x 32, 32 x 24, 40 x 30}[k/2] with {2, 1}[k%2] resident CTAs per SM.
+ * Candidates 6 and 7: one launch per step with one CTA per tile of every
+ * group (populations read through L1, as in per-context stepping), tile
+ * shape 32 x 32 and 40 x 30.  40-column tiles cut columns at multiples of 4,
+ * up to 40 wide.  Each candidate runs `steps_per_candidate` (1..1024) real
+ * steps timed with CUDA events; the fastest becomes the configuration.  Every
+ * candidate computes bitwise the same trajectory, so the tuning steps are
+ * ordinary steps: the ensemble advances by TF_ENS_CANDIDATES *
+ * steps_per_candidate steps (plus the first pass if one is due).
  * Synchronous. */
 int tf_ensemble_autotune(tf_ensemble* ens, int steps_per_candidate);
 
 /* Current configuration: tile height (30 means the 40 x 30 shape), CTAs per
- * SM, grid size of the persistent launch, tiles per step; us_per_step (may be NULL) receives the
+ * SM, grid size of one launch (of the persistent launch, or tiles per step
+ * for candidates 6, 7), tiles per step; us_per_step (may be NULL) receives the
  * TF_ENS_CANDIDATES autotuner timings in microseconds per step (0 before
  * tf_ensemble_autotune).  *graphs = 1 when launches replay CUDA graphs, 0
  * when they are issued directly (stream capture unavailable). */
 int tf_ensemble_config(const tf_ensemble* ens, int* tile_y, int* ctas_per_sm, int* grid,
                        int64_t* tiles_per_step, double* us_per_step, int* graphs);
 
-/* Kernel launches issued by this ensemble so far (a graph replay counts its
- * one kernel). */
+/* Kernel launches issued by this ensemble so far (a graph replay counts the
+ * kernels it holds). */
 int64_t tf_ensemble_launches(const tf_ensemble* ens);
 
-/* Failure-detection drill for the persistent launch's grid barrier (no fault
+/* The candidate in use (0 .. TF_ENS_CANDIDATES - 1, see tf_ensemble_autotune;
+ * 0 after tf_ensemble_create), or TF_ERR_ARG for a null ensemble. */
+int tf_ensemble_candidate(const tf_ensemble* ens);
+
+/* Use candidate `candidate` from the next tf_ensemble_step on (results do not
+ * depend on it).  TF_ERR_ARG when it is out of range. */
+int tf_ensemble_select(tf_ensemble* ens, int candidate);
+
+/* Failure-detection drill for the persistent launch's grid barrier (candidates
+ * 0..5; launches of candidates 6, 7 have no grid barrier) (no fault
  * is injected on the device: a CTA just leaves early).  From the next
  * tf_ensemble_step on, the barrier gives up after `barrier_polls` polls of
  * ~128 ns each (0 restores the default of about one second) and, when

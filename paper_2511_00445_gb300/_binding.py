@@ -54,7 +54,8 @@ EXPORTS = [
     "tf_state_bytes", "tf_advance_host", "tf_save", "tf_load", "tf_plan_tiles",
     "tf_ensemble_workspace_bytes", "tf_ensemble_create", "tf_ensemble_destroy",
     "tf_ensemble_last_error", "tf_ensemble_step", "tf_ensemble_sync", "tf_ensemble_autotune",
-    "tf_ensemble_config", "tf_ensemble_launches", "tf_ensemble_fault_drill",
+    "tf_ensemble_config", "tf_ensemble_launches", "tf_ensemble_candidate", "tf_ensemble_select",
+    "tf_ensemble_fault_drill",
     "tf_sur_workspace_bytes", "tf_sur_create", "tf_sur_destroy", "tf_sur_last_error",
     "tf_sur_num_params", "tf_sur_init_weights", "tf_sur_set_weights", "tf_sur_get_weights",
     "tf_sur_forward", "tf_sur_gradients", "tf_sur_add_pair", "tf_sur_fit_normalisation",
@@ -68,7 +69,8 @@ class TFSurConfig(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("base_channels", ctypes.c_int), ("nx", ctypes.c_int),
                 ("ny", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_pairs", ctypes.c_int),
                 ("horizon", ctypes.c_int)]
-ENS_CANDIDATES = 6
+ENS_CANDIDATES = 8
+ENS_PERSISTENT_CANDIDATES = 6     # candidates 0..5: one persistent launch; 6, 7: a launch per step
 
 
 class TFParams(ctypes.Structure):
@@ -187,6 +189,8 @@ def load_library() -> ctypes.CDLL:
         "tf_ensemble_config": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                    ctypes.POINTER(i64), dp, ctypes.POINTER(i)]),
         "tf_ensemble_launches": (i64, [vp]),
+        "tf_ensemble_candidate": (i, [vp]),
+        "tf_ensemble_select": (i, [vp, i]),
         "tf_ensemble_fault_drill": (i, [vp, ctypes.c_uint32, i]),
         "tf_sur_workspace_bytes": (sz, [ctypes.POINTER(TFSurConfig)]),
         "tf_sur_create": (i, [ctypes.POINTER(TFSurConfig), vp, sz, vp, ctypes.POINTER(vp)]),
@@ -448,12 +452,20 @@ class Ensemble:
         self._check(self.lib.tf_ensemble_config(self.ens, ctypes.byref(ty), ctypes.byref(cps),
                                                 ctypes.byref(grid), ctypes.byref(tiles), _dptr(us),
                                                 ctypes.byref(gr)))
-        return {"tile_y": ty.value, "ctas_per_sm": cps.value, "grid": grid.value,
+        cand = self.candidate()
+        return {"candidate": cand, "persistent": cand < ENS_PERSISTENT_CANDIDATES,
+                "tile_y": ty.value, "ctas_per_sm": cps.value, "grid": grid.value,
                 "tiles_per_step": tiles.value, "us_per_step": us.tolist(), "graphs": bool(gr.value),
                 "note": self.lib.tf_ensemble_last_error(self.ens).decode()}
 
     def launches(self) -> int:
         return int(self.lib.tf_ensemble_launches(self.ens))
+
+    def candidate(self) -> int:
+        return int(self.lib.tf_ensemble_candidate(self.ens))
+
+    def select(self, candidate: int):
+        self._check(self.lib.tf_ensemble_select(self.ens, candidate))
 
     def fault_drill(self, barrier_polls: int = 0, held_cta: int = -1):
         self._check(self.lib.tf_ensemble_fault_drill(self.ens, barrier_polls, held_cta))

@@ -19,11 +19,18 @@
 
 namespace {
 
-// Candidate tile shapes (columns x rows): the 32-column shapes cut columns at
-// multiples of 32, the wide one like the per-context wide tiles (tile_col).
+// Candidate tile shapes (columns x rows, the largest tile of each; ens_tile
+// balances the tiles of a group like the per-context tiles).
 constexpr int kTileX[3] = {TX, TX, TX_WIDE};
 constexpr int kTileY[3] = {32, 24, TY_WIDE};
-constexpr int kCandidates = TF_ENS_CANDIDATES; // tile shape x CTAs per SM {2, 1}
+// Candidates 0..5: persistent launches, tile shape c / 2 with 2 - c % 2 CTAs
+// per SM; 6, 7: one launch per step over every tile of every group (k_ens_step)
+// with the 32 x 32 and the 40 x 30 shape.
+constexpr int kCandidates = TF_ENS_CANDIDATES;
+constexpr int kPersistentCandidates = 6;
+constexpr bool persistent_cfg(int c) { return c < kPersistentCandidates; }
+constexpr int shape_of(int c) { return c < kPersistentCandidates ? c / 2 : (c == 6 ? 0 : 2); }
+constexpr int ctas_of(int c) { return c < kPersistentCandidates ? 2 - c % 2 : 2; }
 constexpr uint32_t kBarrierPolls = 1u << 23;   // x ~128 ns sleeps: about one second
 constexpr int64_t kMaxStepsPerLaunch = 1024;
 
@@ -94,6 +101,33 @@ __device__ __forceinline__ bool grid_barrier(EnsCtl* ctl, int k, int* err, uint3
     return s_ok != 0;
 }
 
+// Tile t of a step: group g, instance b and rectangle.  Per group and shape
+// the tiles are numbered instance by instance, row-major; the ny rows are cut
+// into ceil(ny / TY) tile rows of floor or ceil(ny / that) rows, the nx columns
+// into ceil(nx / TXW) columns by tile_col, so no tile is a thin remainder.
+struct EnsTile {
+    int g, b, x0, y0, tw, th;
+};
+
+template <int TY, int TXW>
+__device__ __forceinline__ EnsTile ens_tile(const EnsGroup* __restrict__ groups, int n_groups,
+                                            long long t) {
+    constexpr int TI = shape_index<TY, TXW>();
+    int g = 0;
+    while (g + 1 < n_groups && groups[g + 1].begin[TI] <= t) ++g;
+    const EnsGroup& G = groups[g];
+    const long long local = t - G.begin[TI];
+    const int ntx = G.tiles_x[TI], nty = (G.ny + TY - 1) / TY;
+    const long long per = (long long)ntx * nty;
+    const int b = (int)(local / per);
+    const long long r = local - (long long)b * per;
+    const int tyi = (int)(r / ntx), txi = (int)(r - (long long)tyi * ntx);
+    const int y0 = (int)((long long)tyi * G.ny / nty);
+    const int y1 = (int)((long long)(tyi + 1) * G.ny / nty);
+    const int x0 = tile_col(txi, ntx, G.nx);
+    return {g, b, x0, y0, tile_col(txi + 1, ntx, G.nx) - x0, y1 - y0};
+}
+
 // `steps` lattice steps of every tile of every group.  Parities fpar, ppar,
 // upar select the current population, phi/Q and velocity buffers at step 0;
 // each step flips the ones it writes.
@@ -101,7 +135,6 @@ template <bool DO_FD, bool DO_LBM, class S, int TY, int TXW>
 __global__ void __launch_bounds__(NT, 2)
 k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int steps, int fpar,
       int ppar, int upar, EnsCtl* ctl, uint32_t polls, int held) {
-    constexpr int TI = shape_index<TY, TXW>();
     using T = typename S::T;
     __shared__ __align__(8) uint64_t bar;
     __shared__ long long s_ticket;
@@ -125,22 +158,13 @@ k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int st
             const long long t = s_ticket;
             __syncthreads();
             if (t >= total) break;
-            int g = 0;
-            while (g + 1 < n_groups && groups[g + 1].begin[TI] <= t) ++g;
-            const EnsGroup& G = groups[g];
-            const long long local = t - G.begin[TI];
-            const int ntx = G.tiles_x[TI];
-            const long long per = (long long)ntx * ((G.ny + TY - 1) / TY);
-            const int b = (int)(local / per);
-            const long long r = local - (long long)b * per;
-            const int tyi = (int)(r / ntx), txi = (int)(r - (long long)tyi * ntx);
+            const EnsTile r = ens_tile<TY, TXW>(groups, n_groups, t);
+            const EnsGroup& G = groups[r.g];
             const TileArgs<S> a{static_cast<const T*>(G.f[fp]), static_cast<T*>(G.f[fp ^ 1]),
                                 G.phi[pp], G.phi[pp ^ 1], G.Q[pp], G.Q[pp ^ 1], G.u[up],
                                 G.u[up ^ 1], G.prm, G.nx, G.ny, G.err};
-            const int y0 = tyi * TY, th = min(TY, G.ny - y0);
-            const int x0 = TXW == TX ? txi * TX : tile_col(txi, ntx, G.nx);
-            const int tw = TXW == TX ? min(TX, G.nx - x0) : tile_col(txi + 1, ntx, G.nx) - x0;
-            if (!fused_tile<DO_FD, DO_LBM, S, TY, true, TXW>(a, b, x0, y0, tw, th, &bar, phase)) {
+            if (!fused_tile<DO_FD, DO_LBM, S, TY, true, TXW>(a, r.b, r.x0, r.y0, r.tw, r.th, &bar,
+                                                           phase)) {
                 if (threadIdx.x == 0) atomicExch(&ctl->abort, 1);
                 return;
             }
@@ -155,6 +179,31 @@ k_ens(const EnsGroup* __restrict__ groups, int n_groups, long long total, int st
     TF_BC_END(groups[0].err);
 }
 
+// One step of every tile of every group, one tile per CTA (candidates 6, 7).
+// Nothing in the launch reads what it writes, so the populations are read
+// through L1 like in the per-context kernel, and no grid barrier is needed.
+// The per-step parities are the launch's.
+template <class S, int TY, int TXW>
+__global__ void __launch_bounds__(NT, 2)
+k_ens_step(const EnsGroup* __restrict__ groups, int n_groups, int fp, int pp, int up) {
+    using T = typename S::T;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tfp::mbar_init(&bar, 1);
+        tfp::fence_mbar_init();
+    }
+    __syncthreads();
+    TF_BC_BEGIN();
+    const EnsTile r = ens_tile<TY, TXW>(groups, n_groups, blockIdx.x);
+    const EnsGroup& G = groups[r.g];
+    const TileArgs<S> a{static_cast<const T*>(G.f[fp]), static_cast<T*>(G.f[fp ^ 1]),
+                        G.phi[pp], G.phi[pp ^ 1], G.Q[pp], G.Q[pp ^ 1], G.u[up],
+                        G.u[up ^ 1], G.prm, G.nx, G.ny, G.err};
+    // a bulk copy that did not complete is reported in the group's status word
+    fused_tile<true, true, S, TY, false, TXW>(a, r.b, r.x0, r.y0, r.tw, r.th, &bar, 0u);
+    TF_BC_END(G.err);
+}
+
 enum Mode { kPrologue = 0, kSteady = 1 };
 
 typedef void (*EnsKernel)(const EnsGroup*, int, long long, int, int, int, int, EnsCtl*, uint32_t,
@@ -166,6 +215,20 @@ EnsKernel pick(int mode, int ti) {
     if (ti == 0) return k_ens<true, true, S, 32, TX>;
     if (ti == 1) return k_ens<true, true, S, 24, TX>;
     return k_ens<true, true, S, TY_WIDE, TX_WIDE>;
+}
+
+typedef void (*StepKernel)(const EnsGroup*, int, int, int, int);
+
+template <class S>
+StepKernel pick_step(int ti) {
+    if (ti == 0) return k_ens_step<S, 32, TX>;
+    return k_ens_step<S, TY_WIDE, TX_WIDE>;
+}
+
+StepKernel step_kernel_for(int storage, int ti) {
+    if (storage == TF_STORE_F16) return pick_step<PopF16>(ti);
+    if (storage == TF_STORE_BF16) return pick_step<PopBF16>(ti);
+    return pick_step<PopF32>(ti);
 }
 
 EnsKernel kernel_for(int storage, int mode, int ti) {
@@ -226,8 +289,9 @@ int efail_cuda(tf_ensemble* e, const char* where, cudaError_t err) {
     } while (0)
 
 int grid_for(tf_ensemble* e, int mode, int cfg) {
-    const int ti = mode == kPrologue ? 0 : cfg / 2;
-    const int want = mode == kPrologue ? 2 : 2 - cfg % 2;
+    const int ti = mode == kPrologue ? 0 : shape_of(cfg);
+    if (mode == kSteady && !persistent_cfg(cfg)) return (int)e->tiles[ti];   // one CTA per tile
+    const int want = mode == kPrologue ? 2 : ctas_of(cfg);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(e->storage, mode, ti), NT,
                                                       smem_for(mode, ti)) != cudaSuccess ||
@@ -238,11 +302,24 @@ int grid_for(tf_ensemble* e, int mode, int cfg) {
     return (int)(g < tiles ? g : tiles);
 }
 
-// Zero the control block, then one cooperative launch of `steps` steps on
-// `grid` CTAs (grid_for; computed outside any stream capture) into `st`.
+// Persistent candidates: zero the control block, then one cooperative launch
+// of `steps` steps on `grid` CTAs (grid_for; computed outside any stream
+// capture) into `st`.  Per-step candidates: `steps` launches of k_ens_step.
 cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid, cudaStream_t st) {
-    const int ti = mode == kPrologue ? 0 : cfg / 2;
+    const int ti = mode == kPrologue ? 0 : shape_of(cfg);
     if (grid < 1) return cudaErrorInvalidConfiguration;
+    if (mode == kSteady && !persistent_cfg(cfg)) {
+        const StepKernel k = step_kernel_for(e->storage, ti);
+        const size_t smem = smem_for(kSteady, ti);
+        const int ng = (int)e->groups.size();
+        for (int s = 0; s < steps; ++s) {
+            const int f = s & 1;
+            k<<<grid, NT, smem, st>>>(e->d_groups, ng, e->fpar ^ f, e->ppar ^ f, e->upar ^ f);
+            const cudaError_t err = cudaGetLastError();
+            if (err != cudaSuccess) return err;
+        }
+        return cudaSuccess;
+    }
     cudaError_t err = cudaMemsetAsync(e->d_ctl, 0, sizeof(EnsCtl), st);
     if (err != cudaSuccess) return err;
     cudaLaunchConfig_t lc = {};
@@ -308,7 +385,7 @@ int issue(tf_ensemble* e, int mode, int steps) {
         }
         if (!done) TF_ECK(e, enqueue(e, mode, steps, e->cfg, grid, e->stream));
     }
-    e->launches += 1;
+    e->launches += mode == kSteady && !persistent_cfg(e->cfg) ? steps : 1;
     if (mode == kPrologue) {
         e->fpar ^= 1;
         e->upar ^= 1;
@@ -391,9 +468,17 @@ cudaError_t set_smem() {
                                 (int)Geo<DO_FD, DO_LBM, TY, TXW>::SMEM);
 }
 
+template <class S, int TY, int TXW>
+cudaError_t set_step_smem() {
+    return cudaFuncSetAttribute(k_ens_step<S, TY, TXW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Geo<true, true, TY, TXW>::SMEM);
+}
+
 template <class S>
 cudaError_t configure_storage() {
     cudaError_t e = set_smem<false, true, S, 32, TX>();
+    if (e == cudaSuccess) e = set_step_smem<S, 32, TX>();
+    if (e == cudaSuccess) e = set_step_smem<S, TY_WIDE, TX_WIDE>();
     if (e == cudaSuccess) e = set_smem<true, true, S, 32, TX>();
     if (e == cudaSuccess) e = set_smem<true, true, S, 24, TX>();
     if (e == cudaSuccess) e = set_smem<true, true, S, TY_WIDE, TX_WIDE>();
@@ -547,9 +632,9 @@ int tf_ensemble_autotune(tf_ensemble* e, int steps_per_candidate) {
 int tf_ensemble_config(const tf_ensemble* e, int* tile_y, int* ctas_per_sm, int* grid,
                        int64_t* tiles_per_step, double* us_per_step, int* graphs) {
     if (!e) return TF_ERR_ARG;
-    const int ti = e->cfg / 2;
+    const int ti = shape_of(e->cfg);
     if (tile_y) *tile_y = kTileY[ti];
-    if (ctas_per_sm) *ctas_per_sm = 2 - e->cfg % 2;
+    if (ctas_per_sm) *ctas_per_sm = ctas_of(e->cfg);
     if (grid) *grid = grid_for(const_cast<tf_ensemble*>(e), kSteady, e->cfg);
     if (tiles_per_step) *tiles_per_step = e->tiles[ti];
     if (us_per_step)
@@ -559,6 +644,16 @@ int tf_ensemble_config(const tf_ensemble* e, int* tile_y, int* ctas_per_sm, int*
 }
 
 int64_t tf_ensemble_launches(const tf_ensemble* e) { return e ? e->launches : -1; }
+
+int tf_ensemble_candidate(const tf_ensemble* e) { return e ? e->cfg : TF_ERR_ARG; }
+
+int tf_ensemble_select(tf_ensemble* e, int candidate) {
+    if (!e) return TF_ERR_ARG;
+    if (candidate < 0 || candidate >= kCandidates)
+        return efail(e, TF_ERR_ARG, "candidate out of range");
+    e->cfg = candidate;
+    return TF_OK;
+}
 
 int tf_ensemble_fault_drill(tf_ensemble* e, uint32_t barrier_polls, int held_cta) {
     if (!e) return TF_ERR_ARG;

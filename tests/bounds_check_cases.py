@@ -3,7 +3,7 @@
 Run as a script (``python tests/bounds_check_cases.py OUT.npz`` with the
 TF_LIBRARY environment variable naming the library): every case steps small,
 ragged and degenerate grids through the tile kernel, the strip kernel, the
-per-stage kernels and a persistent ensemble, checks that tf_sync / tf_ensemble_sync
+per-stage kernels and ensembles (persistent and per-step launches), checks that tf_sync / tf_ensemble_sync
 report no failed index check, and saves the resulting fields.  The GPU test
 runs the same cases with the normal library and compares them bitwise.
 """
@@ -46,22 +46,25 @@ def run_cases() -> dict:
             for f in FIELDS:
                 out[f"{nx}x{ny}_{kernel}_{n_sub}_{storage}_{inst}_{f}"] = tf.read_field(inst, f)
         tf.close()
-    # a persistent ensemble of ragged groups
+    # ensembles of ragged groups: the persistent launch (candidate 0) and the
+    # per-step launches with both tile shapes (candidates 6, 7)
     base = B.SolverParams(zeta=0.01)
-    groups = [B.TwoFluid([base.with_(nx=40, ny=36), base.with_(nx=40, ny=36, lam=1.1)]),
-              B.TwoFluid(base.with_(nx=33, ny=17))]
-    for g, tf in enumerate(groups):
-        for k in range(tf.batch):
-            tf.init_fields(10 * g + k, phi0=0.5, dphi=0.05, S0=0.2, inst=k)
-    ens = B.Ensemble(groups)
-    ens.step(5)
-    ens.sync()
-    ens.close()
-    for g, tf in enumerate(groups):
-        for inst in range(tf.batch):
-            for f in FIELDS:
-                out[f"ens_{g}_{inst}_{f}"] = tf.read_field(inst, f)
-        tf.close()
+    for cand in (0, 6, 7):
+        groups = [B.TwoFluid([base.with_(nx=40, ny=36), base.with_(nx=40, ny=36, lam=1.1)]),
+                  B.TwoFluid(base.with_(nx=33, ny=17)), B.TwoFluid(base.with_(nx=100, ny=70))]
+        for g, tf in enumerate(groups):
+            for k in range(tf.batch):
+                tf.init_fields(10 * g + k, phi0=0.5, dphi=0.05, S0=0.2, inst=k)
+        ens = B.Ensemble(groups)
+        ens.select(cand)
+        ens.step(5)
+        ens.sync()
+        ens.close()
+        for g, tf in enumerate(groups):
+            for inst in range(tf.batch):
+                for f in FIELDS:
+                    out[f"ens{cand}_{g}_{inst}_{f}"] = tf.read_field(inst, f)
+            tf.close()
     return out
 
 

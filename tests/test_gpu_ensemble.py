@@ -93,25 +93,68 @@ def test_large_grid_matches_grid_stepped_alone(nx, ny, storage):
 
 
 def test_ensemble_autotune_steps_are_real_steps():
-    """Six candidates (tile shapes 32x32, 32x24 and 40x30, one or two CTAs per SM) each run
-    real steps; the trajectory equals stepping alone."""
+    """Eight candidates (persistent launches with tile shapes 32x32, 32x24 and
+    40x30 and one or two CTAs per SM; one launch per step with 32x32 or 40x30)
+    each run real steps; the trajectory equals stepping alone."""
     spec = groups_spec()
     grp = make_groups(spec)
     ens = B.Ensemble(grp)
-    ens.autotune(2)                       # first pass + 6 x 2 steps
+    ens.autotune(2)                       # first pass + 8 x 2 steps
     ens.step(3)
     ens.sync()
-    assert_same(grp, alone(spec, 1 + 12 + 3))
+    assert_same(grp, alone(spec, 1 + 2 * B.ENS_CANDIDATES + 3))
     cfg = ens.config()
+    assert len(cfg["us_per_step"]) == B.ENS_CANDIDATES == 8
     assert all(us > 0 for us in cfg["us_per_step"])
     assert cfg["tile_y"] in (24, 30, 32) and cfg["ctas_per_sm"] in (1, 2)
+    assert 0 <= cfg["candidate"] < 8
+    assert cfg["persistent"] == (cfg["candidate"] < 6)
+
+
+@pytest.mark.parametrize("candidate", [6, 7])
+@pytest.mark.parametrize("storage", [B.STORE_F32, B.STORE_BF16], ids=["f32", "bf16"])
+def test_per_step_launch_candidates(candidate, storage):
+    """Candidates 6 and 7 (one launch per step over every tile of every
+    group, populations read through L1) step the ragged groups bitwise like
+    each context stepped alone, across a member read and repeated calls."""
+    spec = groups_spec(storage)
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.select(candidate)
+    l0 = ens.launches()
+    ens.step(4)
+    assert ens.launches() - l0 == 1 + 3   # the LBM-only first pass, then one launch per step
+    grp[1].read_field(0, B.FIELD_PHI)
+    ens.step(3)
+    ens.step(3)
+    ens.sync()
+    assert_same(grp, alone(spec, 10))
+    cfg = ens.config()
+    assert cfg["candidate"] == candidate and not cfg["persistent"]
+    assert cfg["grid"] == cfg["tiles_per_step"]
+    with pytest.raises(B.TwoFluidError):
+        ens.select(8)
+
+
+@pytest.mark.parametrize("nx,ny,candidate", [(1040, 1000, 7), (1030, 1000, 6)])
+def test_per_step_launches_large_grid(nx, ny, candidate):
+    """A grid of many waves of tiles, ragged last tile row and column (1040 x
+    1000) and rows that are not 16-byte multiples (1030: per-element tile
+    loads), through the per-step launches."""
+    spec = [[B.SolverParams(nx=nx, ny=ny, zeta=0.01)]]
+    grp = make_groups(spec)
+    ens = B.Ensemble(grp)
+    ens.select(candidate)
+    ens.step(6)
+    ens.sync()
+    assert_same(grp, alone(spec, 6))
 
 
 def test_ensemble48_benchmarked_configuration():
     """The benchmarked ensemble: 48 instances of 128^2, 256^2 and 512^2 over
     the zeta / lambda / K combinations (instance b takes combination b mod 27
     of zeta in {0.001, 0.005, 0.01}, lambda in {0.3, 0.7, 1.1}, K in {0.02,
-    0.04, 0.08}; seed b), autotuned, one persistent launch per call.  Every
+    0.04, 0.08}; seed b), autotuned (the launch shape it picks).  Every
     member equals the same instances stepped context by context, bit for bit,
     and the next step of a 512^2 member matches the FP64 oracle on windows."""
     from helpers import interior, oracle_params, read_state, window_step
@@ -132,12 +175,12 @@ def test_ensemble48_benchmarked_configuration():
 
     grp = make()
     ens = B.Ensemble(grp)
-    ens.autotune(2)                       # first pass + 6 x 2 steps
+    ens.autotune(2)                       # first pass + 8 x 2 steps
     ens.step(5)
     ens.sync()
     ref = make()
     for tf in ref:
-        tf.step(18)
+        tf.step(1 + 2 * B.ENS_CANDIDATES + 5)
         tf.sync()
     for g, (a, b) in enumerate(zip(grp, ref)):
         for inst in range(a.batch):
