@@ -123,9 +123,7 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
             f2 pp = ld2(col + TF_BC(o + y0 - 1, H) * W), pcur = ld2(col + TF_BC(o + y0, H) * W);
             for (int y = y0; y < y1; ++y) {
                 const f2 pn = ld2(col + TF_BC(o + y + 1, H) * W);
-                f2 l, r;
-                nbr2(pcur, l, r);
-                const f2 lap = F2(m4, pcur, A2(A2(l, r), A2(pp, pn)));
+                const f2 lap = F2(m4, pcur, A2(hsum2(pcur), A2(pp, pn)));
                 const f2 poly = F2(pcur, F2(pcur, F2(pcur, mu3, mu2), mu1), mu0);
                 st_pair(mu + TF_BC((o + y) * W + pc.c0, A - 1), F2(kap, lap, poly), pc.st);
                 pp = pcur;
@@ -186,11 +184,8 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
     };
     // Compute row y from (Pr, Cr, Nr) = rows y-1, y, y+1 and write it back.
     auto do_row = [&](int y, const Row& Pr, const Row& Cr, const Row& Nr) {
-        f2 l, r;
-        nbr2(Cr.jx, l, r);
-        const f2 dJ = A2(B2(r, l), B2(Nr.jy, Pr.jy));
-        nbr2(Cr.mu, l, r);
-        const f2 lapmu = F2(m4, Cr.mu, A2(A2(l, r), A2(Nr.mu, Pr.mu)));
+        const f2 dJ = A2(hdiff2(Cr.jx), B2(Nr.jy, Pr.jy));
+        const f2 lapmu = F2(m4, Cr.mu, A2(hsum2(Cr.mu), A2(Nr.mu, Pr.mu)));
         const f2 nph = F2(hdt2, F2(M2x, lapmu, N2(dJ)), Cr.ph);
         const int row = o + y;
         const bool qrow = row >= oq && row < oq + th + 2 * rq;
@@ -202,26 +197,24 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
         // lie inside phi's): the row stays one basic block, so the phi and Q
         // chains of consecutive rows interleave.
         {
-            f2 al, ar, bl, br, uxl, uxr, uyl, uyr;
-            nbr2(Cr.qa, al, ar);
-            nbr2(Cr.qb, bl, br);
-            nbr2(Cr.ax, uxl, uxr);
-            nbr2(Cr.ay, uyl, uyr);
+            f2 ah, ax, bh, bx;
+            hsd2(Cr.qa, ah, ax);
+            hsd2(Cr.qb, bh, bx);
             const f2 a = Cr.qa, bq = Cr.qb;
-            const f2 lapa = F2(m4, a, A2(A2(al, ar), A2(Nr.qa, Pr.qa)));
-            const f2 lapb = F2(m4, bq, A2(A2(bl, br), A2(Nr.qb, Pr.qb)));
+            const f2 lapa = F2(m4, a, A2(ah, A2(Nr.qa, Pr.qa)));
+            const f2 lapb = F2(m4, bq, A2(bh, A2(Nr.qb, Pr.qb)));
             const f2 cg = F2(cGC, F2(a, a, M2(bq, bq)), cGA);      // -dt Gamma (A_Q + C_Q q^2)
-            const f2 Dxx = B2(uxr, uxl), Dyy = B2(Nr.ay, Pr.ay);
-            const f2 Dxy = B2(Nr.ax, Pr.ax), Dyx = B2(uyr, uyl);
+            const f2 Dxx = hdiff2(Cr.ax), Dyy = B2(Nr.ay, Pr.ay);
+            const f2 Dxy = B2(Nr.ax, Pr.ax), Dyx = hdiff2(Cr.ay);
             const f2 E1 = B2(Dxx, Dyy), EX = A2(Dxy, Dyx);
             const f2 t1 = F2(half, A2(Dxx, Dyy), N2(F2(a, E1, M2(bq, EX))));
             const f2 cc = F2(lamd, t1, cg);
             const f2 hO = M2(hdt2, B2(Dxy, Dyx));
             const f2 nux = M2(nhdt, Cr.ax), nuy = M2(nhdt, Cr.ay);
             const f2 nqa = A2(a, F2(cc, a, F2(cGK, lapa, F2(lamq, E1, F2(hO, bq,
-                                  F2(nux, B2(ar, al), M2(nuy, B2(Nr.qa, Pr.qa))))))));
+                                  F2(nux, ax, M2(nuy, B2(Nr.qa, Pr.qa))))))));
             const f2 nqb = A2(bq, F2(cc, bq, F2(cGK, lapb, F2(lamq, EX, F2(N2(hO), a,
-                                  F2(nux, B2(br, bl), M2(nuy, B2(Nr.qb, Pr.qb))))))));
+                                  F2(nux, bx, M2(nuy, B2(Nr.qb, Pr.qb))))))));
             st_pair(qa + c, nqa, qs && qrow);
             st_pair(qb + c, nqb, qs && qrow);
         }
@@ -410,12 +403,11 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
                 for (int y = y0; y < y1; ++y) {
                     const int cn = TF_BC((o + y + 1) * W + col, A - 1), cc = TF_BC((o + y) * W + col, A - 1);
                     const f2 dn = ld2(phi + cn), an = ld2(qa + cn), bn = ld2(qb + cn);
-                    f2 dl, dr, al, ar, bl, br;
-                    nbr2(dc, dl, dr);
-                    nbr2(ac, al, ar);
-                    nbr2(bc, bl, br);
+                    f2 ah, ax, bh, bx;
+                    hsd2(ac, ah, ax);
+                    hsd2(bc, bh, bx);
                     const PairStress r =
-                        stress2(P, dc, dl, dr, dn, dp, ac, al, ar, an, ap, bc, bl, br, bn, bp);
+                        stress2(P, dc, hsum2(dc), dn, dp, ac, ah, ax, an, ap, bc, bh, bx, bn, bp);
                     st_pair(tf_smem + P_MU * A + cc, r.mu, pc.st);
                     st_pair(tf_smem + P_U1X * A + cc, r.sxx, pc.st);
                     st_pair(tf_smem + P_U1Y * A + cc, r.sxy, pc.st);

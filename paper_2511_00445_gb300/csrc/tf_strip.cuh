@@ -90,15 +90,28 @@ __device__ __forceinline__ void st4(float* p, const V4& v) {
     *reinterpret_cast<float4*>(p) = make_float4(v.lo.x, v.lo.y, v.hi.x, v.hi.y);
 }
 
-// x-neighbours of each of a lane's four columns, as pairs (the outer ones
-// from the adjacent lanes): l = values at column - 1, r = at column + 1.
-__device__ __forceinline__ void nbr4(const V4& v, V4& l, V4& r) {
+// x-neighbour sums v(x - 1) + v(x + 1) and differences v(x + 1) - v(x - 1) of
+// a lane's four columns (the outer neighbours from the adjacent lanes), each
+// formed by one scalar operation straight into its pair, as hsd2 does for a
+// column pair (2048^2: 318 -> 301 us with the sub-step and stress phases on
+// these forms).
+__device__ __forceinline__ void hsd4(const V4& v, V4& s, V4& d) {
     const float up = __shfl_up_sync(0xffffffffu, v.hi.y, 1);
     const float dn = __shfl_down_sync(0xffffffffu, v.lo.x, 1);
-    l.lo = make_float2(up, v.lo.x);
-    l.hi = make_float2(v.lo.y, v.hi.x);
-    r.lo = make_float2(v.lo.y, v.hi.x);
-    r.hi = make_float2(v.hi.y, dn);
+    s = {make_float2(__fadd_rn(up, v.lo.y), __fadd_rn(v.lo.x, v.hi.x)),
+         make_float2(__fadd_rn(v.lo.y, v.hi.y), __fadd_rn(v.hi.x, dn))};
+    d = {make_float2(__fsub_rn(v.lo.y, up), __fsub_rn(v.hi.x, v.lo.x)),
+         make_float2(__fsub_rn(v.hi.y, v.lo.y), __fsub_rn(dn, v.hi.x))};
+}
+__device__ __forceinline__ V4 hsum4(const V4& v) {
+    V4 s, d;
+    hsd4(v, s, d);
+    return s;
+}
+__device__ __forceinline__ V4 hdiff4(const V4& v) {
+    V4 s, d;
+    hsd4(v, s, d);
+    return d;
 }
 
 // Ring slots of segment row t (any t >= -3 DP; rows below -HALO, or -1 for
@@ -238,15 +251,15 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 oph = phc;
                 // mu = -kappa lap(phi) + A_ch f'(phi) (Eq. 2) of the middle row
                 auto mu_row = [&](const V4& pp, const V4& pc, const V4& pn) {
-                    V4 l, r, mu;
-                    nbr4(pc, l, r);
+                    V4 mu;
+                    const V4 h = hsum4(pc);
                     {
-                        const f2 lap = F2(m4, pc.lo, A2(A2(l.lo, r.lo), A2(pp.lo, pn.lo)));
+                        const f2 lap = F2(m4, pc.lo, A2(h.lo, A2(pp.lo, pn.lo)));
                         const f2 poly = F2(pc.lo, F2(pc.lo, F2(pc.lo, mu3, mu2), mu1), mu0);
                         mu.lo = F2(kap, lap, poly);
                     }
                     {
-                        const f2 lap = F2(m4, pc.hi, A2(A2(l.hi, r.hi), A2(pp.hi, pn.hi)));
+                        const f2 lap = F2(m4, pc.hi, A2(h.hi, A2(pp.hi, pn.hi)));
                         const f2 poly = F2(pc.hi, F2(pc.hi, F2(pc.hi, mu3, mu2), mu1), mu0);
                         mu.hi = F2(kap, lap, poly);
                     }
@@ -264,17 +277,15 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 jys.hi = flux(A2(cref, phs.hi), ays.hi, bys.hi);
                 jyn.lo = flux(A2(cref, phn.lo), ayn.lo, byn.lo);
                 jyn.hi = flux(A2(cref, phn.hi), ayn.hi, byn.hi);
-                V4 jl, jr, ml, mr;
-                nbr4(jx, jl, jr);
-                nbr4(muc, ml, mr);
+                const V4 djx = hdiff4(jx), hm = hsum4(muc);
                 {
-                    const f2 dJ = A2(B2(jr.lo, jl.lo), B2(jyn.lo, jys.lo));
-                    const f2 lapmu = F2(m4, muc.lo, A2(A2(ml.lo, mr.lo), A2(mun.lo, mus.lo)));
+                    const f2 dJ = A2(djx.lo, B2(jyn.lo, jys.lo));
+                    const f2 lapmu = F2(m4, muc.lo, A2(hm.lo, A2(mun.lo, mus.lo)));
                     nph.lo = F2(hdt2, F2(M2x, lapmu, N2(dJ)), phc.lo);
                 }
                 {
-                    const f2 dJ = A2(B2(jr.hi, jl.hi), B2(jyn.hi, jys.hi));
-                    const f2 lapmu = F2(m4, muc.hi, A2(A2(ml.hi, mr.hi), A2(mun.hi, mus.hi)));
+                    const f2 dJ = A2(djx.hi, B2(jyn.hi, jys.hi));
+                    const f2 lapmu = F2(m4, muc.hi, A2(hm.hi, A2(mun.hi, mus.hi)));
                     nph.hi = F2(hdt2, F2(M2x, lapmu, N2(dJ)), phc.hi);
                 }
                 // Q^(s) of the row, also where only phi^(s) is exact (vp && !vq:
@@ -288,34 +299,33 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                     oqa = ac;
                     oqb = bc;
                     const V4 axs = ld4(u1x + us), axn = ld4(u1x + un), ayc = ld4(u1y + uc);
-                    V4 al, ar, bl, br, uxl, uxr, uyl, uyr;
-                    nbr4(ac, al, ar);
-                    nbr4(bc, bl, br);
-                    nbr4(axc, uxl, uxr);
-                    nbr4(ayc, uyl, uyr);
-                    auto qpair = [&](f2 a, f2 bq, f2 al_, f2 ar_, f2 an_, f2 as_, f2 bl_, f2 br_, f2 bn_,
-                                     f2 bs_, f2 uxl_, f2 uxr_, f2 uyl_, f2 uyr_, f2 axn_, f2 axs_,
+                    V4 ah, ax, bh, bx;
+                    hsd4(ac, ah, ax);
+                    hsd4(bc, bh, bx);
+                    const V4 dux = hdiff4(axc), duy = hdiff4(ayc);
+                    auto qpair = [&](f2 a, f2 bq, f2 ah_, f2 ax_, f2 an_, f2 as_, f2 bh_, f2 bx_, f2 bn_,
+                                     f2 bs_, f2 dux_, f2 duy_, f2 axn_, f2 axs_,
                                      f2 ayn_, f2 ays_, f2 axc_, f2 ayc_, f2& oa, f2& ob) {
-                        const f2 lapa = F2(m4, a, A2(A2(al_, ar_), A2(an_, as_)));
-                        const f2 lapb = F2(m4, bq, A2(A2(bl_, br_), A2(bn_, bs_)));
+                        const f2 lapa = F2(m4, a, A2(ah_, A2(an_, as_)));
+                        const f2 lapb = F2(m4, bq, A2(bh_, A2(bn_, bs_)));
                         const f2 cg = F2(cGC, F2(a, a, M2(bq, bq)), cGA);
-                        const f2 Dxx = B2(uxr_, uxl_), Dyy = B2(ayn_, ays_);
-                        const f2 Dxy = B2(axn_, axs_), Dyx = B2(uyr_, uyl_);
+                        const f2 Dxx = dux_, Dyy = B2(ayn_, ays_);
+                        const f2 Dxy = B2(axn_, axs_), Dyx = duy_;
                         const f2 E1 = B2(Dxx, Dyy), EX = A2(Dxy, Dyx);
                         const f2 t1 = F2(half, A2(Dxx, Dyy), N2(F2(a, E1, M2(bq, EX))));
                         const f2 cc = F2(lamd, t1, cg);
                         const f2 hO = M2(hdt2, B2(Dxy, Dyx));
                         const f2 nux = M2(nhdt, axc_), nuy = M2(nhdt, ayc_);
                         oa = A2(a, F2(cc, a, F2(cGK, lapa, F2(lamq, E1, F2(hO, bq,
-                                F2(nux, B2(ar_, al_), M2(nuy, B2(an_, as_))))))));
+                                F2(nux, ax_, M2(nuy, B2(an_, as_))))))));
                         ob = A2(bq, F2(cc, bq, F2(cGK, lapb, F2(lamq, EX, F2(N2(hO), a,
-                                F2(nux, B2(br_, bl_), M2(nuy, B2(bn_, bs_))))))));
+                                F2(nux, bx_, M2(nuy, B2(bn_, bs_))))))));
                     };
-                    qpair(ac.lo, bc.lo, al.lo, ar.lo, an.lo, as.lo, bl.lo, br.lo, bn.lo, bs.lo,
-                          uxl.lo, uxr.lo, uyl.lo, uyr.lo, axn.lo, axs.lo, ayn.lo, ays.lo, axc.lo,
+                    qpair(ac.lo, bc.lo, ah.lo, ax.lo, an.lo, as.lo, bh.lo, bx.lo, bn.lo, bs.lo,
+                          dux.lo, duy.lo, axn.lo, axs.lo, ayn.lo, ays.lo, axc.lo,
                           ayc.lo, nqa.lo, nqb.lo);
-                    qpair(ac.hi, bc.hi, al.hi, ar.hi, an.hi, as.hi, bl.hi, br.hi, bn.hi, bs.hi,
-                          uxl.hi, uxr.hi, uyl.hi, uyr.hi, axn.hi, axs.hi, ayn.hi, ays.hi, axc.hi,
+                    qpair(ac.hi, bc.hi, ah.hi, ax.hi, an.hi, as.hi, bh.hi, bx.hi, bn.hi, bs.hi,
+                          dux.hi, duy.hi, axn.hi, axs.hi, ayn.hi, ays.hi, axc.hi,
                           ayc.hi, nqa.hi, nqb.hi);
                 }
             }
@@ -359,14 +369,21 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 const V4 dp = ld4(ps), dc = ld4(pc), dn = ld4(pn);
                 const V4 ap = ld4(ps + dqa), ac = ld4(pc + dqa), an = ld4(pn + dqa);
                 const V4 bp = ld4(ps + dqb), bc = ld4(pc + dqb), bn = ld4(pn + dqb);
-                V4 dl, dr, al, ar, bl, br;
-                nbr4(dc, dl, dr);
-                nbr4(ac, al, ar);
-                nbr4(bc, bl, br);
-                const PairStress r0 = stress2(P, dc.lo, dl.lo, dr.lo, dn.lo, dp.lo, ac.lo, al.lo,
-                                              ar.lo, an.lo, ap.lo, bc.lo, bl.lo, br.lo, bn.lo, bp.lo);
-                const PairStress r1 = stress2(P, dc.hi, dl.hi, dr.hi, dn.hi, dp.hi, ac.hi, al.hi,
-                                              ar.hi, an.hi, ap.hi, bc.hi, bl.hi, br.hi, bn.hi, bp.hi);
+                const V4 dh = hsum4(dc);
+                V4 ah, ax, bh, bx;
+                hsd4(ac, ah, ax);
+                hsd4(bc, bh, bx);
+                const PairStress r0 = stress2(P, dc.lo, dh.lo, dn.lo, dp.lo, ac.lo, ah.lo, ax.lo,
+                                               an.lo, ap.lo, bc.lo, bh.lo, bx.lo, bn.lo, bp.lo);
+                const PairStress r1 = stress2(P, dc.hi, dh.hi, dn.hi, dp.hi, ac.hi, ah.hi, ax.hi,
+                                               an.hi, ap.hi, bc.hi, bh.hi, bx.hi, bn.hi, bp.hi);
+                // the row's final phi, Q (strip columns): 16-byte stores
+                if (y >= 0 && y < SG && col >= ts::HALO && col < ts::HALO + tw) {
+                    const int g = TF_BC((y0 + y) * nx + x0 + col - ts::HALO, (int)N - 3);
+                    st4(a.phi_out + b * N + g, dc);
+                    st4(a.Q_out + 2 * b * N + g, ac);
+                    st4(a.Q_out + (2 * b + 1) * N + g, bc);
+                }
                 if (lane >= ts::SC0 / 4 && lane < (ts::SC0 + ts::SW) / 4) {
                     float* st = sm + ts::OFF_ST + TF_BC(sslot(y), ts::DS) * ts::SW +
                                 TF_BC(col - ts::SC0, ts::SW - 3);
@@ -391,8 +408,6 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             typename S::T* __restrict__ D1 = a.fdst + 18 * b * N;
             typename S::T* __restrict__ D2 = D1 + 9 * N;
             float* __restrict__ uo = a.u_out + 4 * b * N;
-            float* __restrict__ po = a.phi_out + b * N;
-            float* __restrict__ qo = a.Q_out + 2 * b * N;
             const float* stb = sm + ts::OFF_ST - ts::SC0;   // stress ring, window columns
             constexpr int PL = ts::DS * ts::SW;
             // pulled populations of site (block row r, column cx): f_i(x - c_i)
@@ -454,9 +469,6 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                 uo[N + g] = u1.y;
                 uo[2 * N + g] = u2.x;
                 uo[3 * N + g] = u2.y;
-                po[g] = ph[c];
-                qo[g] = sm[ts::OFF_QA + pc + c];
-                qo[N + g] = sm[ts::OFF_QB + pc + c];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = fn[i];
                 r = rn;
