@@ -18,8 +18,9 @@ four 256 x 256 instances; its state (~44 MB) fits in L2, so L2 is flushed
 
 --workload ensemble48 steps 48 instances of three sizes (the parameter-sweep
 ensemble) through the ensemble API with the launch shape its autotuner chose
-(one persistent launch for all steps, or one launch per step over every tile
-of every group), and also times the same instances stepped context by context.
+(one persistent launch for all steps, one launch per step over every tile of
+every group, or each group's own planned launches recorded into one graph),
+and also times the same instances stepped context by context.
 
 --storage f16|bf16 stores the populations as 16-bit deviations (FP32
 arithmetic).  Such a run also times the FP32 storage on the same workload
@@ -699,6 +700,8 @@ def run_ensemble(args, wl):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                 "kernel": ("k_ens (persistent, all steps in one launch)" if cfg["persistent"] else
+                           "each group's own planned kernel (k_strip / k_fused<1,1>), one launch "
+                           "per group and step" if cfg["group_plans"] else
                            "k_ens_step (one launch per step over every tile of every group)"),
                 "bytes_per_site": bps,
                 "launches_per_step": launches / args.steps,

@@ -178,9 +178,10 @@ int tf_step(tf_ctx* ctx, int64_t n);
  *                    segment, walked down in blocks of 8 rows with the five
  *                    sub-steps pipelined two rows apart (needs nx % 4 == 0);
  *   TF_KERNEL_AUTO:  the strip kernel when the context's 32 x 32 tiles exceed
- *                    one wave of resident CTAs, nx % 4 == 0 and its row
- *                    segments are at least 128 rows long (e.g. 2048^2), else
- *                    the tile kernel.
+ *                    one wave of resident CTAs, nx % 4 == 0 and its strips x
+ *                    row segments (segments of at least 32 rows) fill at
+ *                    least 90% of one wave (e.g. 1024^2, 2048^2, 4 x 512^2),
+ *                    else the tile kernel.
  * tf_set_step_kernel takes effect from the next step (TF_ERR_ARG for an
  * unknown kind, or TF_KERNEL_STRIP on a context it cannot step);
  * tf_step_kernel returns TF_KERNEL_TILE or TF_KERNEL_STRIP, the kernel the
@@ -330,7 +331,7 @@ int tf_plan_tiles(int nx, int ny, int batch, long long slots, int out[3], int* c
  * destroyed, while the ensemble exists. */
 typedef struct tf_ensemble tf_ensemble;
 #define TF_ENS_MAX_GROUPS 64
-#define TF_ENS_CANDIDATES 8    /* autotuner candidates, see tf_ensemble_autotune */
+#define TF_ENS_CANDIDATES 9    /* autotuner candidates, see tf_ensemble_autotune */
 
 /* Device workspace bytes for an ensemble of n_groups (1..64) groups; 0 when
  * n_groups is out of range. */
@@ -349,10 +350,10 @@ const char* tf_ensemble_last_error(const tf_ensemble* ens);
 
 /* Advance every member instance by n >= 0 steps: an LBM-only first pass
  * when the members hold a completed state, then the remaining steps as one
- * persistent launch (candidates 0..5 of tf_ensemble_autotune) or as one
- * launch per step covering every tile of every group (candidates 6, 7), up
- * to 1024 steps per launch or per recorded graph.  Asynchronous on the
- * ensemble's stream. */
+ * persistent launch (candidates 0..5 of tf_ensemble_autotune), as one launch
+ * per step covering every tile of every group (candidates 6, 7), or as each
+ * group's own per-context launches (candidate 8), up to 1024 steps per launch
+ * or per recorded graph.  Asynchronous on the ensemble's stream. */
 int tf_ensemble_step(tf_ensemble* ens, int64_t n);
 
 /* Wait for the ensemble's work and report the members' device status
@@ -366,7 +367,9 @@ int tf_ensemble_sync(tf_ensemble* ens);
  * Candidates 6 and 7: one launch per step with one CTA per tile of every
  * group (populations read through L1, as in per-context stepping), tile
  * shape 32 x 32 and 40 x 30.  40-column tiles cut columns at multiples of 4,
- * up to 40 wide.  Each candidate runs `steps_per_candidate` (1..1024) real
+ * up to 40 wide.  Candidate 8: per step, each group's own per-context launch
+ * (the strip or tile kernel its plan picks, see tf_set_step_kernel), recorded
+ * into the same graph.  Each candidate runs `steps_per_candidate` (1..1024) real
  * steps timed with CUDA events; the fastest becomes the configuration.  Every
  * candidate computes bitwise the same trajectory, so the tuning steps are
  * ordinary steps: the ensemble advances by TF_ENS_CANDIDATES *
@@ -374,9 +377,10 @@ int tf_ensemble_sync(tf_ensemble* ens);
  * Synchronous. */
 int tf_ensemble_autotune(tf_ensemble* ens, int steps_per_candidate);
 
-/* Current configuration: tile height (30 means the 40 x 30 shape), CTAs per
- * SM, grid size of one launch (of the persistent launch, or tiles per step
- * for candidates 6, 7), tiles per step; us_per_step (may be NULL) receives the
+/* Current configuration: tile height (30 means the 40 x 30 shape; 0 for
+ * candidate 8), CTAs per SM, grid size of one launch (of the persistent
+ * launch, tiles per step for candidates 6, 7, all groups' CTAs per step for
+ * candidate 8), tiles per step; us_per_step (may be NULL) receives the
  * TF_ENS_CANDIDATES autotuner timings in microseconds per step (0 before
  * tf_ensemble_autotune).  *graphs = 1 when launches replay CUDA graphs, 0
  * when they are issued directly (stream capture unavailable). */
@@ -396,7 +400,7 @@ int tf_ensemble_candidate(const tf_ensemble* ens);
 int tf_ensemble_select(tf_ensemble* ens, int candidate);
 
 /* Failure-detection drill for the persistent launch's grid barrier (candidates
- * 0..5; launches of candidates 6, 7 have no grid barrier) (no fault
+ * 0..5; launches of candidates 6..8 have no grid barrier) (no fault
  * is injected on the device: a CTA just leaves early).  From the next
  * tf_ensemble_step on, the barrier gives up after `barrier_polls` polls of
  * ~128 ns each (0 restores the default of about one second) and, when

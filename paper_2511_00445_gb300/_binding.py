@@ -69,8 +69,9 @@ class TFSurConfig(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("base_channels", ctypes.c_int), ("nx", ctypes.c_int),
                 ("ny", ctypes.c_int), ("max_batch", ctypes.c_int), ("max_pairs", ctypes.c_int),
                 ("horizon", ctypes.c_int)]
-ENS_CANDIDATES = 8
+ENS_CANDIDATES = 9
 ENS_PERSISTENT_CANDIDATES = 6     # candidates 0..5: one persistent launch; 6, 7: a launch per step
+ENS_GROUP_PLANS = 8               # candidate 8: each group's own per-context launches
 
 
 class TFParams(ctypes.Structure):
@@ -454,6 +455,7 @@ class Ensemble:
                                                 ctypes.byref(gr)))
         cand = self.candidate()
         return {"candidate": cand, "persistent": cand < ENS_PERSISTENT_CANDIDATES,
+                "group_plans": cand == ENS_GROUP_PLANS,
                 "tile_y": ty.value, "ctas_per_sm": cps.value, "grid": grid.value,
                 "tiles_per_step": tiles.value, "us_per_step": us.tolist(), "graphs": bool(gr.value),
                 "note": self.lib.tf_ensemble_last_error(self.ens).decode()}

@@ -25,9 +25,11 @@ constexpr int kTileX[3] = {TX, TX, TX_WIDE};
 constexpr int kTileY[3] = {32, 24, TY_WIDE};
 // Candidates 0..5: persistent launches, tile shape c / 2 with 2 - c % 2 CTAs
 // per SM; 6, 7: one launch per step over every tile of every group (k_ens_step)
-// with the 32 x 32 and the 40 x 30 shape.
+// with the 32 x 32 and the 40 x 30 shape; 8: every group's own planned
+// per-context launch (strip or tile kernel) per step.
 constexpr int kCandidates = TF_ENS_CANDIDATES;
 constexpr int kPersistentCandidates = 6;
+constexpr int kGroupPlans = 8;
 constexpr bool persistent_cfg(int c) { return c < kPersistentCandidates; }
 constexpr int shape_of(int c) { return c < kPersistentCandidates ? c / 2 : (c == 6 ? 0 : 2); }
 constexpr int ctas_of(int c) { return c < kPersistentCandidates ? 2 - c % 2 : 2; }
@@ -288,7 +290,19 @@ int efail_cuda(tf_ensemble* e, const char* where, cudaError_t err) {
         if (e_ != cudaSuccess) return efail_cuda(e, #call, e_);  \
     } while (0)
 
+// CTAs of one step of group member c under its own per-context plan.
+long long planned_ctas(tf_ctx* c) {
+    if (c->tile_rows <= 0 && tf_plan_fused(c) != cudaSuccess) return 0;
+    return c->use_strip ? (long long)c->strip_cols * c->strip_segs * c->batch
+                        : (long long)c->tile_cols * c->tile_rows * c->batch;
+}
+
 int grid_for(tf_ensemble* e, int mode, int cfg) {
+    if (mode == kSteady && cfg == kGroupPlans) {   // CTAs of all groups' launches of one step
+        long long n = 0;
+        for (tf_ctx* c : e->groups) n += planned_ctas(c);
+        return (int)n;
+    }
     const int ti = mode == kPrologue ? 0 : shape_of(cfg);
     if (mode == kSteady && !persistent_cfg(cfg)) return (int)e->tiles[ti];   // one CTA per tile
     const int want = mode == kPrologue ? 2 : ctas_of(cfg);
@@ -308,6 +322,17 @@ int grid_for(tf_ensemble* e, int mode, int cfg) {
 cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid, cudaStream_t st) {
     const int ti = mode == kPrologue ? 0 : shape_of(cfg);
     if (grid < 1) return cudaErrorInvalidConfiguration;
+    if (mode == kSteady && cfg == kGroupPlans) {
+        // each group's own launches, from the ensemble's buffer parities
+        for (size_t g = 0; g < e->groups.size(); ++g) {
+            tf_ctx* c = e->groups[g];
+            FusedCursor cur{e->base_f[g] ^ e->fpar, e->base_p[g] ^ e->ppar,
+                            e->base_u[g] ^ e->upar, true};
+            const cudaError_t err = tf_fused_span(c, 0, c->batch, steps, false, st, &cur);
+            if (err != cudaSuccess) return err;
+        }
+        return cudaSuccess;
+    }
     if (mode == kSteady && !persistent_cfg(cfg)) {
         const StepKernel k = step_kernel_for(e->storage, ti);
         const size_t smem = smem_for(kSteady, ti);
@@ -385,7 +410,9 @@ int issue(tf_ensemble* e, int mode, int steps) {
         }
         if (!done) TF_ECK(e, enqueue(e, mode, steps, e->cfg, grid, e->stream));
     }
-    e->launches += mode == kSteady && !persistent_cfg(e->cfg) ? steps : 1;
+    e->launches += mode == kSteady && e->cfg == kGroupPlans
+                       ? (int64_t)steps * (int64_t)e->groups.size()
+                       : (mode == kSteady && !persistent_cfg(e->cfg) ? steps : 1);
     if (mode == kPrologue) {
         e->fpar ^= 1;
         e->upar ^= 1;
@@ -633,10 +660,12 @@ int tf_ensemble_config(const tf_ensemble* e, int* tile_y, int* ctas_per_sm, int*
                        int64_t* tiles_per_step, double* us_per_step, int* graphs) {
     if (!e) return TF_ERR_ARG;
     const int ti = shape_of(e->cfg);
-    if (tile_y) *tile_y = kTileY[ti];
+    const bool plans = e->cfg == kGroupPlans;
+    const int g = grid_for(const_cast<tf_ensemble*>(e), kSteady, e->cfg);
+    if (tile_y) *tile_y = plans ? 0 : kTileY[ti];
     if (ctas_per_sm) *ctas_per_sm = ctas_of(e->cfg);
-    if (grid) *grid = grid_for(const_cast<tf_ensemble*>(e), kSteady, e->cfg);
-    if (tiles_per_step) *tiles_per_step = e->tiles[ti];
+    if (grid) *grid = g;
+    if (tiles_per_step) *tiles_per_step = plans ? g : e->tiles[ti];
     if (us_per_step)
         for (int c = 0; c < kCandidates; ++c) us_per_step[c] = e->us[c];
     if (graphs) *graphs = e->graphs ? 1 : 0;

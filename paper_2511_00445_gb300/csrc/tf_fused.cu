@@ -184,11 +184,15 @@ int tile_rows_for(int ntx, int ny, int tym, int batch, long long slots) {
 // up to 12 rows of sub-step halo above and below it).
 constexpr int kMinSegRows = 32;
 // TF_KERNEL_AUTO picks the strip kernel on grids of several waves of tiles
-// whose strip segments are at least this long: each segment recomputes up to
-// 12 rows of sub-step halo above and below it, so short segments lose to the
-// tiles (measured: 2048^2, 158-row segments, strip 376 vs tile 381 us per
-// step; 1024^2, 38-row segments, 112 vs 109 us).
-constexpr int kAutoStripMinRows = 128;
+// when the strip plan keeps at least 90% of one wave of resident CTAs busy.
+// Each strip segment (at least kMinSegRows rows) pays up to 12 rows of
+// sub-step halo above and below it and a pipeline fill of about seven 8-row
+// blocks, so a strip plan that leaves SMs idle loses to the tiles.  Measured
+// (us per step, strip / tile): 2048^2 301 / 348, 1536^2 170 / 210, 1024^2
+// (297 CTAs, 38-row segments) 90 / 98, 2 x 1024^2 161 / 181, 4 x 512^2 97 /
+// 106; 768^2 (192 CTAs) 78 / 69, 640^2 (140 CTAs) 49 / 49, 512^2 (96 CTAs)
+// 49 / 31.
+constexpr int kAutoStripFillPct = 90;
 
 int strip_segs_for(int ncols, int ny, int batch, long long slots) {
     const long long per = (long long)ncols * batch;
@@ -218,11 +222,12 @@ cudaError_t plan_tile_rows(tf_ctx* ctx) {
     ctx->strip_cols = (ctx->nx + ts::TWMAX - 1) / ts::TWMAX;
     ctx->strip_segs = strip_segs_for(ctx->strip_cols, ctx->ny, ctx->batch,
                                      (long long)sms * (per_sm_strip > 0 ? per_sm_strip : 1));
-    // Steady-state kernel (tf_set_step_kernel; AUTO: see kAutoStripMinRows).
+    // Steady-state kernel (tf_set_step_kernel; AUTO: see kAutoStripFillPct).
     const bool can = tf_strip_supported(ctx) && per_sm_strip > 0;
-    const bool long_segs = ctx->ny / ctx->strip_segs >= kAutoStripMinRows;
+    const long long strip_ctas = (long long)ctx->strip_cols * ctx->batch * ctx->strip_segs;
+    const bool fills = strip_ctas * 100 >= (long long)sms * per_sm_strip * kAutoStripFillPct;
     ctx->use_strip = can && (ctx->step_kernel == TF_KERNEL_STRIP ||
-                             (ctx->step_kernel == TF_KERNEL_AUTO && ctx->wide_tiles && long_segs));
+                             (ctx->step_kernel == TF_KERNEL_AUTO && ctx->wide_tiles && fills));
     return cudaSuccess;
 }
 

@@ -46,10 +46,11 @@ def run_cases() -> dict:
             for f in FIELDS:
                 out[f"{nx}x{ny}_{kernel}_{n_sub}_{storage}_{inst}_{f}"] = tf.read_field(inst, f)
         tf.close()
-    # ensembles of ragged groups: the persistent launch (candidate 0) and the
-    # per-step launches with both tile shapes (candidates 6, 7)
+    # ensembles of ragged groups: the persistent launch (candidate 0), the
+    # per-step launches with both tile shapes (candidates 6, 7) and the groups'
+    # own launches (candidate 8)
     base = B.SolverParams(zeta=0.01)
-    for cand in (0, 6, 7):
+    for cand in (0, 6, 7, 8):
         groups = [B.TwoFluid([base.with_(nx=40, ny=36), base.with_(nx=40, ny=36, lam=1.1)]),
                   B.TwoFluid(base.with_(nx=33, ny=17)), B.TwoFluid(base.with_(nx=100, ny=70))]
         for g, tf in enumerate(groups):

@@ -93,37 +93,40 @@ def test_large_grid_matches_grid_stepped_alone(nx, ny, storage):
 
 
 def test_ensemble_autotune_steps_are_real_steps():
-    """Eight candidates (persistent launches with tile shapes 32x32, 32x24 and
-    40x30 and one or two CTAs per SM; one launch per step with 32x32 or 40x30)
-    each run real steps; the trajectory equals stepping alone."""
+    """Nine candidates (persistent launches with tile shapes 32x32, 32x24 and
+    40x30 and one or two CTAs per SM; one launch per step with 32x32 or 40x30;
+    the groups' own per-context launches) each run real steps; the trajectory
+    equals stepping alone."""
     spec = groups_spec()
     grp = make_groups(spec)
     ens = B.Ensemble(grp)
-    ens.autotune(2)                       # first pass + 8 x 2 steps
+    ens.autotune(2)                       # first pass + 9 x 2 steps
     ens.step(3)
     ens.sync()
     assert_same(grp, alone(spec, 1 + 2 * B.ENS_CANDIDATES + 3))
     cfg = ens.config()
-    assert len(cfg["us_per_step"]) == B.ENS_CANDIDATES == 8
+    assert len(cfg["us_per_step"]) == B.ENS_CANDIDATES == 9
     assert all(us > 0 for us in cfg["us_per_step"])
-    assert cfg["tile_y"] in (24, 30, 32) and cfg["ctas_per_sm"] in (1, 2)
-    assert 0 <= cfg["candidate"] < 8
+    assert cfg["tile_y"] in (0, 24, 30, 32) and cfg["ctas_per_sm"] in (1, 2)
+    assert 0 <= cfg["candidate"] < 9
     assert cfg["persistent"] == (cfg["candidate"] < 6)
 
 
-@pytest.mark.parametrize("candidate", [6, 7])
+@pytest.mark.parametrize("candidate", [6, 7, 8])
 @pytest.mark.parametrize("storage", [B.STORE_F32, B.STORE_BF16], ids=["f32", "bf16"])
 def test_per_step_launch_candidates(candidate, storage):
     """Candidates 6 and 7 (one launch per step over every tile of every
-    group, populations read through L1) step the ragged groups bitwise like
-    each context stepped alone, across a member read and repeated calls."""
+    group, populations read through L1) and 8 (each group's own per-context
+    launches) step the ragged groups bitwise like each context stepped alone,
+    across a member read and repeated calls."""
     spec = groups_spec(storage)
     grp = make_groups(spec)
     ens = B.Ensemble(grp)
     ens.select(candidate)
     l0 = ens.launches()
     ens.step(4)
-    assert ens.launches() - l0 == 1 + 3   # the LBM-only first pass, then one launch per step
+    per_step = len(grp) if candidate == 8 else 1
+    assert ens.launches() - l0 == 1 + 3 * per_step   # the LBM-only first pass, then the steps
     grp[1].read_field(0, B.FIELD_PHI)
     ens.step(3)
     ens.step(3)
@@ -131,16 +134,17 @@ def test_per_step_launch_candidates(candidate, storage):
     assert_same(grp, alone(spec, 10))
     cfg = ens.config()
     assert cfg["candidate"] == candidate and not cfg["persistent"]
-    assert cfg["grid"] == cfg["tiles_per_step"]
+    assert cfg["grid"] == cfg["tiles_per_step"] > 0
     with pytest.raises(B.TwoFluidError):
-        ens.select(8)
+        ens.select(9)
 
 
-@pytest.mark.parametrize("nx,ny,candidate", [(1040, 1000, 7), (1030, 1000, 6)])
+@pytest.mark.parametrize("nx,ny,candidate", [(1040, 1000, 7), (1030, 1000, 6), (1024, 1024, 8)])
 def test_per_step_launches_large_grid(nx, ny, candidate):
     """A grid of many waves of tiles, ragged last tile row and column (1040 x
     1000) and rows that are not 16-byte multiples (1030: per-element tile
-    loads), through the per-step launches."""
+    loads), through the per-step launches; 1024^2 through its own planned
+    launches (the strip kernel)."""
     spec = [[B.SolverParams(nx=nx, ny=ny, zeta=0.01)]]
     grp = make_groups(spec)
     ens = B.Ensemble(grp)

@@ -95,15 +95,22 @@ def test_strip_parity_against_oracle(nx, ny):
 
 
 def test_kernel_selection():
-    huge = B.TwoFluid(CFG0.with_(nx=2048, ny=2048))     # long strip segments: strip
-    assert huge.step_kernel() == B.KERNEL_STRIP
-    huge.close()
-    big = B.TwoFluid(CFG0.with_(nx=1024, ny=1024))      # short segments: tiles
+    """AUTO takes the strip kernel where its plan fills a wave of resident
+    CTAs (2048^2, 1024^2, 4 x 512^2) and the tiles where it would leave SMs
+    idle (768^2: 192 strip CTAs; 512^2; the 4 x 256^2 sweep) or cannot run."""
+    for n, b in ((2048, 1), (1024, 1), (512, 4)):
+        t = B.TwoFluid([CFG0.with_(nx=n, ny=n)] * b)
+        assert t.step_kernel() == B.KERNEL_STRIP, (n, b)
+        t.close()
+    for n, b in ((768, 1), (512, 1), (256, 4)):
+        t = B.TwoFluid([CFG0.with_(nx=n, ny=n)] * b)
+        assert t.step_kernel() == B.KERNEL_TILE, (n, b)
+        t.close()
+    big = B.TwoFluid(CFG0.with_(nx=1024, ny=1024))
+    big.set_step_kernel("tile")
     assert big.step_kernel() == B.KERNEL_TILE
     big.set_step_kernel("strip")
     assert big.step_kernel() == B.KERNEL_STRIP
-    big.set_step_kernel("tile")
-    assert big.step_kernel() == B.KERNEL_TILE
     small = B.TwoFluid(CFG0.with_(nx=64, ny=64))
     assert small.step_kernel() == B.KERNEL_TILE
     odd = B.TwoFluid(CFG0.with_(nx=1026, ny=1024))      # rows not 16-byte multiples
