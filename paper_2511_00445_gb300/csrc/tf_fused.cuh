@@ -370,9 +370,10 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         __syncthreads();
     }
 
-    // ---- stage 2: sub-steps of the pending FD
+    // ---- stage 2: sub-steps of the pending FD (unrolled: the radii are
+    // constants in each copy)
     if constexpr (DO_FD) {
-#pragma unroll 1
+#pragma unroll
         for (int st = 0; st < NS_FUSED; ++st) {
             const int rp = G::R_END + 2 * (NS_FUSED - 1 - st);
             const int rq = G::R_END + (NS_FUSED - 1 - st);

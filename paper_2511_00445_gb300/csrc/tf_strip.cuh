@@ -215,8 +215,10 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             }
         }
 
-        // ---- the five sub-steps
-#pragma unroll 1
+        // ---- the five sub-steps, unrolled so that every row bound, shadow row
+        // and ring offset that depends on s is a constant (2048^2: 301 -> 292
+        // us; unrolling the LBM site loop as well made the code too large)
+#pragma unroll
         for (int s = 1; s <= ts::NSUB; ++s) {
             const int E = L - 2 * s;                       // block rows [E - R, E)
             const int lo = -(12 - 2 * s), hi = SG + 12 - 2 * s;     // exact rows of phi^(s)
