@@ -1009,6 +1009,7 @@ int tf_sur_init_weights(tf_surrogate* s, uint64_t seed) {
 }
 
 int tf_sur_forward(tf_surrogate* s, const float* x, int batch, float* out) {
+    const TfRange nvtx_range("tf_sur_forward");
     if (!s) return TF_ERR_ARG;
     if (!x || !out || batch < 1 || batch > s->cfg.max_batch) return sfail(s, TF_ERR_ARG, "bad batch or null array");
     int rc = upload_x(s, x, batch);
@@ -1096,6 +1097,7 @@ int tf_sur_fit_normalisation(tf_surrogate* s, int n_pairs) {
 
 int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, uint64_t seed,
                  double* losses) {
+    const TfRange nvtx_range("tf_sur_train");
     if (!s) return TF_ERR_ARG;
     if (!s->norm_ready) return sfail(s, TF_ERR_ARG, "call tf_sur_fit_normalisation first");
     if (n_pairs < 1 || n_pairs > s->cfg.max_pairs || steps < 0 || batch < 1 || batch > s->cfg.max_batch ||
@@ -1127,6 +1129,7 @@ int tf_sur_train(tf_surrogate* s, int n_pairs, int steps, int batch, double lr, 
 }
 
 int tf_sur_predict(tf_surrogate* s, tf_ctx* ctx, int inst) {
+    const TfRange nvtx_range("tf_sur_predict");
     if (!s || !ctx) return TF_ERR_ARG;
     if (!s->norm_ready) return sfail(s, TF_ERR_ARG, "call tf_sur_fit_normalisation first");
     const int i0 = inst < 0 ? 0 : inst, nb = inst < 0 ? ctx->batch : 1;

@@ -276,6 +276,7 @@ int tf_set_equilibrium(tf_ctx* ctx, int inst, const double* u1, const double* u2
 }
 
 int tf_read_field(tf_ctx* ctx, int inst, int field, double* host) {
+    const TfRange nvtx_range("tf_read_field");
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !host) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
     if (!((field >= TF_FIELD_PHI && field <= TF_FIELD_OMEGA_C) || is_pop_field(field)))
@@ -289,6 +290,7 @@ int tf_read_field(tf_ctx* ctx, int inst, int field, double* host) {
 }
 
 int tf_step(tf_ctx* ctx, int64_t n) {
+    const TfRange nvtx_range("tf_step");
     if (!ctx) return TF_ERR_ARG;
     if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
     if (n == 0) return TF_OK;
@@ -357,6 +359,7 @@ int64_t tf_step_count(const tf_ctx* ctx) { return ctx ? ctx->steps : -1; }
 int64_t tf_kernel_launches(const tf_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 int tf_conserved(tf_ctx* ctx, int inst, double out[TF_NCONS]) {
+    const TfRange nvtx_range("tf_conserved");
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
     TF_CK(ctx, tf_launch_flush(ctx));
@@ -403,11 +406,13 @@ int tf_shell_counts(tf_ctx* ctx, double* out, int n_shell) {
 }
 
 int tf_structure_factor(tf_ctx* ctx, int inst, double* S, int n_shell) {
+    const TfRange nvtx_range("tf_structure_factor");
     if (!S) return ctx ? fail(ctx, TF_ERR_ARG, "null array") : TF_ERR_ARG;
     return spectrum_common(ctx, inst, 0, S, n_shell, nullptr);
 }
 
 int tf_length_scale(tf_ctx* ctx, int inst, double* L) {
+    const TfRange nvtx_range("tf_length_scale");
     if (!ctx) return TF_ERR_ARG;
     if (!L) return fail(ctx, TF_ERR_ARG, "null pointer");
     std::vector<double> S(ctx->n_shell);
@@ -424,11 +429,13 @@ int tf_length_scale(tf_ctx* ctx, int inst, double* L) {
 }
 
 int tf_energy_spectrum(tf_ctx* ctx, int inst, double* E, int n_shell, double* E_total) {
+    const TfRange nvtx_range("tf_energy_spectrum");
     if (!E && !E_total) return ctx ? fail(ctx, TF_ERR_ARG, "null arrays") : TF_ERR_ARG;
     return spectrum_common(ctx, inst, 1, E, n_shell, E_total);
 }
 
 int tf_phase_difference(tf_ctx* ctx, int inst, double out[6]) {
+    const TfRange nvtx_range("tf_phase_difference");
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
     TF_CK(ctx, tf_launch_flush(ctx));
@@ -458,6 +465,7 @@ int tf_phi_stats(tf_ctx* ctx, int inst, double* mean, double* stddev) {
 }
 
 int tf_correlation(tf_ctx* ctx, int inst, int which, double* C, int n_shell) {
+    const TfRange nvtx_range("tf_correlation");
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !C) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
     if (which < TF_CORR_U || which > TF_CORR_Q) return fail(ctx, TF_ERR_ARG, "unknown correlation");
@@ -497,6 +505,7 @@ int tf_time_correlation(tf_ctx* ctx, int inst, double out[3]) {
 }
 
 int tf_defects(tf_ctx* ctx, int inst, int64_t out[3]) {
+    const TfRange nvtx_range("tf_defects");
     if (!ctx) return TF_ERR_ARG;
     if (!valid_inst(ctx, inst) || !out) return fail(ctx, TF_ERR_ARG, "bad instance or null array");
     TF_CK(ctx, tf_launch_flush(ctx));
@@ -707,6 +716,7 @@ static int advance_pipelined(tf_ctx* ctx, const void* h_in, int64_t n, void* h_o
 }
 
 int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
+    const TfRange nvtx_range("tf_advance_host");
     if (!ctx) return TF_ERR_ARG;
     if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
     if (ctx->batch > 1 && (h_in || h_out) && tf_fused_supported(ctx))

@@ -589,6 +589,7 @@ const char* tf_ensemble_last_error(const tf_ensemble* e) {
 }
 
 int tf_ensemble_step(tf_ensemble* e, int64_t n) {
+    const TfRange nvtx_range("tf_ensemble_step");
     if (!e) return TF_ERR_ARG;
     if (n < 0) return efail(e, TF_ERR_ARG, "negative step count");
     if (n == 0) return TF_OK;
@@ -622,6 +623,7 @@ int tf_ensemble_sync(tf_ensemble* e) {
 }
 
 int tf_ensemble_autotune(tf_ensemble* e, int steps_per_candidate) {
+    const TfRange nvtx_range("tf_ensemble_autotune");
     if (!e) return TF_ERR_ARG;
     if (steps_per_candidate < 1 || steps_per_candidate > kMaxStepsPerLaunch)
         return efail(e, TF_ERR_ARG, "steps_per_candidate must be in [1, 1024]");

@@ -5,12 +5,23 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
 #include <vector>
 
 #include "twofluid.h"
+
+// NVTX range named after an entry point, open while the call runs on the
+// host (it marks the call and the launches it enqueues in a profiler's
+// timeline; without a tool attached to NVTX the calls do nothing).
+struct TfRange {
+    explicit TfRange(const char* name) { nvtxRangePushA(name); }
+    ~TfRange() { nvtxRangePop(); }
+    TfRange(const TfRange&) = delete;
+    TfRange& operator=(const TfRange&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // D2Q9 velocity set (Sec. III): rest, axes counter-clockwise from +x, then
