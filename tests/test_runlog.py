@@ -81,5 +81,8 @@ def test_logged_gpu_run(tmp_path):
         assert all(ln["nonfinite"] == 0 and ln["L"] > 0 and ln["E"] >= 0 for ln in mine)
         assert all(ln["mlups"] > 0 for ln in mine[1:])
         # the logged values are the library's own observables of the final state
-        assert mine[-1]["L"] == pytest.approx(tf.length_scale(inst), rel=0, abs=0)
+        # (the shell histogram behind L sums within a block by FP64 shared-memory
+        # atomics, so two evaluations agree to rounding, not bit for bit)
+        assert mine[-1]["L"] == pytest.approx(tf.length_scale(inst), rel=1e-12)
+        assert mine[-1]["sum_phi"] == tf.conserved(inst)[0]
     tf.close()
