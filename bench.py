@@ -569,7 +569,8 @@ def run_ours(args, wl):
         el = reduce_max(time.perf_counter() - t0, world, dev)
         e2e = {"value": sites * k_e2e * world / el / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
-               "api": "tf_advance_host (raw state in, 1 step, raw state out; pipelined per instance on batches)"}
+               "api": "tf_advance_host (raw state in, 1 step, raw state out; pipelined per instance on "
+                      "batches, per row band on a single instance)"}
     tf.close()
 
     # 16-bit storage: FP32 storage on the same workload, timed the same way,

@@ -561,11 +561,24 @@ static int copy_state(tf_ctx* ctx, void* host, bool to_host) {
 // Compute lanes of the pipeline: instances are dealt to them in turn, so that
 // the steps of several instances can run at once when they outlast the copies.
 constexpr int kLanes = 4;
+// Row bands of a single instance's host-buffer advance (enqueue_banded):
+// bands of about kBandRows rows, at most kMaxBands, at least 3 (and so at
+// least kBandRows >= 12 rows, the reach of the FD-only pass).  More bands
+// shorten the pipeline's head and tail (2048^2, one step: 981 MLUPS without
+// bands, 1443 with 16 bands of 128 rows).
+constexpr int kBandRows = 64;
+constexpr int kMaxBands = 32;
+
+static int bands_for(const tf_ctx* ctx) {
+    const int k = ctx->ny / kBandRows;
+    return k < 3 ? 0 : (k > kMaxBands ? kMaxBands : k);
+}
 
 static cudaError_t make_pipeline(tf_ctx* ctx) {
     if (ctx->xfer_in) return cudaSuccess;
     const int lanes = ctx->batch < kLanes ? ctx->batch : kLanes;
-    const int events = 2 * ctx->batch + lanes + 3;
+    const int per_instance = 2 * ctx->batch + lanes + 3, banded = 3 * kMaxBands + 4;
+    const int events = per_instance > banded ? per_instance : banded;
     cudaError_t e = cudaStreamCreateWithFlags(&ctx->xfer_in, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->xfer_out, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->xfer_cap, cudaStreamNonBlocking);
@@ -651,6 +664,87 @@ static cudaError_t enqueue_pipeline(tf_ctx* ctx, cudaStream_t origin, const void
     return cudaSuccess;
 }
 
+// Host-buffer advance of a single instance in row bands, so that its upload,
+// steps and download overlap.  From the uploaded plain state, band k's
+// LBM-only pass needs the uploads of bands k - 1 .. k + 1 (it reads within
+// 4 rows), its FD-only pass the LBM-only passes of bands k - 1 .. k + 1 (it
+// reads within 12), and its download its FD-only pass.  Uploads go in the
+// order K - 1, 0, 1, .., K - 2 on one stream, downloads on another, and the
+// passes in order on one compute lane; with one step, the FD-only pass of
+// band k - 1 follows the LBM-only pass of band k, and those of bands K - 1
+// and 0 (which need the last LBM-only pass) come last.  With more steps the
+// middle ones are whole-grid launches between the two banded passes.  Each
+// band of the raw state is three strided pieces (18 population planes, phi,
+// 2 Q planes), one 2D copy each.
+static cudaError_t enqueue_banded(tf_ctx* ctx, cudaStream_t origin, const void* h_in, int64_t n,
+                                  void* h_out, FusedCursor* end) {
+    const int K = bands_for(ctx);
+    const size_t N = (size_t)ctx->N, nx = (size_t)ctx->nx, es = tf_pop_bytes(ctx->storage);
+    cudaEvent_t* ev_in = ctx->events.data();   // [K]
+    cudaEvent_t* ev_fd = ev_in + K;            // [K]: FD-only pass of band k done
+    cudaEvent_t ev_fork = ev_in[2 * K];
+    cudaEvent_t* ev_join = ev_in + 2 * K + 1;  // [3]
+    cudaStream_t lane = ctx->lanes[0];
+    PCK(cudaEventRecord(ev_fork, origin));
+    PCK(cudaStreamWaitEvent(ctx->xfer_in, ev_fork, 0));
+    PCK(cudaStreamWaitEvent(ctx->xfer_out, ev_fork, 0));
+    PCK(cudaStreamWaitEvent(lane, ev_fork, 0));
+    auto y_of = [&](int k) { return (int)((long long)k * ctx->ny / K); };
+    auto copy_band = [&](int k, bool down, const FusedCursor& c) -> cudaError_t {
+        const size_t r0 = (size_t)y_of(k), rows = (size_t)y_of(k + 1) - r0;
+        char* host = down ? static_cast<char*>(h_out) : static_cast<char*>(const_cast<void*>(h_in));
+        char* dev[3] = {(char*)ctx->d.f[c.fcur], (char*)ctx->d.phi[c.pcur], (char*)ctx->d.Q[c.pcur]};
+        const size_t elem[3] = {es, sizeof(float), sizeof(float)}, planes[3] = {18, 1, 2};
+        const size_t hoff[3] = {0, 18 * N * es, 18 * N * es + N * sizeof(float)};
+        for (int q = 0; q < 3; ++q) {
+            const size_t pitch = N * elem[q], off = r0 * nx * elem[q], w = rows * nx * elem[q];
+            const cudaError_t e =
+                down ? cudaMemcpy2DAsync(host + hoff[q] + off, pitch, dev[q] + off, pitch, w, planes[q],
+                                         cudaMemcpyDeviceToHost, ctx->xfer_out)
+                     : cudaMemcpy2DAsync(dev[q] + off, pitch, host + hoff[q] + off, pitch, w, planes[q],
+                                         cudaMemcpyHostToDevice, ctx->xfer_in);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    const FusedCursor start{ctx->fcur, ctx->pcur, ctx->ucur, false};
+    for (int j = 0; j < K; ++j) {                 // uploads: K - 1, 0, 1, .., K - 2
+        const int k = (j + K - 1) % K;
+        PCK(copy_band(k, false, start));
+        PCK(cudaEventRecord(ev_in[k], ctx->xfer_in));
+    }
+    // cursors after the LBM-only pass, after the n - 1 whole-grid steps, and at the end
+    const FusedCursor lbm{start.fcur ^ 1, start.pcur, start.ucur ^ 1, true};
+    FusedCursor mid = lbm;
+    auto fd_band = [&](int k) -> cudaError_t {
+        PCK(tf_fused_band(ctx, 0, y_of(k), y_of(k + 1), false, lane, mid));
+        PCK(cudaEventRecord(ev_fd[k], lane));
+        PCK(cudaStreamWaitEvent(ctx->xfer_out, ev_fd[k], 0));
+        const FusedCursor fin{mid.fcur, mid.pcur ^ 1, mid.ucur, false};
+        return copy_band(k, true, fin);
+    };
+    for (int k = 0; k < K; ++k) {
+        for (int d = -1; d <= 1; ++d) PCK(cudaStreamWaitEvent(lane, ev_in[(k + d + K) % K], 0));
+        PCK(tf_fused_band(ctx, 0, y_of(k), y_of(k + 1), true, lane, start));
+        if (n == 1 && k >= 2) PCK(fd_band(k - 1));
+    }
+    if (n > 1) {
+        PCK(tf_fused_span(ctx, 0, 1, n - 1, false, lane, &mid));
+        for (int k = 0; k < K; ++k) PCK(fd_band(k));
+    } else {
+        PCK(fd_band(K - 1));
+        PCK(fd_band(0));
+    }
+    *end = {mid.fcur, mid.pcur ^ 1, mid.ucur, false};
+    PCK(cudaEventRecord(ev_join[0], lane));
+    PCK(cudaStreamWaitEvent(origin, ev_join[0], 0));
+    PCK(cudaEventRecord(ev_join[1], ctx->xfer_out));
+    PCK(cudaStreamWaitEvent(origin, ev_join[1], 0));
+    PCK(cudaEventRecord(ev_join[2], ctx->xfer_in));
+    PCK(cudaStreamWaitEvent(origin, ev_join[2], 0));
+    return cudaSuccess;
+}
+
 static bool pinned_or_null(const void* p) {
     if (!p) return true;
     cudaPointerAttributes at{};
@@ -667,8 +761,12 @@ static bool pinned_or_null(const void* p) {
 // replayed on the context's stream; other host memory is enqueued directly.
 constexpr size_t kHostGraphs = 4;
 
-static int advance_pipelined(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
+static int advance_pipelined(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out, bool banded) {
     TF_CK(ctx, make_pipeline(ctx));
+    auto enqueue = [&](cudaStream_t origin, FusedCursor* end) {
+        return banded ? enqueue_banded(ctx, origin, h_in, n, h_out, end)
+                      : enqueue_pipeline(ctx, origin, h_in, n, h_out, end);
+    };
     FusedCursor probe{ctx->fcur, ctx->pcur, ctx->ucur, ctx->fd_pending};
     TF_CK(ctx, tf_fused_span(ctx, 0, 1, 0, false, ctx->stream, &probe));   // plans the tiles only
     FusedCursor end{};
@@ -682,7 +780,7 @@ static int advance_pipelined(tf_ctx* ctx, const void* h_in, int64_t n, void* h_o
         if (!g) {
             const int64_t launches0 = ctx->launches;
             TF_CK(ctx, cudaStreamBeginCapture(ctx->xfer_cap, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_pipeline(ctx, ctx->xfer_cap, h_in, n, h_out, &end);
+            cudaError_t e = enqueue(ctx->xfer_cap, &end);
             cudaGraph_t graph = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(ctx->xfer_cap, &graph);
             if (e == cudaSuccess) e = e2;
@@ -704,7 +802,7 @@ static int advance_pipelined(tf_ctx* ctx, const void* h_in, int64_t n, void* h_o
         end = {g->fcur_end, g->pcur_end, g->ucur_end, g->fd_pending_end};
         ctx->launches += g->launches;
     } else {
-        TF_CK(ctx, enqueue_pipeline(ctx, ctx->stream, h_in, n, h_out, &end));
+        TF_CK(ctx, enqueue(ctx->stream, &end));
     }
     ctx->fcur = end.fcur;
     ctx->pcur = end.pcur;
@@ -720,7 +818,9 @@ int tf_advance_host(tf_ctx* ctx, const void* h_in, int64_t n, void* h_out) {
     if (!ctx) return TF_ERR_ARG;
     if (n < 0) return fail(ctx, TF_ERR_ARG, "negative step count");
     if (ctx->batch > 1 && (h_in || h_out) && tf_fused_supported(ctx))
-        return advance_pipelined(ctx, h_in, n, h_out);
+        return advance_pipelined(ctx, h_in, n, h_out, false);
+    if (ctx->batch == 1 && h_in && h_out && n >= 1 && tf_fused_supported(ctx) && bands_for(ctx) >= 3)
+        return advance_pipelined(ctx, h_in, n, h_out, true);
     int rc;
     if (h_in) {
         ctx->fd_pending = false;  // the uploaded raw state is a plain state

@@ -20,12 +20,12 @@ struct CtxGeo {
 };
 
 // One tile per CTA: tile (blockIdx.x, blockIdx.y) of instance blockIdx.z.
-// The ny rows are cut into gridDim.y tile rows of floor or ceil(ny / gridDim.y)
-// rows each (at most TYM; the host picks gridDim.y), the nx columns into
-// gridDim.x tile columns of at most TXM columns (tile_col; the host picks
-// gridDim.x).
+// The rows [y_lo, y_hi) (all ny rows, or a band of them) are cut into
+// gridDim.y tile rows of floor or ceil((y_hi - y_lo) / gridDim.y) rows each
+// (at most TYM; the host picks gridDim.y), the nx columns into gridDim.x tile
+// columns of at most TXM columns (tile_col; the host picks gridDim.x).
 template <bool DO_FD, bool DO_LBM, class S, bool WIDE>
-__global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
+__global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a, int y_lo, int y_hi) {
     using C = CtxGeo<WIDE>;
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const TileArgs<S> a) {
         tfp::fence_mbar_init();
     }
     __syncthreads();
-    const int y0 = (int)((long long)blockIdx.y * a.ny / gridDim.y);
-    const int y1 = (int)((long long)(blockIdx.y + 1) * a.ny / gridDim.y);
+    const int y0 = y_lo + (int)((long long)blockIdx.y * (y_hi - y_lo) / gridDim.y);
+    const int y1 = y_lo + (int)((long long)(blockIdx.y + 1) * (y_hi - y_lo) / gridDim.y);
     const int x0 = tile_col(blockIdx.x, gridDim.x, a.nx), x1 = tile_col(blockIdx.x + 1, gridDim.x, a.nx);
     TF_BC_BEGIN();
     fused_tile<DO_FD, DO_LBM, S, C::TYM, false, C::TXM>(a, blockIdx.z, x0, y0, x1 - x0, y1 - y0, &bar, 0);
@@ -69,6 +69,7 @@ struct Span {
     int inst0, count, tile_rows;
     cudaStream_t stream;
     FusedCursor* cur;
+    int y_lo = 0, y_hi = 0;   // rows of a band launch (y_hi = 0: all rows, tile_rows tile rows)
 };
 
 template <class S>
@@ -91,8 +92,11 @@ void launch_as(tf_ctx* ctx, const Span& sp) {
         launch_strip<S>(a, dim3(ctx->strip_cols, ctx->strip_segs, sp.count), sp.stream);
         return;
     }
-    const dim3 grid(ctx->tile_cols, sp.tile_rows, sp.count);
-    k_fused<DO_FD, DO_LBM, S, WIDE><<<grid, NT, G::SMEM, sp.stream>>>(a);
+    const bool band = sp.y_hi > 0;
+    const int y_lo = band ? sp.y_lo : 0, y_hi = band ? sp.y_hi : ctx->ny;
+    const int rows = band ? (y_hi - y_lo + CtxGeo<WIDE>::TYM - 1) / CtxGeo<WIDE>::TYM : sp.tile_rows;
+    const dim3 grid(ctx->tile_cols, rows, sp.count);
+    k_fused<DO_FD, DO_LBM, S, WIDE><<<grid, NT, G::SMEM, sp.stream>>>(a, y_lo, y_hi);
 }
 
 template <bool DO_FD, bool DO_LBM>
@@ -259,6 +263,14 @@ cudaError_t tf_fused_span(tf_ctx* ctx, int inst0, int count, int64_t n, bool flu
     // different streams, then share the resident CTA slots as one batched
     // launch would.
     return run(ctx, Span{inst0, count, ctx->tile_rows, stream, cur}, n, flush);
+}
+
+cudaError_t tf_fused_band(tf_ctx* ctx, int inst, int y_lo, int y_hi, bool lbm, cudaStream_t stream,
+                          FusedCursor cur) {
+    cudaError_t e = plan_tile_rows(ctx);
+    if (e != cudaSuccess) return e;
+    const Span sp{inst, 1, ctx->tile_rows, stream, &cur, y_lo, y_hi};
+    return lbm ? launch<false, true>(ctx, sp) : launch<true, false>(ctx, sp);
 }
 
 cudaError_t tf_plan_fused(tf_ctx* ctx) {

@@ -212,6 +212,13 @@ struct FusedCursor {
 // are left alone (every instance of a context moves through the same buffers).
 cudaError_t tf_fused_span(tf_ctx* ctx, int inst0, int count, int64_t n, bool flush,
                           cudaStream_t stream, FusedCursor* cur);
+// One tile launch over rows [y_lo, y_hi) of instance inst only, on `stream`:
+// the LBM-only pass (lbm, from a plain state) or the FD-only pass of the
+// pending sub-steps (!lbm), reading and writing the buffers `cur` names.  The
+// LBM-only pass loads phi, Q within 4 rows of the band (it uses 2) and pulls
+// populations within 1 row; the FD-only pass loads phi, Q and u within 12.
+cudaError_t tf_fused_band(tf_ctx* ctx, int inst, int y_lo, int y_hi, bool lbm, cudaStream_t stream,
+                          FusedCursor cur);
 // Evaluate mu, the fluid-1 stress, the Guo velocities, densities and the
 // non-drag force sum of the current state into d.mu, d.tau and macro_out
 // ([B][8][N]: u1x u1y u2x u2y rho1 rho2 (G1+G2)x (G1+G2)y).

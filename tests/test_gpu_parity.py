@@ -375,6 +375,36 @@ def test_advance_host_batch_pipeline_bitwise(storage):
     assert a.step_count() == 9 and b.step_count() == 14 and d.step_count() == 5
 
 
+@pytest.mark.parametrize("nx,ny,storage,n", [(64, 384, B.STORE_F32, 1), (48, 1000, B.STORE_F16, 1),
+                                              (64, 512, B.STORE_BF16, 3), (2048, 2048, B.STORE_F32, 1)],
+                         ids=["3bands", "7bands-ragged-f16", "4bands-3steps-bf16", "2048sq-16bands"])
+def test_advance_host_banded_bitwise(nx, ny, storage, n):
+    """A single instance through host buffers runs in row bands (uploads,
+    LBM-only passes, FD-only passes and downloads of different bands overlap;
+    with more than one step the middle steps are whole-grid launches).  The
+    downloaded raw state and the context's fields equal plain device steps bit
+    for bit, also with one buffer for input and output."""
+    import torch
+    p = CFG0.with_(nx=nx, ny=ny, zeta=0.01, storage=storage)
+    a, b = make(p, seed=9), make(p, seed=9)
+    nb = a.state_bytes()
+    h_in = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    h_ref = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    a.advance_host(None, 0, h_in.data_ptr())                  # the plain state, downloaded
+    a.advance_host(h_in.data_ptr(), n, h_out.data_ptr())      # banded: upload, n steps, download
+    b.step(n)
+    b.advance_host(None, 0, h_ref.data_ptr())
+    assert torch.equal(h_out, h_ref)
+    for fld in (B.FIELD_PHI, B.FIELD_QXY, B.FIELD_U1X, B.FIELD_F1 + 5, B.FIELD_F2 + 8):
+        assert np.array_equal(a.read_field(0, fld), b.read_field(0, fld)), fld
+    a.advance_host(h_out.data_ptr(), n, h_out.data_ptr())     # one buffer in and out (graph replay)
+    b.step(n)
+    b.advance_host(None, 0, h_ref.data_ptr())
+    assert torch.equal(h_out, h_ref)
+    assert a.step_count() == b.step_count() == 2 * n
+
+
 def test_argument_errors():
     tf = make(CFG0.with_(nx=8, ny=8))
     for call in (lambda: tf.read_field(1, B.FIELD_PHI), lambda: tf.read_field(0, 99),
