@@ -26,7 +26,9 @@ and also times the same instances stepped context by context.
 arithmetic).  Such a run also times the FP32 storage on the same workload
 (speedup) and reports how far the two trajectories are apart after
 --error-steps steps from one initial state (fields, L and the energy
-spectrum of instance 0).
+spectrum of instance 0 at the end, and L, E and the spectrum averaged over
+the second half of the run, beside the same averages of an FP32 run from
+another seed: the spread chaotic sampling alone gives).
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own copy of
 the workload with its own seed (independent replicas, weak scaling); only the
@@ -473,18 +475,40 @@ def trajectory_gap(B, params, seed: int, steps: int, storage: int, dev) -> dict:
     normalised by the FP32 field's spread, and the relative differences of
     L (Eq. 27), <|u_c|^2>/2 and the energy spectrum (Eq. 22) shells."""
     import numpy as np
-    runs = {}
-    for mode in (B.STORE_F32, storage):
-        tf = B.TwoFluid([params[0].with_(storage=mode)], device=dev)
-        tf.init_fields(seed=seed, phi0=0.5, dphi=0.01, S0=0.01)
-        tf.step(steps)
+    runs, means = {}, {}
+    # time averages of L, E and the spectrum over the second half of the run
+    # (about 50 samples), the comparison that still means something once the
+    # chaotic trajectories have separated pointwise; "control" is an FP32 run
+    # from another seed, the spread that chaotic sampling alone gives them
+    every = max(1, steps // 100)
+    for mode in (B.STORE_F32, storage, "control"):
+        tf = B.TwoFluid([params[0].with_(storage=B.STORE_F32 if mode == "control" else mode)], device=dev)
+        tf.init_fields(seed=seed + (1000 if mode == "control" else 0), phi0=0.5, dphi=0.01, S0=0.01)
+        done, samples = 0, []
+        while done < steps:
+            k = min(every, steps - done)
+            tf.step(k)
+            done += k
+            if 2 * done > steps:
+                E, Et = tf.energy_spectrum(0)
+                samples.append((tf.length_scale(0), Et, E))
         flds = {k: tf.read_field(0, f) for k, f in (
             ("phi", B.FIELD_PHI), ("Qxx", B.FIELD_QXX), ("Qxy", B.FIELD_QXY),
             ("u1x", B.FIELD_U1X), ("u1y", B.FIELD_U1Y), ("u2x", B.FIELD_U2X), ("u2y", B.FIELD_U2Y))}
         E, Et = tf.energy_spectrum(0)
         runs[mode] = (flds, tf.length_scale(0), E, Et)
+        means[mode] = (float(np.mean([x[0] for x in samples])), float(np.mean([x[1] for x in samples])),
+                       np.mean([x[2] for x in samples], axis=0), len(samples))
         tf.close()
     (f0, L0, E0, Et0), (f1, L1, E1, Et1) = runs[B.STORE_F32], runs[storage]
+    mL0, mE0, mS0, ns = means[B.STORE_F32]
+    mlive = mS0 > 1e-3 * mS0.max()
+
+    def mean_gaps(m):
+        mL, mE, mS, _ = m
+        return {"L_mean_rel": abs(mL - mL0) / mL0, "E_total_mean_rel": abs(mE - mE0) / mE0,
+                "E_shell_mean_l1": float(np.abs(mS - mS0).sum() / mS0.sum()),
+                "E_shell_mean_rel_max": float((np.abs(mS - mS0)[mlive] / mS0[mlive]).max())}
 
     def gap(a, b):
         sp = float(np.abs(a - a.mean()).max()) or float(np.abs(a).max()) or 1.0
@@ -497,7 +521,10 @@ def trajectory_gap(B, params, seed: int, steps: int, storage: int, dev) -> dict:
             "u": max(ugap.values()), "L_rel": abs(L1 - L0) / L0,
             "E_total_rel": abs(Et1 - Et0) / Et0,
             "E_shell_rel_max": float((np.abs(E1 - E0)[live] / E0[live]).max()),
-            "normalisation": "max |X_16 - X_32| / max |X_32 - <X_32>| (u: largest u spread)"}
+            "mean_samples": ns, **mean_gaps(means[storage]),
+            "control_fp32_other_seed": mean_gaps(means["control"]),
+            "normalisation": "max |X_16 - X_32| / max |X_32 - <X_32>| (u: largest u spread); "
+                             "means over the second half of the run"}
 
 
 def run_ours(args, wl):
