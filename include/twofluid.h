@@ -311,17 +311,18 @@ int tf_load(tf_ctx* ctx, const char* path);
 int tf_plan_tiles(int nx, int ny, int batch, long long slots, int out[3], int* col_start,
                   int cap);
 
-/* ---- ensembles: several contexts stepped by one persistent launch ----- */
+/* ---- ensembles: several contexts stepped together ----------------------- */
 /* The paper explores its parameters (activity zeta, tumbling lambda, Frank
  * constant K; Sec. IV) through many separate runs; it has no counterpart to
  * this batching layer.  An ensemble steps several contexts ("groups", each a
- * batch of instances sharing one grid size) together: one lattice step of
- * every member instance is one pass of a persistent cooperative kernel over
- * a ragged work-list of 32 x TY tiles that CTAs take in turn from an atomic
- * counter, and one launch runs many steps separated by a grid barrier.  Every
- * wait in that kernel is bounded; a wait that runs out stops the launch and
- * reports TF_ERR_TIMEOUT through the members' tf_sync.  A launch shape seen
- * before is replayed from a cached CUDA graph.
+ * batch of instances sharing one grid size) together, in one of three launch
+ * shapes its autotuner chooses from (tf_ensemble_autotune): a persistent
+ * cooperative kernel over a ragged work-list of tiles that CTAs take in turn
+ * from an atomic counter, one launch running many steps separated by a grid
+ * barrier (every wait in it is bounded; a wait that runs out stops the launch
+ * and reports TF_ERR_TIMEOUT through the members' tf_sync); one launch per
+ * step over the tiles of every group; or each group's own per-context
+ * launches.  A launch shape seen before is replayed from a cached CUDA graph.
  *
  * The ensemble does not own the members' state: between ensemble calls the
  * members' own entry points (tf_read_field, observables, tf_save, ...) see
