@@ -561,7 +561,7 @@ __global__ void k_writeback(const float* __restrict__ raw, const float* __restri
             const float w = d2q9_w(k);
             const float dev = w * (rho - 1.f) + w * rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
             const int sx = wrap_i(x - d2q9_cx(k), nx), sy = wrap_i(y - d2q9_cy(k), ny);
-            pop_store(f, (18LL * b + 9 * fl + k) * N + (long long)sy * nx + sx, dev, storage);
+            pop_store(f, pop_index(b, fl, k, (long long)sy * nx + sx, N), dev, storage);
         }
     }
 }

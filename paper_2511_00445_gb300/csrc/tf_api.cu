@@ -538,7 +538,7 @@ size_t tf_state_bytes(const tf_ctx* ctx) {
     return 18 * B * N * tf_pop_bytes(ctx->storage) + (1 + 2) * B * N * sizeof(float);
 }
 
-// Raw state blob: populations [B][18][N] (storage type), phi [B][N], Q [B][2][N] (FP32).
+// Raw state blob: populations [B][9][N][2] (storage type), phi [B][N], Q [B][2][N] (FP32).
 static int copy_state(tf_ctx* ctx, void* host, bool to_host) {
     const size_t N = (size_t)ctx->N, B = (size_t)ctx->batch;
     char* h = (char*)host;
@@ -611,7 +611,7 @@ static cudaError_t make_pipeline(tf_ctx* ctx) {
 // upload is done.  All side streams fork from and join back to `origin`.
 // Every instance moves through the same buffer cursors, so the cursors
 // afterwards (*end) are those of any one instance.  The raw state is
-// [f: B x 18 x N][phi: B x N][Q: B x 2 x N] on both sides, so an instance is
+// [f: B x 9 x N x 2][phi: B x N][Q: B x 2 x N] on both sides, so an instance is
 // three contiguous pieces.
 static cudaError_t enqueue_pipeline(tf_ctx* ctx, cudaStream_t origin, const void* h_in, int64_t n,
                                     void* h_out, FusedCursor* end) {
@@ -674,8 +674,8 @@ static cudaError_t enqueue_pipeline(tf_ctx* ctx, cudaStream_t origin, const void
 // band k - 1 follows the LBM-only pass of band k, and those of bands K - 1
 // and 0 (which need the last LBM-only pass) come last.  With more steps the
 // middle ones are whole-grid launches between the two banded passes.  Each
-// band of the raw state is three strided pieces (18 population planes, phi,
-// 2 Q planes), one 2D copy each.
+// band of the raw state is three strided pieces (9 population planes of fluid
+// pairs, phi, 2 Q planes), one 2D copy each.
 static cudaError_t enqueue_banded(tf_ctx* ctx, cudaStream_t origin, const void* h_in, int64_t n,
                                   void* h_out, FusedCursor* end) {
     const int K = bands_for(ctx);
@@ -694,7 +694,8 @@ static cudaError_t enqueue_banded(tf_ctx* ctx, cudaStream_t origin, const void* 
         const size_t r0 = (size_t)y_of(k), rows = (size_t)y_of(k + 1) - r0;
         char* host = down ? static_cast<char*>(h_out) : static_cast<char*>(const_cast<void*>(h_in));
         char* dev[3] = {(char*)ctx->d.f[c.fcur], (char*)ctx->d.phi[c.pcur], (char*)ctx->d.Q[c.pcur]};
-        const size_t elem[3] = {es, sizeof(float), sizeof(float)}, planes[3] = {18, 1, 2};
+        // populations: 9 direction planes of N fluid pairs
+        const size_t elem[3] = {2 * es, sizeof(float), sizeof(float)}, planes[3] = {9, 1, 2};
         const size_t hoff[3] = {0, 18 * N * es, 18 * N * es + N * sizeof(float)};
         for (int q = 0; q < 3; ++q) {
             const size_t pitch = N * elem[q], off = r0 * nx * elem[q], w = rows * nx * elem[q];

@@ -78,7 +78,8 @@ TileArgs<S> span_args(tf_ctx* ctx, const Span& sp) {
     DevBuffers& d = ctx->d;
     const int fc = sp.cur->fcur, pc = sp.cur->pcur, uc = sp.cur->ucur;
     const long long N = ctx->N, b0 = sp.inst0;
-    return TileArgs<S>{static_cast<const T*>(d.f[fc]) + b0 * 18 * N, static_cast<T*>(d.f[fc ^ 1]) + b0 * 18 * N,
+    return TileArgs<S>{static_cast<const T*>(d.f[fc]) + pop_index(b0, 0, 0, 0, N),
+                       static_cast<T*>(d.f[fc ^ 1]) + pop_index(b0, 0, 0, 0, N),
                        d.phi[pc] + b0 * N, d.phi[pc ^ 1] + b0 * N, d.Q[pc] + b0 * 2 * N,
                        d.Q[pc ^ 1] + b0 * 2 * N, d.u[uc] + b0 * 4 * N, d.u[uc ^ 1] + b0 * 4 * N,
                        d.prm + b0, ctx->nx, ctx->ny, d.flags};

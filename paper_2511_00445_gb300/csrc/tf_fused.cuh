@@ -341,14 +341,14 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
             bulk_row(dst_plane(pl) + ly * W, src_plane(pl), gy, x0 - RH, wr, nx, bar);
         }
         if (DO_LBM) {
-            // the population rows the tile pulls (columns x0 - 1 .. x0 + tw)
-            // into L2, so that they stream from HBM during the sub-steps
-            const typename S::T* F = fsrc + 18 * b * N;
-            for (int t = threadIdx.x; t < 18 * (TY + 2); t += NT) {
+            // the population rows the tile pulls (the fluid pairs of columns
+            // x0 - 1 .. x0 + tw) into L2, so that they stream from HBM during
+            // the sub-steps
+            for (int t = threadIdx.x; t < 9 * (TY + 2); t += NT) {
                 const int i = t / (TY + 2), r = t - i * (TY + 2);
                 if (r >= th + 2) continue;
-                prefetch_span(F + (long long)i * N + (long long)wrapc(y0 - 1 + r, ny) * nx,
-                              max(x0 - 1, 0), min(x0 + tw, nx - 1));
+                prefetch_span(fsrc + pop_index(b, 0, i, (long long)wrapc(y0 - 1 + r, ny) * nx, N),
+                              2 * max(x0 - 1, 0), 2 * min(x0 + tw, nx - 1) + 1);
             }
         }
         const bool ok = tfp::wait_bounded(bar, phase & 1u, kWaitPolls);
@@ -431,10 +431,9 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         const float* sxy = tf_smem + P_U1Y * A;
         const float* syx = tf_smem + P_U2X * A;
         const float* syy = tf_smem + P_U2Y * A;
-        const typename S::T* F1 = fsrc + 18 * b * N;
-        const typename S::T* F2p = F1 + 9 * N;
-        typename S::T* D1 = fdst + 18 * b * N;
-        typename S::T* D2 = D1 + 9 * N;
+        using T2 = typename S::T2;
+        const T2* F1 = reinterpret_cast<const T2*>(fsrc + pop_index(b, 0, 0, 0, N));
+        T2* D1 = reinterpret_cast<T2*>(fdst + pop_index(b, 0, 0, 0, N));
         float* uo = u_out + 4 * b * N;
         // the LBM update of site (r, cx) of the tile
         auto lbm_site = [&](int r, int cx) {
@@ -450,9 +449,9 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
                 const int sy = d2q9_cy(i) == 0 ? y : (d2q9_cy(i) > 0 ? ym : yp);
                 const long long src = TF_BC64((long long)sy * nx + sx, N);
                 if constexpr (MULTI)
-                    f[i] = P2(S::load_cg(F1 + i * N + src), S::load_cg(F2p + i * N + src));
+                    f[i] = S::load2_cg(F1 + i * N + src);
                 else
-                    f[i] = P2(S::load(F1 + i * N + src), S::load(F2p + i * N + src));
+                    f[i] = S::load2(F1 + i * N + src);
             }
             f2 u1, u2;
             lbm_site2(P, phi[c], P2(phi[c - 1], phi[c + 1]), P2(phi[c - W], phi[c + W]), mu[c],
@@ -461,10 +460,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
                       P2(syy[c - W], syy[c + W]), f, u1, u2);
             const long long g = TF_BC64((long long)y * nx + x, N);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                S::store(D1 + i * N + g, f[i].x);
-                S::store(D2 + i * N + g, f[i].y);
-            }
+            for (int i = 0; i < 9; ++i) S::store2(D1 + i * N + g, f[i]);
             uo[g] = u1.x;
             uo[N + g] = u1.y;
             uo[2 * N + g] = u2.x;

@@ -47,6 +47,14 @@ __host__ __device__ constexpr double d2q9_wd(int i) {
 // FP16 carries d_i * 2^12 (an exact scale both ways) so that deviations down
 // to 1.5e-8 stay normal.  Zero bits are d_i = 0 in every mode.  load_cg reads
 // through L2 only (ld.global.cg): for data other CTAs of the same launch wrote.
+//
+// Layout: the two fluids' deviations of one direction and site are adjacent,
+// [B][9][N][2] (fluid fastest), so that a site's pull or store of direction i
+// is one 8-byte (FP32) or 4-byte (16-bit) access holding the (fluid 1,
+// fluid 2) pair the paired collision works on (2048^2 step against separate
+// fluid planes [B][18][N]: strip kernel 292 -> 277 us, tile kernel 346 -> 315
+// us).  load2 / store2 move such a
+// pair (type T2) with the same per-element conversions as load / store.
 // ---------------------------------------------------------------------------
 struct PopF32 {
     typedef float T;
@@ -54,6 +62,10 @@ struct PopF32 {
     __device__ static float load(const T* p) { return *p; }
     __device__ static float load_cg(const T* p) { return __ldcg(p); }
     __device__ static void store(T* p, float d) { *p = d; }
+    typedef float2 T2;   // (fluid 1, fluid 2)
+    __device__ static float2 load2(const T2* p) { return *p; }
+    __device__ static float2 load2_cg(const T2* p) { return __ldcg(p); }
+    __device__ static void store2(T2* p, float2 d) { *p = d; }
 };
 struct PopF16 {
     typedef __half T;
@@ -64,6 +76,18 @@ struct PopF16 {
         return __fmul_rn(__half2float(__ushort_as_half(v)), 0x1p-12f);
     }
     __device__ static void store(T* p, float d) { *p = __float2half_rn(__fmul_rn(d, 0x1p12f)); }
+    __device__ static float2 widen(__half2 h) {
+        return make_float2(__fmul_rn(__low2float(h), 0x1p-12f), __fmul_rn(__high2float(h), 0x1p-12f));
+    }
+    typedef __half2 T2;
+    __device__ static float2 load2(const T2* p) { return widen(*p); }
+    __device__ static float2 load2_cg(const T2* p) {
+        const unsigned v = __ldcg(reinterpret_cast<const unsigned*>(p));
+        return widen(*reinterpret_cast<const __half2*>(&v));
+    }
+    __device__ static void store2(T2* p, float2 d) {
+        *p = __floats2half2_rn(__fmul_rn(d.x, 0x1p12f), __fmul_rn(d.y, 0x1p12f));
+    }
 };
 struct PopBF16 {
     typedef __nv_bfloat16 T;
@@ -74,10 +98,25 @@ struct PopBF16 {
         return __bfloat162float(__ushort_as_bfloat16(v));
     }
     __device__ static void store(T* p, float d) { *p = __float2bfloat16_rn(d); }
+    __device__ static float2 widen(__nv_bfloat162 h) { return make_float2(__low2float(h), __high2float(h)); }
+    typedef __nv_bfloat162 T2;
+    __device__ static float2 load2(const T2* p) { return widen(*p); }
+    __device__ static float2 load2_cg(const T2* p) {
+        const unsigned v = __ldcg(reinterpret_cast<const unsigned*>(p));
+        return widen(*reinterpret_cast<const __nv_bfloat162*>(&v));
+    }
+    __device__ static void store2(T2* p, float2 d) { *p = __floats2bfloat162_rn(d.x, d.y); }
 };
 
 // Bytes per stored population element.
 inline size_t tf_pop_bytes(int storage) { return storage == TF_STORE_F32 ? 4 : 2; }
+
+// Element index of fluid fl's deviation of direction k at site `site` of
+// instance b (layout [B][9][N][2]).
+__host__ __device__ __forceinline__ long long pop_index(long long b, int fl, int k, long long site,
+                                                        long long N) {
+    return ((9 * b + k) * N + site) * 2 + fl;
+}
 
 // Run-time dispatch for kernels off the hot path (storage uniform per launch).
 __device__ __forceinline__ float pop_load(const void* base, long long i, int storage) {
@@ -109,8 +148,8 @@ struct DevParams {
 
 // Device buffers carved out of the caller's workspace.
 struct DevBuffers {
-    void* f[2];        // populations [B][18][N] in the storage type (pull layout:
-                       // post-collision deviations of the previous step)
+    void* f[2];        // populations [B][9][N][2 fluids] in the storage type (pull
+                       // layout: post-collision deviations of the previous step)
     float* phi[2];     // phi - phi_ref  [B][N]
     float* Q[2];       // Q_xx, Q_xy     [B][2][N]
     float* u[2];       // u1x, u1y, u2x, u2y [B][4][N]

@@ -94,8 +94,8 @@ k_init(void* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q, lon
         Q[2 * b * N + i] = (float)(S0 * cs);
         Q[(2 * b + 1) * N + i] = (float)(S0 * sn);
         for (int k = 0; k < 9; ++k) {
-            pop_store(f, (18 * b + k) * N + i, (float)(d2q9_wd(k) * ((double)P.rho1 - 1.0)), storage);
-            pop_store(f, (18 * b + 9 + k) * N + i, (float)(d2q9_wd(k) * ((double)P.rho2 - 1.0)),
+            pop_store(f, pop_index(b, 0, k, i, N), (float)(d2q9_wd(k) * ((double)P.rho1 - 1.0)), storage);
+            pop_store(f, pop_index(b, 1, k, i, N), (float)(d2q9_wd(k) * ((double)P.rho2 - 1.0)),
                       storage);
         }
     }
@@ -121,8 +121,7 @@ k_write(void* __restrict__ f, float* __restrict__ phi, float* __restrict__ Q,
         const int k = field - (fl ? TF_FIELD_F2 : TF_FIELD_F1);
         const int x = (int)(i % nx), y = (int)(i / nx);
         const int sx = tfd::wrap(x - d2q9_cx(k), nx), sy = tfd::wrap(y - d2q9_cy(k), ny);
-        pop_store(f, (18 * b + 9 * fl + k) * N + (long long)sy * nx + sx, (float)(v - d2q9_wd(k)),
-                  storage);
+        pop_store(f, pop_index(b, fl, k, (long long)sy * nx + sx, N), (float)(v - d2q9_wd(k)), storage);
     }
 }
 
@@ -143,7 +142,7 @@ k_set_eq(void* __restrict__ f, const double* __restrict__ u1, const double* __re
             const double w = d2q9_wd(k);
             const double dev = w * (rho - 1.0) + w * rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
             const int sx = tfd::wrap(x - d2q9_cx(k), nx), sy = tfd::wrap(y - d2q9_cy(k), ny);
-            pop_store(f, (18 * b + 9 * fl + k) * N + (long long)sy * nx + sx, (float)dev, storage);
+            pop_store(f, pop_index(b, fl, k, (long long)sy * nx + sx, N), (float)dev, storage);
         }
     }
 }
@@ -232,7 +231,7 @@ k_read(const void* __restrict__ f, const float* __restrict__ phi, const float* _
         const int x = (int)(i % nx), y = (int)(i / nx);
         const int sx = tfd::wrap(x - d2q9_cx(k), nx), sy = tfd::wrap(y - d2q9_cy(k), ny);
         v = d2q9_wd(k) +
-            (double)pop_load(f, (18 * b + 9 * fl + k) * N + (long long)sy * nx + sx, storage);
+            (double)pop_load(f, pop_index(b, fl, k, (long long)sy * nx + sx, N), storage);
     }
     dst[i] = v;
 }
@@ -253,8 +252,8 @@ k_conserved(const void* __restrict__ f, const float* __restrict__ phi,
         int bad = 0;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            d1[k] = pop_load(f, (18 * b + k) * N + i, storage);
-            d2[k] = pop_load(f, (18 * b + 9 + k) * N + i, storage);
+            d1[k] = pop_load(f, pop_index(b, 0, k, i, N), storage);
+            d2[k] = pop_load(f, pop_index(b, 1, k, i, N), storage);
             bad += !isfinite(d1[k]) + !isfinite(d2[k]);
         }
         const float p = phi[b * N + i], qa = Q[2 * b * N + i], qb = Q[(2 * b + 1) * N + i];

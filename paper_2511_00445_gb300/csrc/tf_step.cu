@@ -72,14 +72,13 @@ k_lbm(const void* __restrict__ fsrc, void* __restrict__ fdst, const float* __res
                         t[e], t[w], t[N + n], t[N + s], t[2 * N + e], t[2 * N + w], t[3 * N + n],
                         t[3 * N + s]);
     float f1[9], f2[9];
-    const long long F1 = 18 * b * N, F2 = F1 + 9 * N;   // element offsets of the two fluids
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
         const int sy = d2q9_cy(i) == 0 ? y : (d2q9_cy(i) > 0 ? ym : yp);
         const long long src = (long long)sy * nx + sx;
-        f1[i] = pop_load(fsrc, F1 + i * N + src, storage);
-        f2[i] = pop_load(fsrc, F2 + i * N + src, storage);
+        f1[i] = pop_load(fsrc, pop_index(b, 0, i, src, N), storage);
+        f2[i] = pop_load(fsrc, pop_index(b, 1, i, src, N), storage);
     }
     float dr1, m1x, m1y, dr2, m2x, m2y;
     tfd::moments(f1, dr1, m1x, m1y);
@@ -97,8 +96,8 @@ k_lbm(const void* __restrict__ fsrc, void* __restrict__ fdst, const float* __res
         tfd::collide(f2, dr2, v.u2x, v.u2y, v.F2x, v.F2y, P.omega2, P.guo2);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            pop_store(fdst, F1 + i * N + c, f1[i], storage);
-            pop_store(fdst, F2 + i * N + c, f2[i], storage);
+            pop_store(fdst, pop_index(b, 0, i, c, N), f1[i], storage);
+            pop_store(fdst, pop_index(b, 1, i, c, N), f2[i], storage);
         }
     } else {
         float* u0 = u + 8 * b * N;

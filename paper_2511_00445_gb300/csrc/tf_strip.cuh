@@ -205,13 +205,14 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         if (j + 1 < nblk) issue_pq(j + 1);
         // L2 prefetch of the population rows [L - 19, L - 11) that this block's
         // LBM phase pulls (rows L - 21, L - 20 came with the previous block):
-        // thread (plane, row) touches every 128-byte line of columns
-        // [x0 - 1, x0 + tw] of its row; each address lies inside the row.
-        if (threadIdx.x < 18 * R) {
+        // thread (direction, row) touches every 128-byte line of the fluid
+        // pairs of columns [x0 - 1, x0 + tw] of its row; each address lies
+        // inside the row.
+        if (threadIdx.x < 9 * R) {
             const int pl = threadIdx.x / R, t = L - 19 + threadIdx.x % R;
             if (t >= -1 && t < SG + 1) {
-                prefetch_span(a.fsrc + (18 * b + pl) * N + (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx,
-                              max(x0 - 1, 0), min(x0 + tw, nx - 1));
+                prefetch_span(a.fsrc + pop_index(b, 0, pl, (long long)TF_BC(wrapc(y0 + t, ny), ny) * nx, N),
+                              2 * max(x0 - 1, 0), 2 * min(x0 + tw, nx - 1) + 1);
             }
         }
 
@@ -402,13 +403,13 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
         {
             const int eL = L - 12;
             const int r0 = max(eL - R, 0) - (eL - R), r1 = min(eL, SG) - (eL - R);   // block rows
-            // 32-bit element indices within one fluid's nine planes (9 N < 2^31,
-            // checked by the host); the instance offset is in the 64-bit bases
+            // 32-bit pair indices within one instance's nine direction planes
+            // (9 N < 2^31, checked by the host); the instance offset is in the
+            // 64-bit bases
             const int Ni = (int)N;
-            const typename S::T* __restrict__ F1 = a.fsrc + 18 * b * N;
-            const typename S::T* __restrict__ F2p = F1 + 9 * N;
-            typename S::T* __restrict__ D1 = a.fdst + 18 * b * N;
-            typename S::T* __restrict__ D2 = D1 + 9 * N;
+            using T2 = typename S::T2;
+            const T2* __restrict__ F1 = reinterpret_cast<const T2*>(a.fsrc + pop_index(b, 0, 0, 0, N));
+            T2* __restrict__ D1 = reinterpret_cast<T2*>(a.fdst + pop_index(b, 0, 0, 0, N));
             float* __restrict__ uo = a.u_out + 4 * b * N;
             const float* stb = sm + ts::OFF_ST - ts::SC0;   // stress ring, window columns
             constexpr int PL = ts::DS * ts::SW;
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                     const int sx = d2q9_cx(i) == 0 ? x : (d2q9_cx(i) > 0 ? xm : xp);
                     const int sy = d2q9_cy(i) == 0 ? ry : (d2q9_cy(i) > 0 ? rym : ryp);
                     const int idx = TF_BC(i * Ni + sy + sx, 9 * Ni);
-                    f[i] = P2(S::load(F1 + idx), S::load(F2p + idx));
+                    f[i] = S::load2(F1 + idx);
                 }
             };
             // ring slots of the rows the block reads, from the row below its first
@@ -463,10 +464,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                           P2(ss[4 * PL + c], sn[4 * PL + c]), f, u1, u2);
                 const int g = TF_BC((y0 + t) * nx + x0 + cx, Ni);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    S::store(D1 + (i * Ni + g), f[i].x);
-                    S::store(D2 + (i * Ni + g), f[i].y);
-                }
+                for (int i = 0; i < 9; ++i) S::store2(D1 + (i * Ni + g), f[i]);
                 uo[g] = u1.x;
                 uo[N + g] = u1.y;
                 uo[2 * N + g] = u2.x;
