@@ -107,7 +107,9 @@ __device__ __forceinline__ void fd_substep(const DevParams& P, int tw, int th, i
     const float* __restrict__ u2y = tf_smem + P_U2Y * A;
     float* __restrict__ qa = tf_smem + P_QA * A;
     float* __restrict__ qb = tf_smem + P_QB * A;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp index shuffled from lane 0, so that the compiler keeps the
+    // warp-uniform row arithmetic in uniform registers (2048^2: 315 -> 307 us)
+    const int lane = threadIdx.x & 31, warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
     constexpr int NW = NT / 32;
     const f2 mu0 = S2(P.mu0), mu1 = S2(P.mu1), mu2 = S2(P.mu2), mu3 = S2(P.mu3);
     const f2 kap = S2(-P.kappa), m4 = S2(-4.f), half = S2(0.5f), cref = S2(P.phi_ref);
@@ -381,7 +383,7 @@ __device__ __forceinline__ bool fused_tile(const TileArgs<S>& a, int b, int x0, 
         }
     }
 
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int tx = threadIdx.x & 31, ty = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
     if constexpr (DO_LBM) {
         using namespace tfq;
         // ---- stage 3a: chemical potential and fluid-1 stress on radius 1

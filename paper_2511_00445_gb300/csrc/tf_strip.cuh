@@ -140,7 +140,11 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
     const int y0 = (int)((long long)blockIdx.y * ny / gridDim.y);
     const int SG = (int)((long long)(blockIdx.y + 1) * ny / gridDim.y) - y0;
     const DevParams P = a.prm[b];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // The warp index through a shuffle from lane 0: the compiler then treats
+    // it, and every row index and ring slot derived from it, as uniform across
+    // the warp and keeps that arithmetic in uniform registers (2048^2: 276 ->
+    // 269 us; 128 registers with a 24-byte spill -> 122 without).
+    const int lane = threadIdx.x & 31, warp = __shfl_sync(0xffffffffu, (int)(threadIdx.x >> 5), 0);
     const int col = 4 * min(lane, ts::LANES - 1);   // this lane's first window column
     const bool own = lane < ts::LANES;
     const int nblk = (SG + 2 * ts::HALO + R - 1) / R;   // blocks (= iterations)
@@ -216,6 +220,19 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             }
         }
 
+        // Ring row offsets of rows L - R + warp - 12 + m, m = 0 .. 12: every
+        // phi / Q row this warp's sub-steps read or write in this block, each
+        // slot found once per block instead of once per sub-step (uniform;
+        // 269 -> 268 us)
+        int offs[13];
+        {
+            int sl = pslot(L - R + warp - 12);
+#pragma unroll
+            for (int m = 0; m < 13; ++m) {
+                offs[m] = sl * WW;
+                sl = sl + 1 == ts::DP ? 0 : sl + 1;
+            }
+        }
         // ---- the five sub-steps, unrolled so that every row bound, shadow row
         // and ring offset that depends on s is a constant (2048^2: 301 -> 292
         // us; unrolling the LBM site loop as well made the code too large)
@@ -226,17 +243,20 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             const int qlo = -(7 - s), qhi = SG + 7 - s;             // exact rows of Q^(s)
             // the stage touches rows [E - R - 2, E + 2) of phi / Q and [E - R - 1,
             // E + 1) of u; the two rows below the block are this stage's shadows
-            const int tb = E - R - 2, pb = pslot(tb), ub = uslot(tb + 1);
+            const int tb = E - R - 2, ub = uslot(tb + 1);
             const int shr = ts::SH0 + 2 * (s - 1);
-            // row index (ring slot or shadow) of row t of phi^(s-1), Q^(s-1)
-            auto ridx = [&](int t) {
-                const int k = t - tb;
-                return TF_BC(k < 2 ? shr + k : step_slot<ts::DP>(pb, k), ts::FROWS);
-            };
             auto urow = [&](int t) { return TF_BC(step_slot<ts::DU>(ub, t - tb - 1), ts::DU) * WW; };
-            auto phi_row = [&](int t) -> const float* { return sm + ts::OFF_PHI + ridx(t) * WW; };
-            auto qa_row = [&](int t) -> const float* { return sm + ts::OFF_QA + ridx(t) * WW; };
-            auto qb_row = [&](int t) -> const float* { return sm + ts::OFF_QB + ridx(t) * WW; };
+            // row offset (shadow row or ring slot, times the row length) of row
+            // t = y - 2 + j of phi^(s-1), Q^(s-1); j = 0 .. 4 is a constant
+            // once the sub-steps are unrolled
+            auto rof = [&](int t) {
+                const int j = t - tb - warp;
+                const int k = warp + j;
+                return TF_BC(k < 2 ? (shr + k) * WW : offs[10 - 2 * s + j], ts::FROWS * WW);
+            };
+            auto phi_row = [&](int t) -> const float* { return sm + ts::OFF_PHI + rof(t); };
+            auto qa_row = [&](int t) -> const float* { return sm + ts::OFF_QA + rof(t); };
+            auto qb_row = [&](int t) -> const float* { return sm + ts::OFF_QB + rof(t); };
             // (a) phi^(s), Q^(s) of this warp's row into registers, with mu^(s)
             // of rows y-1, y, y+1 evaluated here from phi^(s-1) rows y-2 .. y+2
             const int y = E - R + warp;
@@ -339,7 +359,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             // (b) save the rows the next block reads below its own (phi^(s-1)
             // of rows E - 2, E - 1 and Q^(s-1) of row E - 1), then write in place
             if (own) {
-                const int py = TF_BC(step_slot<ts::DP>(pb, y - tb), ts::DP) * WW + col;
+                const int py = TF_BC(offs[12 - 2 * s], ts::DP * WW) + col;   // row y
                 if (warp >= R - 2 && y >= lo - 2) {
                     const int sh = TF_BC(shr + warp - (R - 2), ts::FROWS) * WW + col;
                     if (!vp) {   // row not computed: its old values are not in registers
