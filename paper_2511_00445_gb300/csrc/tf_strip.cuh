@@ -368,8 +368,10 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                         oqb = ld4(sm + ts::OFF_QB + py);
                     }
                     st4(sm + ts::OFF_PHI + sh, oph);
-                    st4(sm + ts::OFF_QA + sh, oqa);
-                    st4(sm + ts::OFF_QB + sh, oqb);
+                    if (warp == R - 1) {   // Q is read one row outside a block, phi two
+                        st4(sm + ts::OFF_QA + sh, oqa);
+                        st4(sm + ts::OFF_QB + sh, oqb);
+                    }
                 }
                 if (vp) st4(sm + ts::OFF_PHI + py, nph);
                 if (vq) {
