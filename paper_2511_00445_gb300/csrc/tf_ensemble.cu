@@ -256,6 +256,11 @@ struct tf_ensemble {
     std::vector<EnsGroup> host_groups;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;         // private stream used only to record graphs
+    // Group-plan steps: groups 1 .. n-1 run on their own streams, forked from
+    // and joined back to the launching one (in a captured graph: parallel
+    // branches), so that one group's CTAs fill the last wave of another's.
+    std::vector<cudaStream_t> branch;          // [n_groups - 1], empty: one stream
+    std::vector<cudaEvent_t> branch_ev;        // [n_groups]: the fork, then one join per branch
     int storage = TF_STORE_F32;
     EnsGroup* d_groups = nullptr;
     EnsCtl* d_ctl = nullptr;
@@ -274,6 +279,13 @@ struct tf_ensemble {
 };
 
 namespace {
+
+void release_branches(tf_ensemble* e) {
+    for (cudaStream_t b : e->branch) cudaStreamDestroy(b);
+    for (cudaEvent_t ev : e->branch_ev) cudaEventDestroy(ev);
+    e->branch.clear();
+    e->branch_ev.clear();
+}
 
 int efail(tf_ensemble* e, int code, const std::string& msg) {
     if (e) e->last_error = msg;
@@ -323,15 +335,31 @@ cudaError_t enqueue(tf_ensemble* e, int mode, int steps, int cfg, int grid, cuda
     const int ti = mode == kPrologue ? 0 : shape_of(cfg);
     if (grid < 1) return cudaErrorInvalidConfiguration;
     if (mode == kSteady && cfg == kGroupPlans) {
-        // each group's own launches, from the ensemble's buffer parities
-        for (size_t g = 0; g < e->groups.size(); ++g) {
+        // each group's own launches, from the ensemble's buffer parities; the
+        // groups are independent, so all but the first go on branch streams
+        const size_t ng = e->groups.size();
+        const bool fork = ng > 1 && e->branch.size() == ng - 1;
+        cudaError_t err = cudaSuccess;
+        if (fork) {
+            err = cudaEventRecord(e->branch_ev[0], st);
+            for (size_t g = 1; g < ng && err == cudaSuccess; ++g)
+                err = cudaStreamWaitEvent(e->branch[g - 1], e->branch_ev[0], 0);
+            if (err != cudaSuccess) return err;
+        }
+        for (size_t g = 0; g < ng; ++g) {
             tf_ctx* c = e->groups[g];
             FusedCursor cur{e->base_f[g] ^ e->fpar, e->base_p[g] ^ e->ppar,
                             e->base_u[g] ^ e->upar, true};
-            const cudaError_t err = tf_fused_span(c, 0, c->batch, steps, false, st, &cur);
+            err = tf_fused_span(c, 0, c->batch, steps, false, fork && g > 0 ? e->branch[g - 1] : st, &cur);
             if (err != cudaSuccess) return err;
         }
-        return cudaSuccess;
+        if (fork) {
+            for (size_t g = 1; g < ng && err == cudaSuccess; ++g) {
+                err = cudaEventRecord(e->branch_ev[g], e->branch[g - 1]);
+                if (err == cudaSuccess) err = cudaStreamWaitEvent(st, e->branch_ev[g], 0);
+            }
+        }
+        return err;
     }
     if (mode == kSteady && !persistent_cfg(cfg)) {
         const StepKernel k = step_kernel_for(e->storage, ti);
@@ -560,13 +588,34 @@ int tf_ensemble_create(tf_ctx* const* groups, int n_groups, void* d_workspace,
         e->cap_stream = nullptr;   // graphs unavailable; launches go directly into the stream
         cudaGetLastError();
     }
+    if (err == cudaSuccess && n_groups > 1) {
+        // branch streams and events for the group-plan steps; without them
+        // the groups' launches stay on one stream
+        bool ok = true;
+        for (int g = 1; g < n_groups && ok; ++g) {
+            cudaStream_t b = nullptr;
+            ok = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) e->branch.push_back(b);
+        }
+        for (int g = 0; g < n_groups && ok; ++g) {
+            cudaEvent_t ev = nullptr;
+            ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+            if (ok) e->branch_ev.push_back(ev);
+        }
+        if (!ok) {
+            release_branches(e);
+            cudaGetLastError();
+        }
+    }
     if (err != cudaSuccess || !coop) {
+        release_branches(e);
         if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
         delete e;
         return TF_ERR_CUDA;
     }
     const int rc = normalise(e);
     if (rc != TF_OK) {
+        release_branches(e);
         if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
         delete e;
         return rc;
@@ -579,6 +628,7 @@ int tf_ensemble_destroy(tf_ensemble* e) {
     if (!e) return TF_ERR_ARG;
     cudaStreamSynchronize(e->stream);
     for (auto& kv : e->cache) cudaGraphExecDestroy(kv.second);
+    release_branches(e);
     if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
     delete e;
     return TF_OK;
