@@ -322,7 +322,9 @@ int tf_plan_tiles(int nx, int ny, int batch, long long slots, int out[3], int* c
  * barrier (every wait in it is bounded; a wait that runs out stops the launch
  * and reports TF_ERR_TIMEOUT through the members' tf_sync); one launch per
  * step over the tiles of every group; or each group's own per-context
- * launches.  A launch shape seen before is replayed from a cached CUDA graph.
+ * launches, the groups on parallel branches (streams forked from and joined
+ * back to the ensemble's stream), so that their launches overlap.  A launch
+ * shape seen before is replayed from a cached CUDA graph.
  *
  * The ensemble does not own the members' state: between ensemble calls the
  * members' own entry points (tf_read_field, observables, tf_save, ...) see
