@@ -31,8 +31,8 @@
 // The LBM pulls its populations straight from global memory.  At the start
 // of a block every CTA asks L2 for the population rows its LBM phase will pull
 // (per-thread prefetch instructions, ~3 per thread; 343 -> 325 us per 2048^2
-// step), each thread issues its first site's pulls before the barrier that
-// publishes the stress rows and the next site's pulls before computing the
+// step), each thread issues its first site's pulls before waiting for the
+// stress rows its LBM row reads and the next site's pulls before computing the
 // current one.  Measured and removed (2048^2, per step): bulk L2 prefetches
 // through the copy engine (525 -> 442 us without them), prefetching one block
 // further ahead (340 us), and loading the window rows with one bulk copy per
@@ -149,6 +149,14 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
     const bool own = lane < ts::LANES;
     const int nblk = (SG + 2 * ts::HALO + R - 1) / R;   // blocks (= iterations)
     TF_BC_BEGIN();
+    // Warp k's stress row of the current block is stored: one mbarrier per
+    // warp, all 32 lanes arrive once per block.  A warp's LBM row reads the
+    // stress rows of warps k - 2 .. k only (the rows above the block came with
+    // the previous one), so it waits for those three instead of the whole CTA
+    // (2048^2: 266.3 -> 264.7 us).
+    __shared__ __align__(8) uint64_t stress_bar[ts::NW];
+    if (threadIdx.x < ts::NW) tfp::mbar_init(&stress_bar[threadIdx.x], 32);
+    __syncthreads();
 
 
     // Window copies: 16-byte per-thread asynchronous copies.  Warp w copies
@@ -420,6 +428,8 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                     st4(st + 4 * PL, {r0.syy, r1.syy});
                 }
             }
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tfp::smem_addr(&stress_bar[warp]))
+                         : "memory");
         }
         // ---- LBM of rows [L - 12 - R, L - 12) and stores of the new state
         {
@@ -438,7 +448,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             // One block row per warp (its ring slots, row wraps and row bases are
             // warp-uniform), columns lane, lane + 32, lane + 64 of the strip, the
             // next site's pulls in flight while this site is computed (the first
-            // site's before the barrier).  2048^2: 268.9 -> 266.5 us against
+            // site's before the wait for the stress rows).  2048^2: 268.9 -> 266.5 us against
             // the block's sites dealt out to all threads in row-major order.
             const int tb = eL - R + r0 - 1;                // the row below the block's first
             const int pb = pslot(tb), sb = sslot(tb);
@@ -468,7 +478,14 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
             };
             f2 f[9], fn[9];
             if (wrow && lane < tw) pull(f, lane);
-            __syncthreads();   // the stress rows of this block
+            {
+                // stress rows t - 1 .. t + 1 of this warp's LBM row: those of
+                // warps warp - 2 .. warp; every wait is bounded
+                bool ok = true;
+                for (int k = max(warp - 2, 0); k <= warp; ++k)
+                    ok = tfp::wait_bounded(&stress_bar[k], (uint32_t)(j & 1), kWaitPolls) && ok;
+                if (!ok) atomicExch(a.err, TF_ERR_TIMEOUT);
+            }
             if (wrow) {
 #pragma unroll 1
                 for (int cx = lane; cx < tw; cx += 32) {
