@@ -175,3 +175,22 @@ def test_printed_parameter_set_stability():
     assert _printed_run(P["dt"], 2000) is None
     blew = _printed_run(1.0, 2000)
     assert blew is not None and blew < 2000
+
+
+def test_longrun_ensemble_fixture_matches_the_oracle():
+    """golden/longrun_ensemble_64.json is the oracle's own record: its first
+    L(t) values for seed 3 come out again from the oracle (1000 steps)."""
+    import json
+    import sys
+    sys.path.insert(0, str(Path(__file__).parent / "golden"))
+    import make_longrun_ensemble as M
+    doc = json.loads((Path(__file__).parent / "golden" / "longrun_ensemble_64.json").read_text())
+    c = doc["config"]
+    assert (c["zeta"], c["steps"], c["every"], c["window_from"]) == (M.ZETA, M.STEPS, M.EVERY, M.WINDOW_FROM)
+    p = O.Params(nx=c["nx"], ny=c["ny"], zeta=c["zeta"])
+    up, ut = inputs.initial_draws(3, p.nx, p.ny)
+    Q = O.q_from_director(c["S0"], np.pi * ut)
+    s = O.state_from_fields(c["phi0"] + c["dphi"] * (2.0 * up - 1.0), Q[0, 0], Q[0, 1], p)
+    for r in range(4):
+        s = O.run(s, p, c["every"])
+        assert O.length_scale(s.phi) == pytest.approx(doc["L"]["3"][r], rel=1e-9)
