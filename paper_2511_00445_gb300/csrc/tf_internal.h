@@ -55,6 +55,10 @@ __host__ __device__ constexpr double d2q9_wd(int i) {
 // fluid planes [B][18][N]: strip kernel 292 -> 277 us, tile kernel 346 -> 315
 // us).  load2 / store2 move such a
 // pair (type T2) with the same per-element conversions as load / store.
+// store2_stream is store2 with an evict-first (streaming) store, for a step
+// whose state is larger than L2: the new populations are read only by the
+// next step, so they need not displace the source rows prefetched into L2
+// for this step's pulls (2048^2 strip kernel: 264.6 -> 262.9 us).
 // ---------------------------------------------------------------------------
 struct PopF32 {
     typedef float T;
@@ -66,6 +70,7 @@ struct PopF32 {
     __device__ static float2 load2(const T2* p) { return *p; }
     __device__ static float2 load2_cg(const T2* p) { return __ldcg(p); }
     __device__ static void store2(T2* p, float2 d) { *p = d; }
+    __device__ static void store2_stream(T2* p, float2 d) { __stcs(p, d); }
 };
 struct PopF16 {
     typedef __half T;
@@ -88,6 +93,10 @@ struct PopF16 {
     __device__ static void store2(T2* p, float2 d) {
         *p = __floats2half2_rn(__fmul_rn(d.x, 0x1p12f), __fmul_rn(d.y, 0x1p12f));
     }
+    __device__ static void store2_stream(T2* p, float2 d) {
+        const __half2 h = __floats2half2_rn(__fmul_rn(d.x, 0x1p12f), __fmul_rn(d.y, 0x1p12f));
+        __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&h));
+    }
 };
 struct PopBF16 {
     typedef __nv_bfloat16 T;
@@ -106,6 +115,10 @@ struct PopBF16 {
         return widen(*reinterpret_cast<const __nv_bfloat162*>(&v));
     }
     __device__ static void store2(T2* p, float2 d) { *p = __floats2bfloat162_rn(d.x, d.y); }
+    __device__ static void store2_stream(T2* p, float2 d) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(d.x, d.y);
+        __stcs(reinterpret_cast<unsigned*>(p), *reinterpret_cast<const unsigned*>(&h));
+    }
 };
 
 // Bytes per stored population element.

@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const TileArgs<S> a) {
                               P2(ss[4 * PL + c], sn[4 * PL + c]), f, u1, u2);
                     const int g = TF_BC(ry + x0 + cx, Ni);
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) S::store2(D1 + (i * Ni + g), f[i]);
+                    for (int i = 0; i < 9; ++i) S::store2_stream(D1 + (i * Ni + g), f[i]);
                     uo[g] = u1.x;
                     uo[N + g] = u1.y;
                     uo[2 * N + g] = u2.x;
